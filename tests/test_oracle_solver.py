@@ -1,0 +1,89 @@
+"""Pins for the oracle's assembled operator, Jacobi diagonal and PCG (Sec. 2)."""
+
+import numpy as np
+import pytest
+
+from oracle import mesh, solver
+from sem_inputs import forcing
+
+
+@pytest.mark.parametrize("maker,h2", [
+    (lambda: mesh.box(2, 2, 2, 3), 0.0),
+    (lambda: mesh.pipe(2, 1, 2, 3, L=2.0), 0.0),
+    (lambda: mesh.pipe(2, 1, 2, 2, L=2.0), 5.0),
+])
+def test_dense_spd_pcg_matches_cholesky(maker, h2):
+    m = maker()
+    P = solver.Problem(m, 1.0, h2)
+    A, free, rep = P.dense()
+    assert np.abs(A - A.T).max() < 1e-13 * np.abs(A).max()
+    L = np.linalg.cholesky(A)  # raises unless SPD
+    assert L.shape == A.shape
+    # Jacobi diagonal equals the dense diagonal
+    Minv = P.jacobi_inverse().reshape(-1)
+    np.testing.assert_allclose(1.0 / Minv[rep[free]], np.diag(A), rtol=1e-13)
+    # PCG vs a direct solve
+    f = forcing.evaluate(m.xyz, forcing.random_modes(7, L=2.0))
+    b = P.rhs(f)
+    res = solver.pcg(P, b)
+    assert res.status == solver.CONVERGED and res.rel_res <= 1e-10
+    xd = np.linalg.solve(A, b.reshape(-1)[rep[free]])
+    xg = res.x.reshape(-1)[rep[free]]
+    assert np.linalg.norm(xg - xd) <= 1e-9 * np.linalg.norm(xd)
+
+
+def test_manufactured_solution_spectral_convergence_box():
+    errs = []
+    for N in (2, 4, 6, 8):
+        m = mesh.box(2, 2, 2, N)
+        P = solver.Problem(m)
+        b = P.rhs(forcing.manufactured(m.xyz))
+        res = solver.pcg(P, b, tol=1e-13)
+        errs.append(np.abs(res.x - forcing.manufactured_solution(m.xyz)).max())
+    assert all(errs[i + 1] < 0.05 * errs[i] for i in range(len(errs) - 1)), errs
+    assert errs[-1] < 1e-6, errs
+
+
+def test_manufactured_solution_converges_on_curved_pipe():
+    # u* = (1 - r^2) cos(2 pi z / L): zero on the wall r = 1, periodic in z;
+    # f = -lap u* = [4 + (1 - r^2) (2 pi / L)^2] cos(2 pi z / L).
+    L = 2.0
+    k = 2 * np.pi / L
+    errs = []
+    for N in (3, 5, 7):
+        m = mesh.pipe(2, 1, 2, N, L=L)
+        x, y, z = m.xyz[:, 0], m.xyz[:, 1], m.xyz[:, 2]
+        r2 = x * x + y * y
+        f = (4.0 + (1.0 - r2) * k * k) * np.cos(k * z)
+        ustar = (1.0 - r2) * np.cos(k * z)
+        P = solver.Problem(m)
+        res = solver.pcg(P, P.rhs(f), tol=1e-13)
+        errs.append(np.abs(res.x - ustar).max())
+    assert errs[0] > errs[1] > errs[2], errs
+    assert errs[-1] < 1e-4, errs
+
+
+def test_zero_rhs_and_initial_guess():
+    m = mesh.box(2, 2, 2, 3)
+    P = solver.Problem(m)
+    res = solver.pcg(P, np.zeros(P.shape))
+    assert res.iters == 0 and np.all(res.x == 0)
+    b = P.rhs(forcing.manufactured(m.xyz))
+    exact = solver.pcg(P, b, tol=1e-13).x
+    res = solver.pcg(P, b, x0=exact)
+    assert res.iters == 0
+
+
+@pytest.mark.parametrize("inner_tol", [1e-3, 1e-5])
+def test_mixed_precision_refinement(inner_tol):
+    m = mesh.pipe(2, 1, 2, 4, L=2.0)
+    P = solver.Problem(m, 1.0, 0.5)
+    b = P.rhs(forcing.evaluate(m.xyz, forcing.random_modes(3, L=2.0)))
+    res = solver.pcg_mixed(P, b, tol=1e-10, inner_tol=inner_tol)
+    assert res.status == solver.CONVERGED
+    r = b - P.A(res.x)
+    assert np.sqrt(P.dot(r, r) / P.dot(b, b)) <= 1e-10
+    ref = solver.pcg(P, b, tol=1e-12).x
+    err = np.sqrt(P.dot(res.x - ref, res.x - ref) / P.dot(ref, ref))
+    assert err < 1e-8
+    assert res.outer_iters >= 2  # FP32 alone cannot reach 1e-10
