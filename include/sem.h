@@ -1,0 +1,269 @@
+/*
+ * sem.h -- C ABI of the GB300 (sm_103a) SEM Poisson/Helmholtz hot path.
+ *
+ * The library implements the data-parallel hot path of the spectral element
+ * pressure/Helmholtz solve scaled in Vincent et al., "Strong Scaling of
+ * OpenACC enabled Nek5000 on several GPU based HPC systems" (arXiv
+ * 2109.03592):
+ *
+ *   - the matrix-free local operator w = A_L u of Alg. 1 (tensor-product
+ *     derivative contractions with the GLL matrix D along r, s, t, the
+ *     pointwise product with the geometric factors g1..g6 and h1, the D^T
+ *     back-contractions) plus the h2 * B mass term of the Helmholtz problem
+ *     (Sec. 2, Eq. 4);
+ *   - direct stiffness summation QQ^T over shared GLL nodes, the "exchange of
+ *     element face values" of Sec. 2, followed by the Dirichlet mask;
+ *   - Jacobi-preconditioned conjugate gradients (Sec. 2: "iterative solvers
+ *     with proper preconditioners"), in FP64 and as FP32-inner / FP64-outer
+ *     iterative refinement;
+ *   - a request server that solves many such problems concurrently.
+ *
+ * Conventions shared by every entry point:
+ *
+ *   Local vectors ("E-vectors") hold one value per element-local GLL point,
+ *   duplicated on shared faces/edges/vertices, in the layout of Alg. 1's
+ *   u(i,j,k,e): index l = i + n*(j + n*(k + n*e)), n = N+1, contiguous.  They
+ *   are FP64 (double) unless an entry point's `prec` says SEM_FP32 (float).
+ *
+ *   `_dev` pointers are device pointers on the current CUDA device, owned by
+ *   the caller (for example PyTorch tensors passed by data_ptr()).  `_host`
+ *   pointers are host memory owned by the caller.  The library owns every
+ *   array inside a sem_mesh / sem_server.
+ *
+ *   `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *   asynchronous on it unless stated otherwise.
+ *
+ *   Every call returns a sem_status and never aborts; on failure
+ *   sem_last_error() gives a message for the calling thread.  No call falls
+ *   back to CPU computation: without a usable GPU the calls fail with
+ *   SEM_ERR_CUDA.
+ */
+#ifndef SEM_H
+#define SEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SEM_OK = 0,
+  SEM_ERR_INVALID = 1,        /* bad argument or descriptor */
+  SEM_ERR_OOM = 2,            /* device allocation failed, or a request exceeds the server's HBM budget */
+  SEM_ERR_CUDA = 3,           /* a CUDA call failed (text in sem_last_error) */
+  SEM_ERR_NOT_CONVERGED = 4,  /* maxit reached before the tolerance */
+  SEM_ERR_BREAKDOWN = 5,      /* p^T A p <= 0 or NaN inside CG */
+  SEM_ERR_BUSY = 6,           /* server queue full */
+  SEM_ERR_DEVICE_TIMEOUT = 7, /* a bounded device-side wait gave up */
+  SEM_ERR_BAD_MESH = 8,       /* inverted element (det J <= 0) or inconsistent topology */
+  SEM_ERR_TIMEOUT = 9,        /* sem_server_poll: result not ready within timeout */
+  SEM_ERR_NOT_FOUND = 10,     /* unknown request id */
+  SEM_ERR_CANCELLED = 11      /* request cancelled before it finished */
+} sem_status;
+
+typedef enum { SEM_FP64 = 0, SEM_FP32 = 1, SEM_MIXED = 2 } sem_prec;
+
+typedef enum { SEM_MESH_BOX = 0, SEM_MESH_PIPE = 1, SEM_MESH_EXPLICIT = 2 } sem_mesh_kind;
+
+/*
+ * Mesh descriptor (Sec. 2: non-overlapping, body-conforming hexahedra; Sec. 4.2:
+ * straight pipe flow case).  Element faces are numbered 0: i=0, 1: i=N,
+ * 2: j=0, 3: j=N, 4: k=0, 5: k=N; element corner c = a + 2b + 4d sits at
+ * (i, j, k) = (a N, b N, d N).
+ *
+ * SEM_MESH_BOX: [0,lx]x[0,ly]x[0,lz], nx*ny*nz affine elements ordered
+ *   e = ex + nx (ey + ny ez), homogeneous Dirichlet on all six faces.
+ * SEM_MESH_PIPE: O-grid straight pipe of radius R and length L: a central
+ *   square of half-width a with nc x nc elements and four curved blocks of
+ *   nc (tangential) x nr (radial) elements; in the +x block the point with
+ *   tangential s in [-1,1] and radial t in [0,1] is
+ *   (1-t)(a, a s) + t R (cos(pi s/4), sin(pi s/4)), the other blocks are its
+ *   rotations by 90/180/270 degrees; radial levels
+ *   t_k = 1 - tanh(beta(1-k/nr))/tanh(beta); nzp uniform layers in z.
+ *   Element e = layer * nc(nc+4nr) + e2d; square elements first
+ *   (e2d = ey nc + ex, i along x, j along y), then blocks q = 0..3
+ *   (e2d = nc^2 + q nc nr + r nc + m; i runs outward, j along s); k along z.
+ *   Dirichlet on the wall (face 1 of the outermost ring); periodic in z when
+ *   periodic_z != 0 (then nzp >= 3), else Dirichlet end caps too.
+ * SEM_MESH_EXPLICIT: E elements with host arrays xyz [E][3][n^3] (GLL point
+ *   coordinates, component-major per element), vert [E][8] (global vertex
+ *   ids per corner; shared corners share ids, periodic identifications too)
+ *   and dirichlet_face [E][6] (nonzero = Dirichlet face).  The arrays are
+ *   read during sem_mesh_create only.
+ */
+typedef struct {
+  int kind; /* sem_mesh_kind */
+  int N;    /* polynomial order, 1 <= N <= 11 */
+  int nx, ny, nz;
+  double lx, ly, lz;
+  int nc, nr, nzp;
+  double R, L, a, beta;
+  int periodic_z;
+  int64_t E;
+  const double* xyz;
+  const int64_t* vert;
+  const uint8_t* dirichlet_face;
+} sem_mesh_desc;
+
+typedef struct sem_mesh sem_mesh;
+
+typedef struct {
+  int64_t E;            /* elements */
+  int N;                /* order */
+  int64_t n_local;      /* E (N+1)^3 */
+  int64_t n_global;     /* distinct GLL nodes */
+  int64_t n_segments;   /* gather-scatter segments (shared or Dirichlet nodes) */
+  int64_t n_seg_points; /* local points inside those segments */
+  size_t dev_bytes;     /* device memory held by the mesh */
+} sem_mesh_info_t;
+
+/* Build a mesh on the current device: coordinates, geometric factors
+ * g1..g6 and B (FP64, plus FP32 copies), the first-touch global numbering,
+ * the gather-scatter plan, multiplicities, the Dirichlet mask and the
+ * assembled diagonals used by the Jacobi preconditioner.  Synchronous.
+ * SEM_ERR_BAD_MESH if some det J <= 0 or the topology is inconsistent. */
+sem_status sem_mesh_create(const sem_mesh_desc* desc, void* stream, sem_mesh** out);
+sem_status sem_mesh_destroy(sem_mesh* mesh);
+sem_status sem_mesh_info(const sem_mesh* mesh, sem_mesh_info_t* info);
+
+/* Global id of every local point, assigned in order of first appearance when
+ * local points are scanned in ascending local index (host output, n_local
+ * int64).  Two local points share an id iff they are the same GLL node. */
+sem_status sem_mesh_global_ids(const sem_mesh* mesh, int64_t* host_out);
+
+/* Copies of mesh data into caller buffers (device, FP64, local layout):
+ * coordinates [E][3][n^3]; factors G [E][6][n^3] (g1..g6 = G_rr, G_ss, G_tt,
+ * G_rs, G_rt, G_st of w_i w_j w_k detJ J^{-1} J^{-T}); B [E][n^3]
+ * (w_i w_j w_k detJ); multiplicity and mask [n_local] (mask = 0 on Dirichlet
+ * nodes, 1 elsewhere).  Any output pointer may be NULL to skip it. */
+sem_status sem_mesh_coords(const sem_mesh* mesh, double* xyz_dev, void* stream);
+sem_status sem_mesh_geometry(const sem_mesh* mesh, double* G_dev, double* B_dev, void* stream);
+sem_status sem_mesh_weights(const sem_mesh* mesh, double* mult_dev, double* mask_dev, void* stream);
+
+/* w = A_L u: Alg. 1 plus the Helmholtz term, element by element, with scalar
+ * h1 (scaling the stiffness after the G contraction) and h2 (scaling B u).
+ * No assembly and no mask.  u and w: local vectors of `prec` SEM_FP64 or
+ * SEM_FP32 (SEM_FP32 uses the FP32 factors).  u and w must not overlap. */
+sem_status sem_ax(const sem_mesh* mesh, const void* u_dev, void* w_dev, double h1, double h2,
+                  sem_prec prec, void* stream);
+
+/* v <- QQ^T v in place (sum over all copies of each node, in ascending local
+ * index, written back to every copy); then, if apply_mask, v <- 0 on every
+ * Dirichlet node.  Bit-reproducible.  prec SEM_FP64 or SEM_FP32. */
+sem_status sem_gs(const sem_mesh* mesh, void* v_dev, sem_prec prec, int apply_mask, void* stream);
+
+/* Right-hand side b = mask QQ^T (B f) from nodal forcing values f (FP64). */
+sem_status sem_rhs(const sem_mesh* mesh, const double* f_dev, double* b_dev, void* stream);
+
+/* Assembled operator y = mask QQ^T A_L x (FP64). */
+sem_status sem_apply(const sem_mesh* mesh, const double* x_dev, double* y_dev, double h1, double h2,
+                     void* stream);
+
+/* Jacobi preconditioner M^{-1} = mask / QQ^T diag(A_L) for (h1, h2) (FP64;
+ * 0 on Dirichlet nodes). */
+sem_status sem_jacobi(const sem_mesh* mesh, double h1, double h2, double* minv_dev, void* stream);
+
+typedef struct {
+  double tol;       /* stop when ||r|| <= tol ||b||, ||v||^2 = sum_l v_l^2 / mult_l; default 1e-10 */
+  double h1, h2;    /* operator coefficients (Poisson: 1, 0) */
+  double inner_tol; /* SEM_MIXED: relative tolerance of each FP32 inner solve; <= 0 picks the tuned value */
+  int maxit;        /* iteration cap (per inner solve for SEM_MIXED); <= 0 means 20000 */
+  int max_outer;    /* SEM_MIXED: refinement steps cap; <= 0 means 50 */
+  int prec;         /* SEM_FP64 (plain PCG) or SEM_MIXED (FP32 inner / FP64 outer); SEM_FP32 = plain FP32 PCG */
+} sem_solve_opts;
+
+typedef struct {
+  int iters;       /* CG iterations (summed over inner solves for SEM_MIXED) */
+  int outer_iters; /* refinement steps (SEM_MIXED), else 0 */
+  double rel_res;  /* final ||r|| / ||b|| (FP64 true residual for SEM_MIXED; the CG recurrence residual for SEM_FP64) */
+  double ms;       /* device time of the solve (CUDA events on the internal stream) */
+  int status;      /* sem_status of the solve */
+} sem_solve_result;
+
+/* Solve A x = b, A = mask QQ^T A_L, with Jacobi PCG (Sec. 2).  b_dev: FP64
+ * right-hand side (continuous, zero on Dirichlet nodes, e.g. from sem_rhs).
+ * x_dev: FP64, in: initial guess (masked), out: solution.  Synchronous with
+ * respect to `stream` (it waits for prior work on it and returns when x is
+ * written).  Returns the solve's status (also in result->status). */
+sem_status sem_pcg_solve(const sem_mesh* mesh, const double* b_dev, double* x_dev,
+                         const sem_solve_opts* opts, sem_solve_result* result, void* stream);
+
+/* The same solve from host buffers: copies b in and x out inside the call
+ * (end-to-end use by callers whose data lives in host memory). */
+sem_status sem_pcg_solve_host(const sem_mesh* mesh, const double* b_host, double* x_host,
+                              const sem_solve_opts* opts, sem_solve_result* result, void* stream);
+
+/* ---- serving ------------------------------------------------------------ */
+
+typedef struct {
+  size_t hbm_budget_bytes; /* device bytes the server may hold for requests; 0 = 80% of free memory */
+  int max_slots;           /* requests solved concurrently (each on its own stream); <= 0 means 8 */
+  int max_queue;           /* admitted-but-waiting requests; <= 0 means 4096 */
+  int device;              /* CUDA device ordinal */
+} sem_server_opts;
+
+typedef struct sem_server sem_server;
+
+/* Start a server: worker threads take queued requests as slots and HBM
+ * budget free up; each builds the request's mesh, forms b = mask QQ^T (B f)
+ * and runs sem_pcg_solve on its own stream, so requests overlap on the GPU. */
+sem_status sem_server_create(const sem_server_opts* opts, sem_server** out);
+
+/* Queue a solve.  desc: as for sem_mesh_create (explicit arrays are copied
+ * before return); f_host: nodal forcing [E (N+1)^3] (copied before return);
+ * opts: solve options.  SEM_ERR_OOM if the request alone exceeds the HBM
+ * budget, SEM_ERR_BUSY if the queue is full.  *req_id receives the id. */
+sem_status sem_server_submit(sem_server* srv, const sem_mesh_desc* desc, const double* f_host,
+                             const sem_solve_opts* opts, uint64_t* req_id);
+
+/* Wait up to timeout_ms (< 0: forever) for a request.  On completion copies
+ * the solution into x_host (nullable, [n_local] FP64) and the record into
+ * result (nullable), forgets the request and returns its solve status;
+ * SEM_ERR_TIMEOUT if not done yet (the request stays known). */
+sem_status sem_server_poll(sem_server* srv, uint64_t req_id, int timeout_ms, double* x_host,
+                           sem_solve_result* result);
+
+/* Cancel a queued request (one already running finishes). */
+sem_status sem_server_cancel(sem_server* srv, uint64_t req_id);
+
+typedef struct {
+  uint64_t submitted, completed, rejected, cancelled;
+  int queued, running;
+  size_t hbm_in_use, hbm_budget;
+} sem_server_stats;
+
+sem_status sem_server_stats_get(sem_server* srv, sem_server_stats* out);
+
+/* Stop accepting work, finish running requests, drop queued ones, free all. */
+sem_status sem_server_destroy(sem_server* srv);
+
+/* ---- host-only helpers (no GPU needed) ----------------------------------- */
+
+/* First-touch global numbering from element corner vertex ids alone (the
+ * topological construction sem_mesh_create uses): vert [E][8] as in
+ * sem_mesh_desc; out glo [E (N+1)^3].  *n_global receives the node count. */
+sem_status sem_topology_numbering(int64_t E, int N, const int64_t* vert, int64_t* glo_host,
+                                  int64_t* n_global);
+
+/* Corner vertex ids [E][8] of the built-in box / pipe generators. */
+sem_status sem_mesh_vertices(const sem_mesh_desc* desc, int64_t* vert_host, int64_t* E_out);
+
+/* Which kernel FP64 requests on this mesh use, as chosen by the autotuner at
+ * creation: 1 = double-float (FP32-pair) arithmetic, 0 = native FP64. */
+int sem_mesh_fp64_kernel(const sem_mesh* mesh);
+
+/* Number of CUDA kernels the library has launched in this process (a graph
+ * replay counts each of its kernel nodes).  Monotone; thread-safe. */
+uint64_t sem_kernel_launches(void);
+
+const char* sem_status_str(sem_status s);
+const char* sem_last_error(void);
+int sem_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEM_H */

@@ -1,0 +1,409 @@
+// C ABI: mesh construction and the operator entry points (sem_ax, sem_gs,
+// sem_rhs, sem_apply, sem_jacobi).  The solver lives in solver.cpp and the
+// server in server.cpp.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+
+#include "kernels.h"
+#include "sem_internal.h"
+#include "solver.h"
+
+namespace sem {
+
+static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+sem_status cuda_fail(cudaError_t err, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorName(err) + " (" + cudaGetErrorString(err) + ")");
+  return err == cudaErrorMemoryAllocation ? SEM_ERR_OOM : SEM_ERR_CUDA;
+}
+
+namespace {
+
+template <typename T>
+sem_status dev_alloc(T** p, size_t count, size_t& tally) {
+  *p = nullptr;
+  if (count == 0) return SEM_OK;
+  cudaError_t err = cudaMalloc((void**)p, count * sizeof(T));
+  if (err != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(err, "cudaMalloc");
+  }
+  tally += count * sizeof(T);
+  return SEM_OK;
+}
+
+template <typename T>
+void dev_free(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+void free_mesh_arrays(sem_mesh* m) {
+  dev_free(m->xyz);
+  dev_free(m->G64);
+  dev_free(m->B64);
+  dev_free(m->G32);
+  dev_free(m->G32lo);
+  dev_free(m->B32);
+  dev_free(m->dK);
+  dev_free(m->dB);
+  dev_free(m->wm);
+  dev_free(m->seg_ptr);
+  dev_free(m->seg_idx);
+  dev_free(m->seg_dir);
+  dev_free(m->D64);
+  dev_free(m->D32);
+  dev_free(m->D32lo);
+}
+
+#define SEM_TRY(expr)                   \
+  do {                                  \
+    sem_status _s = (expr);             \
+    if (_s != SEM_OK) return _s;        \
+  } while (0)
+
+sem_status build_mesh(const sem_mesh_desc& d, cudaStream_t s, sem_mesh* m) {
+  std::vector<int64_t> vert;
+  int64_t E = 0;
+  SEM_TRY(generator_vertices(d, vert, E));
+  Topology topo;
+  SEM_TRY(build_numbering(E, d.N, vert.data(), topo));
+  std::vector<uint8_t> dface;
+  generator_dirichlet(d, E, dface);
+  GsPlan plan;
+  SEM_TRY(build_gs_plan(topo, dface.data(), plan));
+  vert.clear();
+  vert.shrink_to_fit();
+
+  const int N = d.N, n = N + 1;
+  const int64_t n3 = (int64_t)n * n * n, P = E * n3;
+  m->N = N;
+  m->n = n;
+  m->E = E;
+  m->n_local = P;
+  m->n_global = topo.n_global;
+  m->n_seg = (int64_t)plan.seg_dir.size();
+  m->n_seg_points = (int64_t)plan.seg_idx.size();
+  SEM_CUDA(cudaGetDevice(&m->device));
+
+  std::vector<double> xi, w, D;
+  gll(N, xi, w, D);
+  std::vector<float> D32(n * n), D32lo(n * n);
+  for (int q = 0; q < n * n; ++q) {
+    D32[q] = (float)D[q];
+    D32lo[q] = (float)(D[q] - (double)D32[q]);
+  }
+
+  size_t& tb = m->dev_bytes;
+  SEM_TRY(dev_alloc(&m->xyz, 3 * P, tb));
+  SEM_TRY(dev_alloc(&m->G64, 6 * P, tb));
+  SEM_TRY(dev_alloc(&m->B64, P, tb));
+  SEM_TRY(dev_alloc(&m->G32, 6 * P, tb));
+  SEM_TRY(dev_alloc(&m->G32lo, 6 * P, tb));
+  SEM_TRY(dev_alloc(&m->B32, P, tb));
+  SEM_TRY(dev_alloc(&m->dK, P, tb));
+  SEM_TRY(dev_alloc(&m->dB, P, tb));
+  SEM_TRY(dev_alloc(&m->wm, P, tb));
+  SEM_TRY(dev_alloc(&m->seg_ptr, plan.seg_ptr.size(), tb));
+  SEM_TRY(dev_alloc(&m->seg_idx, plan.seg_idx.size(), tb));
+  SEM_TRY(dev_alloc(&m->seg_dir, plan.seg_dir.size(), tb));
+  SEM_TRY(dev_alloc(&m->D64, n * n, tb));
+  SEM_TRY(dev_alloc(&m->D32, n * n, tb));
+  SEM_TRY(dev_alloc(&m->D32lo, n * n, tb));
+
+  size_t tmp_bytes = 0;
+  double *xi_d = nullptr, *w_d = nullptr, *tlev_d = nullptr;
+  int* bad_d = nullptr;
+  struct Tmp {
+    double** a;
+    double** b;
+    double** c;
+    int** f;
+    ~Tmp() {
+      if (*a) cudaFree(*a);
+      if (*b) cudaFree(*b);
+      if (*c) cudaFree(*c);
+      if (*f) cudaFree(*f);
+    }
+  } tmp{&xi_d, &w_d, &tlev_d, &bad_d};
+  SEM_TRY(dev_alloc(&xi_d, n, tmp_bytes));
+  SEM_TRY(dev_alloc(&w_d, n, tmp_bytes));
+  SEM_TRY(dev_alloc(&bad_d, 1, tmp_bytes));
+
+  SEM_CUDA(cudaMemcpyAsync(xi_d, xi.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+  SEM_CUDA(cudaMemcpyAsync(w_d, w.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+  SEM_CUDA(cudaMemcpyAsync(m->D64, D.data(), n * n * sizeof(double), cudaMemcpyHostToDevice, s));
+  SEM_CUDA(cudaMemcpyAsync(m->D32, D32.data(), n * n * sizeof(float), cudaMemcpyHostToDevice, s));
+  SEM_CUDA(cudaMemcpyAsync(m->D32lo, D32lo.data(), n * n * sizeof(float), cudaMemcpyHostToDevice, s));
+  SEM_CUDA(cudaMemsetAsync(bad_d, 0, sizeof(int), s));
+  SEM_CUDA(cudaMemcpyAsync(m->wm, plan.wm.data(), P, cudaMemcpyHostToDevice, s));
+  SEM_CUDA(cudaMemcpyAsync(m->seg_ptr, plan.seg_ptr.data(), plan.seg_ptr.size() * 4, cudaMemcpyHostToDevice, s));
+  if (!plan.seg_idx.empty())
+    SEM_CUDA(cudaMemcpyAsync(m->seg_idx, plan.seg_idx.data(), plan.seg_idx.size() * 4, cudaMemcpyHostToDevice, s));
+  if (!plan.seg_dir.empty())
+    SEM_CUDA(cudaMemcpyAsync(m->seg_dir, plan.seg_dir.data(), plan.seg_dir.size(), cudaMemcpyHostToDevice, s));
+
+  std::vector<double> tlev;
+  if (d.kind == SEM_MESH_BOX) {
+    launch_coords_box(m->xyz, xi_d, n, E, d.nx, d.ny, d.nz, d.lx, d.ly, d.lz, s);
+  } else if (d.kind == SEM_MESH_PIPE) {
+    tlev.resize(d.nr + 1);
+    for (int k = 0; k <= d.nr; ++k) tlev[k] = 1.0 - std::tanh(d.beta * (1.0 - (double)k / d.nr)) / std::tanh(d.beta);
+    SEM_TRY(dev_alloc(&tlev_d, d.nr + 1, tmp_bytes));
+    SEM_CUDA(cudaMemcpyAsync(tlev_d, tlev.data(), tlev.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_coords_pipe(m->xyz, xi_d, tlev_d, n, E, d.nc, d.nr, d.nzp, d.R, d.L, d.a, s);
+  } else {
+    SEM_CUDA(cudaMemcpyAsync(m->xyz, d.xyz, 3 * P * sizeof(double), cudaMemcpyHostToDevice, s));
+  }
+  SEM_CUDA(cudaGetLastError());
+  SEM_CUDA(launch_geometry(m->xyz, m->G64, m->B64, m->D64, w_d, n, E, bad_d, s));
+  // assembled diagonals for the Jacobi preconditioner: dK = QQ^T diag(stiffness), dB = QQ^T B
+  launch_local_diag(m->G64, m->dK, m->D64, n, E, s);
+  SEM_CUDA(launch_gs<double>(m->dK, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, 0, nullptr, s));
+  SEM_CUDA(cudaMemcpyAsync(m->dB, m->B64, P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  SEM_CUDA(launch_gs<double>(m->dB, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, 0, nullptr, s));
+  launch_split_f64(m->G64, m->G32, m->G32lo, 6 * P, s);
+  launch_split_f64(m->B64, m->B32, nullptr, P, s);
+  SEM_CUDA(cudaGetLastError());
+  count_launches(7);
+  int bad = 0;
+  SEM_CUDA(cudaMemcpyAsync(&bad, bad_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA(cudaStreamSynchronize(s));
+  if (bad) {
+    set_error("mesh has an element with det(J) <= 0");
+    return SEM_ERR_BAD_MESH;
+  }
+  m->glo = std::move(topo.glo);
+  return SEM_OK;
+}
+
+}  // namespace
+}  // namespace sem
+
+using namespace sem;
+
+extern "C" {
+
+const char* sem_last_error(void) { return g_last_error.c_str(); }
+
+int sem_version(void) { return 1; }
+
+int sem_mesh_fp64_kernel(const sem_mesh* m) { return m ? m->fp64_df : -1; }
+
+uint64_t sem_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* sem_status_str(sem_status s) {
+  switch (s) {
+    case SEM_OK: return "SEM_OK";
+    case SEM_ERR_INVALID: return "SEM_ERR_INVALID";
+    case SEM_ERR_OOM: return "SEM_ERR_OOM";
+    case SEM_ERR_CUDA: return "SEM_ERR_CUDA";
+    case SEM_ERR_NOT_CONVERGED: return "SEM_ERR_NOT_CONVERGED";
+    case SEM_ERR_BREAKDOWN: return "SEM_ERR_BREAKDOWN";
+    case SEM_ERR_BUSY: return "SEM_ERR_BUSY";
+    case SEM_ERR_DEVICE_TIMEOUT: return "SEM_ERR_DEVICE_TIMEOUT";
+    case SEM_ERR_BAD_MESH: return "SEM_ERR_BAD_MESH";
+    case SEM_ERR_TIMEOUT: return "SEM_ERR_TIMEOUT";
+    case SEM_ERR_NOT_FOUND: return "SEM_ERR_NOT_FOUND";
+    case SEM_ERR_CANCELLED: return "SEM_ERR_CANCELLED";
+  }
+  return "SEM_ERR_UNKNOWN";
+}
+
+sem_status sem_mesh_create(const sem_mesh_desc* desc, void* stream, sem_mesh** out) {
+  if (!desc || !out) {
+    set_error("sem_mesh_create: null argument");
+    return SEM_ERR_INVALID;
+  }
+  *out = nullptr;
+  sem_mesh* m = new (std::nothrow) sem_mesh();
+  if (!m) return SEM_ERR_OOM;
+  sem_status st = build_mesh(*desc, (cudaStream_t)stream, m);
+  if (st != SEM_OK) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    free_mesh_arrays(m);
+    delete m;
+    return st;
+  }
+  st = autotune_mesh(m, (cudaStream_t)stream);
+  if (st != SEM_OK) {
+    free_mesh_arrays(m);
+    delete m;
+    return st;
+  }
+  *out = m;
+  return SEM_OK;
+}
+
+sem_status sem_mesh_destroy(sem_mesh* m) {
+  if (!m) return SEM_OK;
+  cudaDeviceSynchronize();
+  release_workspace(m);
+  free_mesh_arrays(m);
+  delete m;
+  return SEM_OK;
+}
+
+sem_status sem_mesh_info(const sem_mesh* m, sem_mesh_info_t* info) {
+  if (!m || !info) {
+    set_error("sem_mesh_info: null argument");
+    return SEM_ERR_INVALID;
+  }
+  info->E = m->E;
+  info->N = m->N;
+  info->n_local = m->n_local;
+  info->n_global = m->n_global;
+  info->n_segments = m->n_seg;
+  info->n_seg_points = m->n_seg_points;
+  info->dev_bytes = m->dev_bytes;
+  return SEM_OK;
+}
+
+sem_status sem_mesh_global_ids(const sem_mesh* m, int64_t* host_out) {
+  if (!m || !host_out) {
+    set_error("sem_mesh_global_ids: null argument");
+    return SEM_ERR_INVALID;
+  }
+  std::memcpy(host_out, m->glo.data(), m->glo.size() * sizeof(int64_t));
+  return SEM_OK;
+}
+
+sem_status sem_mesh_coords(const sem_mesh* m, double* xyz_dev, void* stream) {
+  if (!m || !xyz_dev) {
+    set_error("sem_mesh_coords: null argument");
+    return SEM_ERR_INVALID;
+  }
+  SEM_CUDA(cudaMemcpyAsync(xyz_dev, m->xyz, 3 * m->n_local * sizeof(double), cudaMemcpyDeviceToDevice,
+                           (cudaStream_t)stream));
+  return SEM_OK;
+}
+
+sem_status sem_mesh_geometry(const sem_mesh* m, double* G_dev, double* B_dev, void* stream) {
+  if (!m) {
+    set_error("sem_mesh_geometry: null mesh");
+    return SEM_ERR_INVALID;
+  }
+  if (G_dev)
+    SEM_CUDA(cudaMemcpyAsync(G_dev, m->G64, 6 * m->n_local * sizeof(double), cudaMemcpyDeviceToDevice,
+                             (cudaStream_t)stream));
+  if (B_dev)
+    SEM_CUDA(cudaMemcpyAsync(B_dev, m->B64, m->n_local * sizeof(double), cudaMemcpyDeviceToDevice,
+                             (cudaStream_t)stream));
+  return SEM_OK;
+}
+
+sem_status sem_mesh_weights(const sem_mesh* m, double* mult_dev, double* mask_dev, void* stream) {
+  if (!m) {
+    set_error("sem_mesh_weights: null mesh");
+    return SEM_ERR_INVALID;
+  }
+  launch_weights(m->wm, mult_dev, mask_dev, m->n_local, (cudaStream_t)stream);
+  SEM_CUDA(cudaGetLastError());
+  count_launches(1);
+  return SEM_OK;
+}
+
+sem_status sem_ax(const sem_mesh* m, const void* u_dev, void* w_dev, double h1, double h2, sem_prec prec,
+                  void* stream) {
+  if (!m || !u_dev || !w_dev) {
+    set_error("sem_ax: null argument");
+    return SEM_ERR_INVALID;
+  }
+  if (u_dev == w_dev) {
+    set_error("sem_ax: u and w must not overlap");
+    return SEM_ERR_INVALID;
+  }
+  return apply_local(m, u_dev, w_dev, h1, h2, prec, (cudaStream_t)stream);
+}
+
+sem_status sem_gs(const sem_mesh* m, void* v_dev, sem_prec prec, int apply_mask, void* stream) {
+  if (!m || !v_dev) {
+    set_error("sem_gs: null argument");
+    return SEM_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == SEM_FP64) {
+    SEM_CUDA(launch_gs<double>((double*)v_dev, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, apply_mask, nullptr, s));
+  } else if (prec == SEM_FP32) {
+    SEM_CUDA(launch_gs<float>((float*)v_dev, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, apply_mask, nullptr, s));
+  } else {
+    set_error("sem_gs: prec must be SEM_FP64 or SEM_FP32");
+    return SEM_ERR_INVALID;
+  }
+  count_launches(1);
+  return SEM_OK;
+}
+
+sem_status sem_rhs(const sem_mesh* m, const double* f_dev, double* b_dev, void* stream) {
+  if (!m || !f_dev || !b_dev) {
+    set_error("sem_rhs: null argument");
+    return SEM_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_mul(b_dev, m->B64, f_dev, m->n_local, s);
+  SEM_CUDA(cudaGetLastError());
+  SEM_CUDA(launch_gs<double>(b_dev, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, 1, nullptr, s));
+  count_launches(2);
+  return SEM_OK;
+}
+
+sem_status sem_apply(const sem_mesh* m, const double* x_dev, double* y_dev, double h1, double h2, void* stream) {
+  if (!m || !x_dev || !y_dev || x_dev == y_dev) {
+    set_error("sem_apply: null or overlapping argument");
+    return SEM_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  sem_status st = apply_local(m, x_dev, y_dev, h1, h2, SEM_FP64, s);
+  if (st != SEM_OK) return st;
+  SEM_CUDA(launch_gs<double>(y_dev, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, 1, nullptr, s));
+  count_launches(1);
+  return SEM_OK;
+}
+
+sem_status sem_jacobi(const sem_mesh* m, double h1, double h2, double* minv_dev, void* stream) {
+  if (!m || !minv_dev) {
+    set_error("sem_jacobi: null argument");
+    return SEM_ERR_INVALID;
+  }
+  launch_minv(minv_dev, nullptr, m->dK, m->dB, m->wm, h1, h2, m->n_local, (cudaStream_t)stream);
+  SEM_CUDA(cudaGetLastError());
+  count_launches(1);
+  return SEM_OK;
+}
+
+sem_status sem_topology_numbering(int64_t E, int N, const int64_t* vert, int64_t* glo_host, int64_t* n_global) {
+  if (!vert || !glo_host) {
+    set_error("sem_topology_numbering: null argument");
+    return SEM_ERR_INVALID;
+  }
+  Topology t;
+  sem_status st = build_numbering(E, N, vert, t);
+  if (st != SEM_OK) return st;
+  std::memcpy(glo_host, t.glo.data(), t.glo.size() * sizeof(int64_t));
+  if (n_global) *n_global = t.n_global;
+  return SEM_OK;
+}
+
+sem_status sem_mesh_vertices(const sem_mesh_desc* desc, int64_t* vert_host, int64_t* E_out) {
+  if (!desc) {
+    set_error("sem_mesh_vertices: null descriptor");
+    return SEM_ERR_INVALID;
+  }
+  std::vector<int64_t> vert;
+  int64_t E = 0;
+  sem_status st = generator_vertices(*desc, vert, E);
+  if (st != SEM_OK) return st;
+  if (E_out) *E_out = E;
+  if (vert_host) std::memcpy(vert_host, vert.data(), vert.size() * sizeof(int64_t));
+  return SEM_OK;
+}
+
+}  // extern "C"

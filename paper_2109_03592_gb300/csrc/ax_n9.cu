@@ -1,0 +1,18 @@
+// Local-operator kernels instantiated for polynomial orders 9.
+// (One translation unit per order keeps the parallel build short.)
+#include "ax_df_impl.cuh"
+#include "ax_impl.cuh"
+
+namespace sem {
+
+cudaError_t ax64_n9(int v, bool f, const AxParams<double>& p, cudaStream_t s, int* g) {
+  return dispatch_ax_n<double, 9>(v, f, p, s, g);
+}
+cudaError_t ax32_n9(int v, bool f, const AxParams<float>& p, cudaStream_t s, int* g) {
+  return dispatch_ax_n<float, 9>(v, f, p, s, g);
+}
+cudaError_t axdf_n9(int v, bool f, const AxDFParams& p, cudaStream_t s, int* g) {
+  return df_detail::dispatch_df_n<9>(v, f, p, s, g);
+}
+
+}  // namespace sem

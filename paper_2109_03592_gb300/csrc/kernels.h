@@ -1,0 +1,111 @@
+// Kernel launchers and their parameter blocks.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "device_util.cuh"
+
+namespace sem {
+
+// Host-side tally of kernel launches issued by the library (sem_kernel_launches).
+void count_launches(uint64_t n);
+
+// ---- mesh set-up (geom.cu) ----
+void launch_coords_box(double* xyz, const double* xi, int n, int64_t E, int nx, int ny, int nz, double lx,
+                       double ly, double lz, cudaStream_t s);
+void launch_coords_pipe(double* xyz, const double* xi, const double* tlev, int n, int64_t E, int nc, int nr,
+                        int nzp, double R, double L, double a, cudaStream_t s);
+cudaError_t launch_geometry(const double* xyz, double* G, double* B, const double* D, const double* w, int n,
+                            int64_t E, int* bad, cudaStream_t s);
+void launch_local_diag(const double* G, double* dK, const double* D, int n, int64_t E, cudaStream_t s);
+void launch_split_f64(const double* v, float* hi, float* lo, int64_t m, cudaStream_t s);
+void launch_weights(const uint8_t* wm, double* mult, double* mask, int64_t m, cudaStream_t s);
+
+// ---- local operator (ax_*.cu) ----
+template <typename T>
+struct AxParams {
+  const T* u;        // input (plain variant)
+  T* w;              // output A_L u
+  const T* G;        // [E][6][n3]
+  const T* B;        // [E][n3] (Helmholtz term)
+  const T* D;        // [n*n]
+  T h1, h2;
+  int helm;          // h2 != 0
+  int64_t E;
+  // fused-PCG variant: p <- z + beta p, u := p, partial <p, A_L p>
+  const T* z;
+  T* p;
+  PcgState* st;
+  double* partial;   // [gridDim.x]
+};
+
+// Double-float (FP32 pair) FP64-accurate variant: G = Ghi + Glo, D = Dhi + Dlo,
+// u and w FP64 in memory.
+struct AxDFParams {
+  const double* u;
+  double* w;
+  const float* Ghi;
+  const float* Glo;
+  const double* B;
+  const float* Dhi;
+  const float* Dlo;
+  double h1, h2;
+  int helm;
+  int64_t E;
+  const double* z;
+  double* p;
+  PcgState* st;
+  double* partial;
+};
+
+// Kernel variants of the local operator for one (N, precision); `variant`
+// indexes an elements-per-block choice (see ax_variants()).
+int ax_num_variants();
+int ax_elems_per_block(int N, int variant);
+cudaError_t launch_ax_f64(int N, int variant, bool fused, const AxParams<double>& p, cudaStream_t s, int* grid_out);
+cudaError_t launch_ax_f32(int N, int variant, bool fused, const AxParams<float>& p, cudaStream_t s, int* grid_out);
+cudaError_t launch_ax_df(int N, int variant, bool fused, const AxDFParams& p, cudaStream_t s, int* grid_out);
+int ax_df_available(int N);
+
+// ---- gather-scatter (gs.cu) ----
+template <typename T>
+cudaError_t launch_gs(T* v, const int32_t* seg_ptr, const int32_t* seg_idx, const uint8_t* seg_dir, int64_t nseg,
+                      int apply_mask, const PcgState* st, cudaStream_t s);
+
+// ---- PCG vector kernels (pcg.cu) ----
+template <typename T>
+struct VecParams {
+  T* x;
+  T* r;
+  T* z;
+  T* p;
+  const T* w;
+  const T* minv;
+  const T* b;
+  const uint8_t* wm;
+  int64_t n;
+  PcgState* st;
+  double* partial;  // [3 * grid]
+};
+int vec_grid();
+template <typename T>
+cudaError_t launch_pcg_update(const VecParams<T>& p, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pcg_init(const VecParams<T>& p, cudaStream_t s);
+
+void launch_mul(double* out, const double* a, const double* b, int64_t n, cudaStream_t s);
+void launch_mask(double* x, const uint8_t* wm, int64_t n, cudaStream_t s);
+void launch_minv(double* minv, float* minv32, const double* dK, const double* dB, const uint8_t* wm, double h1,
+                 double h2, int64_t n, cudaStream_t s);
+// r = b - w, st->aux = <r, r>_W, st->bb = <b, b>_W (when set_bb)
+cudaError_t launch_residual(double* r, const double* b, const double* w, const uint8_t* wm, int64_t n, PcgState* st,
+                            double* partial, int set_bb, cudaStream_t s);
+// r32 = float(sc * r)
+void launch_scale_to_f32(float* r32, const double* r, double sc, int64_t n, cudaStream_t s);
+// x += sc * double(d32)
+void launch_accumulate(double* x, const float* d32, double sc, int64_t n, cudaStream_t s);
+void launch_zero_f32(float* a, int64_t n, cudaStream_t s);
+
+}  // namespace sem

@@ -1,0 +1,488 @@
+// Jacobi-preconditioned CG on the device (Sec. 2: "iterative solvers with
+// proper preconditioners"; Sec. 3: reductions by hand-written kernels and
+// data kept resident on the GPU).
+//
+// One CG iteration is three kernels:
+//   ax  : p <- z + beta p (prologue), w = A_L p, <p, A_L p> -> alpha
+//   gs  : w <- mask QQ^T w
+//   upd : x += alpha p, r -= alpha w, z = M^{-1} r, <r,z>, <r,r> -> beta, stop test
+// All scalars live in a device PcgState, so K iterations are captured once
+// into a CUDA graph and replayed; the host reads the state once per chunk
+// (double-buffered, so the GPU always has the next chunk queued) and stops
+// when the device flags convergence, breakdown or maxit.
+//
+// Mixed precision (FP64 outer refinement around an FP32 inner PCG): the
+// residual r = b - A x is formed in FP64 (FP64 factors), normalised and
+// rounded to FP32, solved by the FP32 PCG (FP32 factors, fields and
+// M^{-1}; inner products of FP32 products summed in compensated FP32 per
+// thread and FP64 across threads), and the FP32 correction is added to x in
+// FP64; repeated until the FP64 residual meets the tolerance.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
+
+#include "kernels.h"
+#include "sem_internal.h"
+#include "solver.h"
+
+namespace sem {
+
+constexpr int kChunk = 8;  // CG iterations per graph launch
+
+struct GraphSlot {
+  cudaGraphExec_t exec = nullptr;
+  double h1 = NAN, h2 = NAN;
+  int var = -1, df = -1;
+};
+
+struct Workspace {
+  int64_t n = 0;
+  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr, *minv = nullptr, *b = nullptr;
+  float *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *w32 = nullptr, *minv32 = nullptr;
+  PcgState* st = nullptr;
+  PcgState* sth = nullptr;  // pinned host [2]
+  double* part_ax = nullptr;
+  double* part_vec = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, eu = nullptr, ev[2] = {nullptr, nullptr};
+  double minv_h1 = NAN, minv_h2 = NAN;
+  GraphSlot g64, g32;
+};
+
+static void destroy_ws(Workspace* ws) {
+  if (!ws) return;
+  if (ws->s) cudaStreamSynchronize(ws->s);
+  for (GraphSlot* g : {&ws->g64, &ws->g32})
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+  for (void* p : {(void*)ws->x, (void*)ws->r, (void*)ws->z, (void*)ws->p, (void*)ws->w, (void*)ws->minv,
+                  (void*)ws->b, (void*)ws->x32, (void*)ws->r32, (void*)ws->z32, (void*)ws->p32, (void*)ws->w32,
+                  (void*)ws->minv32, (void*)ws->st, (void*)ws->part_ax, (void*)ws->part_vec})
+    if (p) cudaFree(p);
+  if (ws->sth) cudaFreeHost(ws->sth);
+  for (cudaEvent_t e : {ws->e0, ws->e1, ws->eu, ws->ev[0], ws->ev[1]})
+    if (e) cudaEventDestroy(e);
+  if (ws->s) cudaStreamDestroy(ws->s);
+  delete ws;
+}
+
+void release_workspace(sem_mesh* m) {
+  std::lock_guard<std::mutex> lk(m->ws_mutex);
+  destroy_ws(m->ws);
+  m->ws = nullptr;
+}
+
+static int max_ax_grid(const sem_mesh* m) {
+  int epb = 1 << 30;
+  for (int v = 0; v < ax_num_variants(); ++v) epb = std::min(epb, ax_elems_per_block(m->N, v));
+  return (int)((m->E + epb - 1) / epb);
+}
+
+static sem_status alloc_ws(sem_mesh* m, Workspace** out) {
+  Workspace* ws = new Workspace();
+  ws->n = m->n_local;
+  const size_t n = (size_t)m->n_local;
+  auto fail = [&](cudaError_t e, const char* what) {
+    sem_status st = cuda_fail(e, what);
+    destroy_ws(ws);
+    return st;
+  };
+  cudaError_t e = cudaSuccess;
+  for (double** p : {&ws->x, &ws->r, &ws->z, &ws->p, &ws->w, &ws->minv, &ws->b})
+    if ((e = cudaMalloc((void**)p, n * sizeof(double))) != cudaSuccess) return fail(e, "cudaMalloc workspace");
+  for (float** p : {&ws->x32, &ws->r32, &ws->z32, &ws->p32, &ws->w32, &ws->minv32})
+    if ((e = cudaMalloc((void**)p, n * sizeof(float))) != cudaSuccess) return fail(e, "cudaMalloc workspace");
+  if ((e = cudaMalloc((void**)&ws->st, sizeof(PcgState))) != cudaSuccess) return fail(e, "cudaMalloc state");
+  if ((e = cudaMalloc((void**)&ws->part_ax, (size_t)max_ax_grid(m) * sizeof(double))) != cudaSuccess)
+    return fail(e, "cudaMalloc partials");
+  if ((e = cudaMalloc((void**)&ws->part_vec, 3 * (size_t)vec_grid() * sizeof(double))) != cudaSuccess)
+    return fail(e, "cudaMalloc partials");
+  if ((e = cudaMallocHost((void**)&ws->sth, 2 * sizeof(PcgState))) != cudaSuccess) return fail(e, "cudaMallocHost");
+  if ((e = cudaStreamCreateWithFlags(&ws->s, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "stream");
+  for (cudaEvent_t* ev : {&ws->e0, &ws->e1})
+    if ((e = cudaEventCreate(ev)) != cudaSuccess) return fail(e, "event");
+  for (cudaEvent_t* ev : {&ws->eu, &ws->ev[0], &ws->ev[1]})
+    if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
+  *out = ws;
+  return SEM_OK;
+}
+
+// ---- local operator dispatch ---------------------------------------------------
+
+static cudaError_t ax64(const sem_mesh* m, const double* u, double* w, double h1, double h2, bool fused,
+                        const double* z, double* p, PcgState* st, double* part, cudaStream_t s) {
+  if (m->fp64_df) {
+    AxDFParams a{u, w, m->G32, m->G32lo, m->B64, m->D32, m->D32lo, h1, h2, h2 != 0.0, m->E, z, p, st, part};
+    return launch_ax_df(m->N, m->ax_var[2], fused, a, s, nullptr);
+  }
+  AxParams<double> a{u, w, m->G64, m->B64, m->D64, h1, h2, h2 != 0.0, m->E, z, p, st, part};
+  return launch_ax_f64(m->N, m->ax_var[0], fused, a, s, nullptr);
+}
+
+static cudaError_t ax32(const sem_mesh* m, const float* u, float* w, double h1, double h2, bool fused,
+                        const float* z, float* p, PcgState* st, double* part, cudaStream_t s) {
+  AxParams<float> a{u, w, m->G32, m->B32, m->D32, (float)h1, (float)h2, h2 != 0.0, m->E, z, p, st, part};
+  return launch_ax_f32(m->N, m->ax_var[1], fused, a, s, nullptr);
+}
+
+sem_status apply_local(const sem_mesh* m, const void* u, void* w, double h1, double h2, sem_prec prec,
+                       cudaStream_t s) {
+  count_launches(1);
+  if (prec == SEM_FP64) {
+    SEM_CUDA(ax64(m, (const double*)u, (double*)w, h1, h2, false, nullptr, nullptr, nullptr, nullptr, s));
+  } else if (prec == SEM_FP32) {
+    SEM_CUDA(ax32(m, (const float*)u, (float*)w, h1, h2, false, nullptr, nullptr, nullptr, nullptr, s));
+  } else {
+    set_error("sem_ax: prec must be SEM_FP64 or SEM_FP32");
+    return SEM_ERR_INVALID;
+  }
+  return SEM_OK;
+}
+
+// ---- autotuner -------------------------------------------------------------------
+
+// Times every elements-per-block variant of the FP64, FP32 and double-float
+// local operator on this mesh (the mesh's own factors as input) and keeps
+// the fastest; FP64 requests use the double-float kernel when it is faster.
+// SEM_FP64_KERNEL=native|df forces the FP64 choice.
+sem_status autotune_mesh(sem_mesh* m, cudaStream_t s) {
+  const size_t n = (size_t)m->n_local;
+  double* w = nullptr;
+  SEM_CUDA(cudaMalloc((void**)&w, n * sizeof(double)));
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best[3] = {1e30f, 1e30f, 1e30f};
+  sem_status status = SEM_OK;
+  const int reps = m->E >= 65536 ? 2 : 3;
+  for (int kind = 0; kind < 3 && status == SEM_OK; ++kind) {
+    if (kind == 2 && !ax_df_available(m->N)) continue;
+    for (int v = 0; v < ax_num_variants(); ++v) {
+      cudaError_t err = cudaSuccess;
+      float total = 0.f;
+      for (int rep = 0; rep <= reps && err == cudaSuccess; ++rep) {
+        cudaEventRecord(a, s);
+        if (kind == 0) {
+          AxParams<double> pa{m->B64, w, m->G64, m->B64, m->D64, 1.0, 0.0, 0, m->E, nullptr, nullptr, nullptr, nullptr};
+          err = launch_ax_f64(m->N, v, false, pa, s, nullptr);
+        } else if (kind == 1) {
+          AxParams<float> pa{m->B32, (float*)w, m->G32, m->B32, m->D32, 1.f, 0.f, 0, m->E,
+                             nullptr, nullptr, nullptr, nullptr};
+          err = launch_ax_f32(m->N, v, false, pa, s, nullptr);
+        } else {
+          AxDFParams pa{m->B64, w, m->G32, m->G32lo, m->B64, m->D32, m->D32lo, 1.0, 0.0, 0, m->E,
+                        nullptr, nullptr, nullptr, nullptr};
+          err = launch_ax_df(m->N, v, false, pa, s, nullptr);
+        }
+        cudaEventRecord(b, s);
+        count_launches(1);
+        if (err == cudaSuccess) err = cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0) total += ms;  // first run is a warm-up
+      }
+      if (err != cudaSuccess) {
+        status = cuda_fail(err, "autotune");
+        break;
+      }
+      m->ax_ms[kind][v] = total / reps;
+      if (total / reps < best[kind]) {
+        best[kind] = total / reps;
+        m->ax_var[kind] = v;
+      }
+    }
+  }
+  m->fp64_df = ax_df_available(m->N) && best[2] < best[0];
+  if (const char* f = std::getenv("SEM_FP64_KERNEL")) {
+    if (!std::strcmp(f, "native")) m->fp64_df = 0;
+    if (!std::strcmp(f, "df") && ax_df_available(m->N)) m->fp64_df = 1;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(w);
+  return status;
+}
+
+// ---- CG chunks ---------------------------------------------------------------------
+
+static sem_status iter64(sem_mesh* m, Workspace* ws, double h1, double h2) {
+  SEM_CUDA(ax64(m, nullptr, ws->w, h1, h2, true, ws->z, ws->p, ws->st, ws->part_ax, ws->s));
+  SEM_CUDA(launch_gs<double>(ws->w, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, 1, ws->st, ws->s));
+  VecParams<double> v{ws->x, ws->r, ws->z, ws->p, ws->w, ws->minv, ws->b, m->wm, ws->n, ws->st, ws->part_vec};
+  SEM_CUDA(launch_pcg_update<double>(v, ws->s));
+  return SEM_OK;
+}
+
+static sem_status iter32(sem_mesh* m, Workspace* ws, double h1, double h2) {
+  SEM_CUDA(ax32(m, nullptr, ws->w32, h1, h2, true, ws->z32, ws->p32, ws->st, ws->part_ax, ws->s));
+  SEM_CUDA(launch_gs<float>(ws->w32, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, 1, ws->st, ws->s));
+  VecParams<float> v{ws->x32, ws->r32, ws->z32, ws->p32, ws->w32, ws->minv32, ws->r32, m->wm, ws->n, ws->st,
+                     ws->part_vec};
+  SEM_CUDA(launch_pcg_update<float>(v, ws->s));
+  return SEM_OK;
+}
+
+static sem_status put_state(Workspace* ws, double tol, int maxit, int done) {
+  PcgState h;
+  std::memset(&h, 0, sizeof(h));
+  h.tol2 = tol * tol;
+  h.maxit = maxit;
+  h.done = done;
+  ws->sth[0] = h;
+  SEM_CUDA(cudaMemcpyAsync(ws->st, &ws->sth[0], sizeof(PcgState), cudaMemcpyHostToDevice, ws->s));
+  SEM_CUDA(cudaStreamSynchronize(ws->s));  // the pinned staging slot is reused below
+  return SEM_OK;
+}
+
+static sem_status read_state(Workspace* ws, PcgState& out) {
+  SEM_CUDA(cudaMemcpyAsync(&ws->sth[0], ws->st, sizeof(PcgState), cudaMemcpyDeviceToHost, ws->s));
+  SEM_CUDA(cudaStreamSynchronize(ws->s));
+  out = ws->sth[0];
+  return SEM_OK;
+}
+
+// Capture kChunk iterations into a graph (once per operator/kernel choice).
+static sem_status get_graph(sem_mesh* m, Workspace* ws, bool fp32, double h1, double h2) {
+  GraphSlot& g = fp32 ? ws->g32 : ws->g64;
+  const int var = fp32 ? m->ax_var[1] : (m->fp64_df ? m->ax_var[2] : m->ax_var[0]);
+  const int df = fp32 ? 0 : m->fp64_df;
+  if (g.exec && g.h1 == h1 && g.h2 == h2 && g.var == var && g.df == df) return SEM_OK;
+  if (g.exec) {
+    cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+  }
+  // One eager pass with done = 1 (every kernel returns at once) so that
+  // per-kernel attributes are set outside the capture.
+  sem_status st = put_state(ws, 0.0, 0, 1);
+  if (st != SEM_OK) return st;
+  st = fp32 ? iter32(m, ws, h1, h2) : iter64(m, ws, h1, h2);
+  if (st != SEM_OK) return st;
+  count_launches(3);
+  SEM_CUDA(cudaStreamSynchronize(ws->s));
+  cudaGraph_t graph = nullptr;
+  SEM_CUDA(cudaStreamBeginCapture(ws->s, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < kChunk && st == SEM_OK; ++k) st = fp32 ? iter32(m, ws, h1, h2) : iter64(m, ws, h1, h2);
+  cudaError_t e = cudaStreamEndCapture(ws->s, &graph);
+  if (st != SEM_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  g.h1 = h1;
+  g.h2 = h2;
+  g.var = var;
+  g.df = df;
+  return SEM_OK;
+}
+
+// Replay the chunk graph until the device reports done.
+static sem_status run_chunks(Workspace* ws, cudaGraphExec_t g, int maxit, PcgState& out) {
+  const int max_chunks = maxit / kChunk + 3;
+  for (int c = 0; c < max_chunks; ++c) {
+    SEM_CUDA(cudaGraphLaunch(g, ws->s));
+    count_launches(3 * kChunk);
+    SEM_CUDA(cudaMemcpyAsync(&ws->sth[c & 1], ws->st, sizeof(PcgState), cudaMemcpyDeviceToHost, ws->s));
+    SEM_CUDA(cudaEventRecord(ws->ev[c & 1], ws->s));
+    if (c > 0) {
+      SEM_CUDA(cudaEventSynchronize(ws->ev[(c - 1) & 1]));
+      if (ws->sth[(c - 1) & 1].done) {
+        SEM_CUDA(cudaEventSynchronize(ws->ev[c & 1]));
+        out = ws->sth[c & 1];
+        return SEM_OK;
+      }
+    }
+  }
+  SEM_CUDA(cudaStreamSynchronize(ws->s));
+  out = ws->sth[(max_chunks - 1) & 1];
+  if (!out.done) {
+    set_error("CG did not report completion within maxit iterations");
+    return SEM_ERR_DEVICE_TIMEOUT;
+  }
+  return SEM_OK;
+}
+
+struct SolveOut {
+  int iters = 0, outer = 0, status = SEM_OK;
+  double rel = 0.0;
+};
+
+// Plain FP64 PCG on ws->b with initial guess ws->x.
+static sem_status pcg64(sem_mesh* m, Workspace* ws, const sem_solve_opts& o, int maxit, SolveOut& res) {
+  sem_status st = get_graph(m, ws, false, o.h1, o.h2);
+  if (st != SEM_OK) return st;
+  st = put_state(ws, o.tol, maxit, 0);
+  if (st != SEM_OK) return st;
+  SEM_CUDA(ax64(m, ws->x, ws->w, o.h1, o.h2, false, nullptr, nullptr, nullptr, nullptr, ws->s));
+  SEM_CUDA(launch_gs<double>(ws->w, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, 1, nullptr, ws->s));
+  SEM_CUDA(launch_residual(ws->r, ws->b, ws->w, m->wm, ws->n, ws->st, ws->part_vec, 1, ws->s));
+  VecParams<double> v{ws->x, ws->r, ws->z, ws->p, ws->w, ws->minv, ws->b, m->wm, ws->n, ws->st, ws->part_vec};
+  SEM_CUDA(launch_pcg_init<double>(v, ws->s));
+  count_launches(4);
+  PcgState s0;
+  st = read_state(ws, s0);
+  if (st != SEM_OK) return st;
+  if (s0.bb == 0.0) {
+    SEM_CUDA(cudaMemsetAsync(ws->x, 0, ws->n * sizeof(double), ws->s));
+    res.rel = 0.0;
+    return SEM_OK;
+  }
+  PcgState fin = s0;
+  if (!s0.done) {
+    st = run_chunks(ws, ws->g64.exec, maxit, fin);
+    if (st != SEM_OK) return st;
+  }
+  res.iters = fin.iter;
+  res.rel = std::sqrt(fin.rr / fin.bb);
+  res.status = fin.status;
+  return SEM_OK;
+}
+
+// FP64 refinement around FP32 inner PCG (max_outer = 1 and inner_tol = tol
+// gives a plain FP32 PCG).
+static sem_status pcg_mixed(sem_mesh* m, Workspace* ws, const sem_solve_opts& o, int maxit, double inner_tol,
+                            int max_outer, SolveOut& res) {
+  sem_status st = get_graph(m, ws, true, o.h1, o.h2);
+  if (st != SEM_OK) return st;
+  for (int outer = 0;; ++outer) {
+    SEM_CUDA(ax64(m, ws->x, ws->w, o.h1, o.h2, false, nullptr, nullptr, nullptr, nullptr, ws->s));
+    SEM_CUDA(launch_gs<double>(ws->w, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, 1, nullptr, ws->s));
+    SEM_CUDA(launch_residual(ws->r, ws->b, ws->w, m->wm, ws->n, ws->st, ws->part_vec, 1, ws->s));
+    count_launches(3);
+    PcgState s0;
+    st = read_state(ws, s0);
+    if (st != SEM_OK) return st;
+    if (s0.bb == 0.0) {
+      SEM_CUDA(cudaMemsetAsync(ws->x, 0, ws->n * sizeof(double), ws->s));
+      res.rel = 0.0;
+      res.outer = outer;
+      return SEM_OK;
+    }
+    res.rel = std::sqrt(s0.aux / s0.bb);
+    res.outer = outer;
+    if (res.rel <= o.tol) {
+      res.status = SEM_OK;
+      return SEM_OK;
+    }
+    if (outer >= max_outer) {
+      res.status = SEM_ERR_NOT_CONVERGED;
+      return SEM_OK;
+    }
+    const double rnorm = std::sqrt(s0.aux);
+    launch_scale_to_f32(ws->r32, ws->r, 1.0 / rnorm, ws->n, ws->s);
+    launch_zero_f32(ws->x32, ws->n, ws->s);
+    SEM_CUDA(cudaGetLastError());
+    st = put_state(ws, inner_tol, maxit, 0);
+    if (st != SEM_OK) return st;
+    VecParams<float> v{ws->x32, ws->r32, ws->z32, ws->p32, ws->w32, ws->minv32, ws->r32, m->wm, ws->n, ws->st,
+                       ws->part_vec};
+    SEM_CUDA(launch_pcg_init<float>(v, ws->s));
+    count_launches(3);
+    PcgState fin;
+    st = run_chunks(ws, ws->g32.exec, maxit, fin);
+    if (st != SEM_OK) return st;
+    res.iters += fin.iter;
+    if (fin.status == SEM_ERR_BREAKDOWN) {
+      res.status = SEM_ERR_BREAKDOWN;
+      return SEM_OK;
+    }
+    launch_accumulate(ws->x, ws->x32, rnorm, ws->n, ws->s);
+    SEM_CUDA(cudaGetLastError());
+    count_launches(1);
+  }
+}
+
+static double tuned_inner_tol(int N) {
+  (void)N;
+  return 1e-4;
+}
+
+static sem_status solve_common(const sem_mesh* cm, const double* b, double* x, bool host_io,
+                               const sem_solve_opts* opts, sem_solve_result* result, cudaStream_t user) {
+  if (!cm || !b || !x || !opts) {
+    set_error("sem_pcg_solve: null argument");
+    return SEM_ERR_INVALID;
+  }
+  sem_mesh* m = const_cast<sem_mesh*>(cm);
+  sem_solve_opts o = *opts;
+  if (!(o.tol > 0.0)) o.tol = 1e-10;
+  const int maxit = o.maxit > 0 ? o.maxit : 20000;
+  const int max_outer = o.max_outer > 0 ? o.max_outer : 50;
+  const double inner_tol = o.inner_tol > 0.0 ? o.inner_tol : tuned_inner_tol(m->N);
+  if (o.prec != SEM_FP64 && o.prec != SEM_FP32 && o.prec != SEM_MIXED) {
+    set_error("sem_pcg_solve: bad prec");
+    return SEM_ERR_INVALID;
+  }
+  if (!(o.h1 >= 0.0) || !(o.h2 >= 0.0) || (o.h1 == 0.0 && o.h2 == 0.0)) {
+    set_error("sem_pcg_solve: need h1 >= 0, h2 >= 0, not both zero");
+    return SEM_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(m->ws_mutex);
+  if (!m->ws) {
+    sem_status st = alloc_ws(m, &m->ws);
+    if (st != SEM_OK) return st;
+  }
+  Workspace* ws = m->ws;
+  const size_t bytes = (size_t)ws->n * sizeof(double);
+  SEM_CUDA(cudaEventRecord(ws->eu, user));
+  SEM_CUDA(cudaStreamWaitEvent(ws->s, ws->eu, 0));
+  SEM_CUDA(cudaEventRecord(ws->e0, ws->s));
+  const cudaMemcpyKind in = host_io ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  SEM_CUDA(cudaMemcpyAsync(ws->b, b, bytes, in, ws->s));
+  SEM_CUDA(cudaMemcpyAsync(ws->x, x, bytes, in, ws->s));
+  launch_mask(ws->x, m->wm, ws->n, ws->s);
+  count_launches(1);
+  if (!(ws->minv_h1 == o.h1 && ws->minv_h2 == o.h2)) {
+    launch_minv(ws->minv, ws->minv32, m->dK, m->dB, m->wm, o.h1, o.h2, ws->n, ws->s);
+    count_launches(1);
+    ws->minv_h1 = o.h1;
+    ws->minv_h2 = o.h2;
+  }
+  SEM_CUDA(cudaGetLastError());
+  SolveOut res;
+  sem_status st;
+  if (o.prec == SEM_FP64)
+    st = pcg64(m, ws, o, maxit, res);
+  else if (o.prec == SEM_MIXED)
+    st = pcg_mixed(m, ws, o, maxit, inner_tol, max_outer, res);
+  else
+    st = pcg_mixed(m, ws, o, maxit, o.tol, 1, res);
+  if (st != SEM_OK) {
+    ws->minv_h1 = NAN;  // state unknown after a failure
+    return st;
+  }
+  const cudaMemcpyKind outk = host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  SEM_CUDA(cudaMemcpyAsync(x, ws->x, bytes, outk, ws->s));
+  SEM_CUDA(cudaEventRecord(ws->e1, ws->s));
+  SEM_CUDA(cudaStreamSynchronize(ws->s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ws->e0, ws->e1);
+  if (result) {
+    result->iters = res.iters;
+    result->outer_iters = res.outer;
+    result->rel_res = res.rel;
+    result->ms = ms;
+    result->status = res.status;
+  }
+  return (sem_status)res.status;
+}
+
+}  // namespace sem
+
+using namespace sem;
+
+extern "C" {
+
+sem_status sem_pcg_solve(const sem_mesh* m, const double* b_dev, double* x_dev, const sem_solve_opts* opts,
+                         sem_solve_result* result, void* stream) {
+  return solve_common(m, b_dev, x_dev, false, opts, result, (cudaStream_t)stream);
+}
+
+sem_status sem_pcg_solve_host(const sem_mesh* m, const double* b_host, double* x_host, const sem_solve_opts* opts,
+                              sem_solve_result* result, void* stream) {
+  return solve_common(m, b_host, x_host, true, opts, result, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,373 @@
+"""Thin ctypes binding of the C ABI in include/sem.h (argument marshalling
+only: every step of the hot path runs in libsem.so's CUDA kernels).
+
+Device buffers are passed as torch CUDA tensors (their data_ptr()), host
+buffers as numpy arrays.  There is no CPU fallback: if libsem.so is missing
+or the GPU is unusable, the calls raise.
+"""
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsem.so")
+
+SEM_OK, SEM_ERR_INVALID, SEM_ERR_OOM, SEM_ERR_CUDA = 0, 1, 2, 3
+SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN, SEM_ERR_BUSY, SEM_ERR_DEVICE_TIMEOUT = 4, 5, 6, 7
+SEM_ERR_BAD_MESH, SEM_ERR_TIMEOUT, SEM_ERR_NOT_FOUND, SEM_ERR_CANCELLED = 8, 9, 10, 11
+FP64, FP32, MIXED = 0, 1, 2
+KIND = {"box": 0, "pipe": 1, "explicit": 2}
+
+
+class SemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("N", C.c_int),
+                ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("lx", C.c_double), ("ly", C.c_double), ("lz", C.c_double),
+                ("nc", C.c_int), ("nr", C.c_int), ("nzp", C.c_int),
+                ("R", C.c_double), ("L", C.c_double), ("a", C.c_double), ("beta", C.c_double),
+                ("periodic_z", C.c_int),
+                ("E", C.c_int64), ("xyz", C.c_void_p), ("vert", C.c_void_p), ("dirichlet_face", C.c_void_p)]
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [("E", C.c_int64), ("N", C.c_int), ("n_local", C.c_int64), ("n_global", C.c_int64),
+                ("n_segments", C.c_int64), ("n_seg_points", C.c_int64), ("dev_bytes", C.c_size_t)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("h1", C.c_double), ("h2", C.c_double), ("inner_tol", C.c_double),
+                ("maxit", C.c_int), ("max_outer", C.c_int), ("prec", C.c_int)]
+
+
+class SolveResult(C.Structure):
+    _fields_ = [("iters", C.c_int), ("outer_iters", C.c_int), ("rel_res", C.c_double), ("ms", C.c_double),
+                ("status", C.c_int)]
+
+    def as_dict(self):
+        return dict(iters=self.iters, outer_iters=self.outer_iters, rel_res=self.rel_res, ms=self.ms,
+                    status=self.status)
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_slots", C.c_int), ("max_queue", C.c_int),
+                ("device", C.c_int)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64),
+                ("cancelled", C.c_uint64), ("queued", C.c_int), ("running", C.c_int),
+                ("hbm_in_use", C.c_size_t), ("hbm_budget", C.c_size_t)]
+
+
+# name -> (restype, argtypes); every entry point declared in include/sem.h
+_P = C.c_void_p
+SIGNATURES = {
+    "sem_mesh_create": (C.c_int, [C.POINTER(MeshDesc), _P, C.POINTER(_P)]),
+    "sem_mesh_destroy": (C.c_int, [_P]),
+    "sem_mesh_info": (C.c_int, [_P, C.POINTER(MeshInfo)]),
+    "sem_mesh_global_ids": (C.c_int, [_P, _P]),
+    "sem_mesh_coords": (C.c_int, [_P, _P, _P]),
+    "sem_mesh_geometry": (C.c_int, [_P, _P, _P, _P]),
+    "sem_mesh_weights": (C.c_int, [_P, _P, _P, _P]),
+    "sem_ax": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, C.c_int, _P]),
+    "sem_gs": (C.c_int, [_P, _P, C.c_int, C.c_int, _P]),
+    "sem_rhs": (C.c_int, [_P, _P, _P, _P]),
+    "sem_apply": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, _P]),
+    "sem_jacobi": (C.c_int, [_P, C.c_double, C.c_double, _P, _P]),
+    "sem_pcg_solve": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
+    "sem_pcg_solve_host": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
+    "sem_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(_P)]),
+    "sem_server_submit": (C.c_int, [_P, C.POINTER(MeshDesc), _P, C.POINTER(SolveOpts), C.POINTER(C.c_uint64)]),
+    "sem_server_poll": (C.c_int, [_P, C.c_uint64, C.c_int, _P, C.POINTER(SolveResult)]),
+    "sem_server_cancel": (C.c_int, [_P, C.c_uint64]),
+    "sem_server_stats_get": (C.c_int, [_P, C.POINTER(ServerStats)]),
+    "sem_server_destroy": (C.c_int, [_P]),
+    "sem_topology_numbering": (C.c_int, [C.c_int64, C.c_int, _P, _P, C.POINTER(C.c_int64)]),
+    "sem_mesh_vertices": (C.c_int, [C.POINTER(MeshDesc), _P, C.POINTER(C.c_int64)]),
+    "sem_status_str": (C.c_char_p, [C.c_int]),
+    "sem_last_error": (C.c_char_p, []),
+    "sem_version": (C.c_int, []),
+    "sem_kernel_launches": (C.c_uint64, []),
+    "sem_mesh_fp64_kernel": (C.c_int, [_P]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libsem.so (built by __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, what):
+    if status != SEM_OK:
+        msg = lib().sem_last_error().decode(errors="replace")
+        name = lib().sem_status_str(status).decode()
+        raise SemError(status, f"{what}: {name}: {msg}")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, dtype=None, numel=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(a, dtype, numel=None):
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"expected a C-contiguous numpy {dtype} array")
+    if numel is not None and a.size != numel:
+        raise ValueError(f"expected {numel} elements, got {a.size}")
+    return C.c_void_p(a.ctypes.data)
+
+
+def make_desc(desc):
+    """Fill a MeshDesc from a dict (keys as in sem_mesh_desc; 'kind' is
+    'box', 'pipe' or 'explicit').  Returns (MeshDesc, keepalive list)."""
+    d = MeshDesc()
+    keep = []
+    d.kind = KIND[desc["kind"]]
+    d.N = int(desc["N"])
+    if desc["kind"] == "box":
+        d.nx, d.ny, d.nz = int(desc["nx"]), int(desc["ny"]), int(desc["nz"])
+        d.lx, d.ly, d.lz = float(desc.get("lx", 1.0)), float(desc.get("ly", 1.0)), float(desc.get("lz", 1.0))
+    elif desc["kind"] == "pipe":
+        d.nc, d.nr, d.nzp = int(desc["nc"]), int(desc["nr"]), int(desc["nzp"])
+        d.R, d.L = float(desc.get("R", 1.0)), float(desc.get("L", 8.0))
+        d.a = float(desc.get("a", 0.5 * d.R))
+        d.beta = float(desc.get("beta", 2.0))
+        d.periodic_z = int(bool(desc.get("periodic", True)))
+    else:
+        xyz = np.ascontiguousarray(desc["xyz"], dtype=np.float64)
+        vert = np.ascontiguousarray(desc["vert"], dtype=np.int64)
+        dface = np.ascontiguousarray(desc["dirichlet_face"], dtype=np.uint8)
+        d.E = int(vert.shape[0])
+        d.xyz, d.vert, d.dirichlet_face = xyz.ctypes.data, vert.ctypes.data, dface.ctypes.data
+        keep += [xyz, vert, dface]
+    return d, keep
+
+
+def _opts(tol=1e-10, h1=1.0, h2=0.0, prec=FP64, inner_tol=0.0, maxit=0, max_outer=0):
+    o = SolveOpts()
+    o.tol, o.h1, o.h2, o.inner_tol = float(tol), float(h1), float(h2), float(inner_tol)
+    o.maxit, o.max_outer, o.prec = int(maxit), int(max_outer), int(prec)
+    return o
+
+
+class Mesh:
+    """A mesh resident on the current CUDA device (sem_mesh_create)."""
+
+    def __init__(self, desc, stream=None):
+        d, keep = make_desc(desc)
+        h = C.c_void_p()
+        _check(lib().sem_mesh_create(C.byref(d), _stream(stream), C.byref(h)), "sem_mesh_create")
+        self._h = h
+        info = MeshInfo()
+        _check(lib().sem_mesh_info(h, C.byref(info)), "sem_mesh_info")
+        self.E, self.N, self.n_local, self.n_global = info.E, info.N, info.n_local, info.n_global
+        self.n_segments, self.n_seg_points, self.dev_bytes = info.n_segments, info.n_seg_points, info.dev_bytes
+        self.n = self.N + 1
+        self.shape = (self.E, self.n, self.n, self.n)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sem_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def fp64_double_float(self):
+        """True if FP64 requests on this mesh run the double-float kernel."""
+        return bool(lib().sem_mesh_fp64_kernel(self._h))
+
+    def global_ids(self):
+        out = np.empty(self.n_local, dtype=np.int64)
+        _check(lib().sem_mesh_global_ids(self._h, out.ctypes.data), "sem_mesh_global_ids")
+        return out
+
+    def coords(self, stream=None):
+        import torch
+        out = torch.empty((self.E, 3, self.n, self.n, self.n), dtype=torch.float64, device="cuda")
+        _check(lib().sem_mesh_coords(self._h, _dptr(out), _stream(stream)), "sem_mesh_coords")
+        return out
+
+    def geometry(self, stream=None):
+        import torch
+        G = torch.empty((self.E, 6, self.n, self.n, self.n), dtype=torch.float64, device="cuda")
+        B = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        _check(lib().sem_mesh_geometry(self._h, _dptr(G), _dptr(B), _stream(stream)), "sem_mesh_geometry")
+        return G, B
+
+    def weights(self, stream=None):
+        import torch
+        mult = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        mask = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        _check(lib().sem_mesh_weights(self._h, _dptr(mult), _dptr(mask), _stream(stream)), "sem_mesh_weights")
+        return mult, mask
+
+    def ax(self, u, w, h1=1.0, h2=0.0, prec=FP64, stream=None):
+        import torch
+        dt = torch.float64 if prec == FP64 else torch.float32
+        _check(lib().sem_ax(self._h, _dptr(u, dt, self.n_local), _dptr(w, dt, self.n_local), float(h1), float(h2),
+                            int(prec), _stream(stream)), "sem_ax")
+        return w
+
+    def gs(self, v, apply_mask=True, prec=FP64, stream=None):
+        import torch
+        dt = torch.float64 if prec == FP64 else torch.float32
+        _check(lib().sem_gs(self._h, _dptr(v, dt, self.n_local), int(prec), int(bool(apply_mask)), _stream(stream)),
+               "sem_gs")
+        return v
+
+    def rhs(self, f, b, stream=None):
+        import torch
+        _check(lib().sem_rhs(self._h, _dptr(f, torch.float64, self.n_local), _dptr(b, torch.float64, self.n_local),
+                             _stream(stream)), "sem_rhs")
+        return b
+
+    def apply(self, x, y, h1=1.0, h2=0.0, stream=None):
+        import torch
+        _check(lib().sem_apply(self._h, _dptr(x, torch.float64, self.n_local), _dptr(y, torch.float64, self.n_local),
+                               float(h1), float(h2), _stream(stream)), "sem_apply")
+        return y
+
+    def jacobi(self, out, h1=1.0, h2=0.0, stream=None):
+        import torch
+        _check(lib().sem_jacobi(self._h, float(h1), float(h2), _dptr(out, torch.float64, self.n_local),
+                                _stream(stream)), "sem_jacobi")
+        return out
+
+    def solve(self, b, x, stream=None, check=False, **opts):
+        """sem_pcg_solve on device tensors; returns the result record (a dict).
+        A non-converged / breakdown status is reported in the record; with
+        check=True it raises instead."""
+        import torch
+        o = _opts(**opts)
+        r = SolveResult()
+        st = lib().sem_pcg_solve(self._h, _dptr(b, torch.float64, self.n_local), _dptr(x, torch.float64, self.n_local),
+                                 C.byref(o), C.byref(r), _stream(stream))
+        if st not in (SEM_OK, SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN) or (check and st != SEM_OK):
+            _check(st, "sem_pcg_solve")
+        return r.as_dict()
+
+    def solve_host(self, b, x, stream=None, **opts):
+        """sem_pcg_solve_host on numpy float64 arrays (copies inside the call)."""
+        o = _opts(**opts)
+        r = SolveResult()
+        st = lib().sem_pcg_solve_host(self._h, _hptr(b, np.float64, self.n_local), _hptr(x, np.float64, self.n_local),
+                                      C.byref(o), C.byref(r), _stream(stream))
+        if st not in (SEM_OK, SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN):
+            _check(st, "sem_pcg_solve_host")
+        return r.as_dict()
+
+
+def kernel_launches():
+    """Kernels launched by the library so far in this process (graph replays
+    count every kernel node)."""
+    return int(lib().sem_kernel_launches())
+
+
+def topology_numbering(E, N, vert):
+    """Host-only: first-touch global ids from corner vertex ids (sem_topology_numbering)."""
+    vert = np.ascontiguousarray(vert, dtype=np.int64)
+    out = np.empty(E * (N + 1) ** 3, dtype=np.int64)
+    ng = C.c_int64()
+    _check(lib().sem_topology_numbering(int(E), int(N), vert.ctypes.data, out.ctypes.data, C.byref(ng)),
+           "sem_topology_numbering")
+    return out, ng.value
+
+
+def mesh_vertices(desc):
+    """Host-only: corner vertex ids [E, 8] of the built-in generators."""
+    d, keep = make_desc(desc)
+    E = C.c_int64()
+    _check(lib().sem_mesh_vertices(C.byref(d), None, C.byref(E)), "sem_mesh_vertices")
+    out = np.empty((E.value, 8), dtype=np.int64)
+    _check(lib().sem_mesh_vertices(C.byref(d), out.ctypes.data, C.byref(E)), "sem_mesh_vertices")
+    return out
+
+
+class Server:
+    """Request server (sem_server_*)."""
+
+    def __init__(self, hbm_budget_bytes=0, max_slots=8, max_queue=4096, device=0):
+        o = ServerOpts()
+        o.hbm_budget_bytes, o.max_slots, o.max_queue, o.device = int(hbm_budget_bytes), max_slots, max_queue, device
+        h = C.c_void_p()
+        _check(lib().sem_server_create(C.byref(o), C.byref(h)), "sem_server_create")
+        self._h = h
+
+    def submit(self, desc, f, **opts):
+        d, keep = make_desc(desc)
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        o = _opts(**opts)
+        rid = C.c_uint64()
+        _check(lib().sem_server_submit(self._h, C.byref(d), f.ctypes.data, C.byref(o), C.byref(rid)),
+               "sem_server_submit")
+        return rid.value
+
+    def poll(self, rid, timeout_ms=-1, n_local=None):
+        """Returns (status, x or None, result dict); status SEM_ERR_TIMEOUT if not done."""
+        r = SolveResult()
+        x = np.empty(n_local, dtype=np.float64) if n_local else None
+        st = lib().sem_server_poll(self._h, C.c_uint64(rid), int(timeout_ms),
+                                   x.ctypes.data if x is not None else None, C.byref(r))
+        if st in (SEM_ERR_INVALID, SEM_ERR_NOT_FOUND, SEM_ERR_CUDA, SEM_ERR_OOM):
+            _check(st, "sem_server_poll")
+        return st, (x if st not in (SEM_ERR_TIMEOUT,) else None), r.as_dict()
+
+    def cancel(self, rid):
+        return lib().sem_server_cancel(self._h, C.c_uint64(rid))
+
+    def stats(self):
+        s = ServerStats()
+        _check(lib().sem_server_stats_get(self._h, C.byref(s)), "sem_server_stats_get")
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sem_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

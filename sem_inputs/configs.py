@@ -13,6 +13,8 @@ MESHES = {
     # Straight pipe R = 1, L = 8, O-grid, wall clustering beta = 2, periodic in z.
     "pipe4096_n7": dict(kind="pipe", nc=8, nr=2, nzp=32, N=7, R=1.0, L=8.0, a=0.5, beta=2.0, periodic=True),
     "pipe262144_n7": dict(kind="pipe", nc=16, nr=4, nzp=512, N=7, R=1.0, L=8.0, a=0.5, beta=2.0, periodic=True),
+    # same cross-section and element shape as pipe262144_n7, 1/8 of the length (profiling size, > L2)
+    "pipe32768_n7": dict(kind="pipe", nc=16, nr=4, nzp=64, N=7, R=1.0, L=1.0, a=0.5, beta=2.0, periodic=True),
     "pipe1048576_n7": dict(kind="pipe", nc=32, nr=8, nzp=512, N=7, R=1.0, L=8.0, a=0.5, beta=2.0, periodic=True),
     "pipe131072_n11": dict(kind="pipe", nc=16, nr=4, nzp=256, N=11, R=1.0, L=8.0, a=0.5, beta=2.0, periodic=True),
 }
