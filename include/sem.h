@@ -195,6 +195,32 @@ sem_status sem_pcg_solve(const sem_mesh* mesh, const double* b_dev, double* x_de
 sem_status sem_pcg_solve_host(const sem_mesh* mesh, const double* b_host, double* x_host,
                               const sem_solve_opts* opts, sem_solve_result* result, void* stream);
 
+/* ---- solve without device allocation -------------------------------------- */
+
+/* Largest mesh (local points) sem_pcg_solve_noalloc accepts. */
+#define SEM_NOALLOC_MAX_POINTS (1 << 18)
+
+/* The FP64 solve of sem_pcg_solve (opts->prec must be SEM_FP64) for callers
+ * that cannot allocate device memory: code whose device memory is owned by a
+ * fixed pool or another allocator, and real-time loops that cannot afford
+ * cudaMalloc's latency or its implicit synchronisation.  The paper has no
+ * counterpart; this is an interface convenience of this library.
+ *
+ * Its scratch (work vectors, reduction partials, the CG state; ~10.5 MB) is
+ * one file-scope device array of fixed size, present on every device that
+ * loads the library until the process exits; the call itself allocates
+ * nothing.  The caller passes b_dev (input) and x_dev (initial guess in,
+ * solution out) as for sem_pcg_solve.  Meshes with more than
+ * SEM_NOALLOC_MAX_POINTS local points are rejected with SEM_ERR_INVALID.
+ * b_dev and x_dev must be 16-byte aligned (SEM_ERR_INVALID otherwise).
+ * Every call shares the one array and overwrites it, so calls whose work
+ * overlaps on the GPU (different streams or threads) race and must not be
+ * issued.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Runs on `stream` and returns when x is written; result->ms is 0. */
+sem_status sem_pcg_solve_noalloc(const sem_mesh* mesh, const double* b_dev, double* x_dev,
+                                 const sem_solve_opts* opts, sem_solve_result* result, void* stream);
+
 /* ---- serving ------------------------------------------------------------ */
 
 typedef struct {

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libsem.so")
 SEM_OK, SEM_ERR_INVALID, SEM_ERR_OOM, SEM_ERR_CUDA = 0, 1, 2, 3
 SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN, SEM_ERR_BUSY, SEM_ERR_DEVICE_TIMEOUT = 4, 5, 6, 7
 SEM_ERR_BAD_MESH, SEM_ERR_TIMEOUT, SEM_ERR_NOT_FOUND, SEM_ERR_CANCELLED = 8, 9, 10, 11
+NOALLOC_MAX_POINTS = 1 << 18
 FP64, FP32, MIXED = 0, 1, 2
 KIND = {"box": 0, "pipe": 1, "explicit": 2}
 
@@ -84,6 +85,7 @@ SIGNATURES = {
     "sem_jacobi": (C.c_int, [_P, C.c_double, C.c_double, _P, _P]),
     "sem_pcg_solve": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
     "sem_pcg_solve_host": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
+    "sem_pcg_solve_noalloc": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
     "sem_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(_P)]),
     "sem_server_submit": (C.c_int, [_P, C.POINTER(MeshDesc), _P, C.POINTER(SolveOpts), C.POINTER(C.c_uint64)]),
     "sem_server_poll": (C.c_int, [_P, C.c_uint64, C.c_int, _P, C.POINTER(SolveResult)]),
@@ -285,6 +287,19 @@ class Mesh:
                                  C.byref(o), C.byref(r), _stream(stream))
         if st not in (SEM_OK, SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN) or (check and st != SEM_OK):
             _check(st, "sem_pcg_solve")
+        return r.as_dict()
+
+    def solve_noalloc(self, b, x, stream=None, **opts):
+        """sem_pcg_solve_noalloc: the FP64 solve with all scratch in the
+        library's fixed device array (no device allocation in the call)."""
+        import torch
+        o = _opts(**opts)
+        r = SolveResult()
+        st = lib().sem_pcg_solve_noalloc(self._h, _dptr(b, torch.float64, self.n_local),
+                                         _dptr(x, torch.float64, self.n_local), C.byref(o), C.byref(r),
+                                         _stream(stream))
+        if st not in (SEM_OK, SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN):
+            _check(st, "sem_pcg_solve_noalloc")
         return r.as_dict()
 
     def solve_host(self, b, x, stream=None, **opts):
