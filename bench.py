@@ -295,7 +295,8 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer (mixed)", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer (mixed, reliable updates)",
+            "data": "synthetic",
             "config": {"workload": f"{args.workload}: O-grid pipe E={m.E} N={m.N}, mixed-precision Jacobi-PCG "
                                    f"to 1e-10 (FP32 inner, FP64 outer residual)",
                        "E": m.E, "N": m.N, "n_local": P, "n_global": m.n_global, "tol": 1e-10,

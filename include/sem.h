@@ -172,6 +172,11 @@ typedef struct {
   int maxit;        /* iteration cap (per inner solve for SEM_MIXED); <= 0 means 20000 */
   int max_outer;    /* SEM_MIXED: refinement steps cap; <= 0 means 50 */
   int prec;         /* SEM_FP64 (plain PCG) or SEM_MIXED (FP32 inner / FP64 outer); SEM_FP32 = plain FP32 PCG */
+  int refine;       /* SEM_MIXED: 0 = reliable updates (CG direction kept across FP64 residual
+                       replacements; Sleijpen & van der Vorst 1996), 1 = restarted refinement
+                       (defect correction: a fresh FP32 PCG on each FP64 residual) */
+  double delta;     /* SEM_MIXED, refine = 0: replace the residual when the FP32 one has dropped by
+                       this factor since the last replacement; <= 0 means 0.1 */
 } sem_solve_opts;
 
 typedef struct {

@@ -15,7 +15,11 @@ The reading taken here (the paper fixes none of these details):
   ||r|| <= tol ||b|| in the norm above, tol = 1e-10, maxit = 20000;
 * mixed precision: an FP64 outer iterative refinement r = b - A x around an
   inner PCG run entirely on FP32 copies of G, B, M^{-1} and the fields, whose
-  inner products are FP32 products summed in FP64.
+  inner products are FP32 products summed in FP64 -- either restarted at
+  every refinement step (``pcg_mixed``, classic defect correction) or keeping
+  the CG direction across refinements (``pcg_mixed_reliable``: "reliable
+  updates", Sleijpen & van der Vorst, Computing 56 (1996); Clark et al.,
+  Comput. Phys. Commun. 181 (2010), Sec. 4).
 """
 
 import numpy as np
@@ -185,3 +189,62 @@ def pcg_mixed(prob, b, tol=1e-10, inner_tol=1e-5, max_outer=50, maxit=20000):
         outer += 1
     st = CONVERGED if rnorm <= tol * bnorm else NOT_CONVERGED
     return Result(x, total, rnorm / bnorm, st, hist, outer)
+
+
+def pcg_mixed_reliable(prob, b, tol=1e-10, delta=0.1, maxit=20000, gamma=0.2):
+    """Mixed-precision PCG with reliable updates.
+
+    The CG recurrences run in FP32 on the scaled system (b / ||b||): x32 holds
+    the solution increment since the last reliable update.  Whenever the FP32
+    iterated residual has dropped below delta times its largest value since
+    that update (or below gamma * tol: the FP32 residual must undershoot the
+    target, otherwise a true residual just above tol triggers a replacement
+    after every few steps and stalls), the increment is added to the FP64
+    solution, the true residual r = b - A64 x is recomputed in FP64 and
+    replaces the FP32 one, and CG continues with its current direction p:
+    z = M^{-1} r, beta = <r,z>_new / <r,z>_old, p = z + beta p.  The solve stops
+    when the FP64 true residual meets the tolerance."""
+    p32 = Problem32(prob)
+    x = np.zeros(prob.shape)
+    bnorm = np.sqrt(prob.dot(b, b))
+    if bnorm == 0.0:
+        return Result(x, 0, 0.0, CONVERGED, [])
+    s = 1.0 / bnorm
+    r = (b * s).astype(np.float32)
+    x32 = np.zeros(prob.shape, dtype=np.float32)
+    z = p32.Minv * r
+    p = np.zeros(prob.shape, dtype=np.float32)
+    rho = p32.dot(r, z)
+    beta = np.float32(0.0)
+    rr_max = p32.dot(r, r)
+    hist, updates = [1.0], 0
+    for k in range(1, maxit + 1):
+        p = z + beta * p
+        w = p32.A(p)
+        sigma = p32.dot(p, w)
+        if not sigma > 0.0:
+            return Result(x + x32.astype(np.float64) / s, k, hist[-1], BREAKDOWN, hist, updates)
+        alpha = np.float32(rho / sigma)
+        x32 = x32 + alpha * p
+        r = r - alpha * w
+        rr = p32.dot(r, r)
+        if rr <= delta * delta * rr_max or rr <= (gamma * tol) ** 2:
+            x = x + x32.astype(np.float64) / s
+            x32[:] = 0.0
+            rt = b - prob.A(x)
+            rel = np.sqrt(prob.dot(rt, rt)) / bnorm
+            hist.append(rel)
+            updates += 1
+            if rel <= tol:
+                return Result(x, k, rel, CONVERGED, hist, updates)
+            r = (rt * s).astype(np.float32)
+            rr_max = p32.dot(r, r)
+        else:
+            rr_max = max(rr_max, rr)
+        z = p32.Minv * r
+        rho_new = p32.dot(r, z)
+        beta = np.float32(rho_new / rho)
+        rho = rho_new
+    x = x + x32.astype(np.float64) / s
+    rt = b - prob.A(x)
+    return Result(x, maxit, np.sqrt(prob.dot(rt, rt)) / bnorm, NOT_CONVERGED, hist, updates)

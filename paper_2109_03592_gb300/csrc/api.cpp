@@ -53,12 +53,12 @@ void free_mesh_arrays(sem_mesh* m) {
   dev_free(m->G32);
   dev_free(m->G32lo);
   dev_free(m->B32);
+  dev_free(m->B32lo);
   dev_free(m->dK);
   dev_free(m->dB);
   dev_free(m->wm);
-  dev_free(m->seg_ptr);
-  dev_free(m->seg_idx);
-  dev_free(m->seg_dir);
+  dev_free(m->gs_idx);
+  dev_free(m->gs_ptr);
   dev_free(m->D64);
   dev_free(m->D32);
   dev_free(m->D32lo);
@@ -90,8 +90,12 @@ sem_status build_mesh(const sem_mesh_desc& d, cudaStream_t s, sem_mesh* m) {
   m->E = E;
   m->n_local = P;
   m->n_global = topo.n_global;
-  m->n_seg = (int64_t)plan.seg_dir.size();
-  m->n_seg_points = (int64_t)plan.seg_idx.size();
+  m->n_seg = plan.n_nodes;
+  m->n_seg_points = plan.n_points;
+  for (int c = 0; c < kGsClasses; ++c) {
+    m->gs_off[c] = plan.off[c];
+    m->gs_cnt[c] = plan.cnt[c];
+  }
   SEM_CUDA(cudaGetDevice(&m->device));
 
   std::vector<double> xi, w, D;
@@ -109,12 +113,12 @@ sem_status build_mesh(const sem_mesh_desc& d, cudaStream_t s, sem_mesh* m) {
   SEM_TRY(dev_alloc(&m->G32, 6 * P, tb));
   SEM_TRY(dev_alloc(&m->G32lo, 6 * P, tb));
   SEM_TRY(dev_alloc(&m->B32, P, tb));
+  SEM_TRY(dev_alloc(&m->B32lo, P, tb));
   SEM_TRY(dev_alloc(&m->dK, P, tb));
   SEM_TRY(dev_alloc(&m->dB, P, tb));
   SEM_TRY(dev_alloc(&m->wm, P, tb));
-  SEM_TRY(dev_alloc(&m->seg_ptr, plan.seg_ptr.size(), tb));
-  SEM_TRY(dev_alloc(&m->seg_idx, plan.seg_idx.size(), tb));
-  SEM_TRY(dev_alloc(&m->seg_dir, plan.seg_dir.size(), tb));
+  SEM_TRY(dev_alloc(&m->gs_idx, plan.idx.size(), tb));
+  SEM_TRY(dev_alloc(&m->gs_ptr, plan.gptr.size(), tb));
   SEM_TRY(dev_alloc(&m->D64, n * n, tb));
   SEM_TRY(dev_alloc(&m->D32, n * n, tb));
   SEM_TRY(dev_alloc(&m->D32lo, n * n, tb));
@@ -145,11 +149,9 @@ sem_status build_mesh(const sem_mesh_desc& d, cudaStream_t s, sem_mesh* m) {
   SEM_CUDA(cudaMemcpyAsync(m->D32lo, D32lo.data(), n * n * sizeof(float), cudaMemcpyHostToDevice, s));
   SEM_CUDA(cudaMemsetAsync(bad_d, 0, sizeof(int), s));
   SEM_CUDA(cudaMemcpyAsync(m->wm, plan.wm.data(), P, cudaMemcpyHostToDevice, s));
-  SEM_CUDA(cudaMemcpyAsync(m->seg_ptr, plan.seg_ptr.data(), plan.seg_ptr.size() * 4, cudaMemcpyHostToDevice, s));
-  if (!plan.seg_idx.empty())
-    SEM_CUDA(cudaMemcpyAsync(m->seg_idx, plan.seg_idx.data(), plan.seg_idx.size() * 4, cudaMemcpyHostToDevice, s));
-  if (!plan.seg_dir.empty())
-    SEM_CUDA(cudaMemcpyAsync(m->seg_dir, plan.seg_dir.data(), plan.seg_dir.size(), cudaMemcpyHostToDevice, s));
+  if (!plan.idx.empty())
+    SEM_CUDA(cudaMemcpyAsync(m->gs_idx, plan.idx.data(), plan.idx.size() * 4, cudaMemcpyHostToDevice, s));
+  SEM_CUDA(cudaMemcpyAsync(m->gs_ptr, plan.gptr.data(), plan.gptr.size() * 4, cudaMemcpyHostToDevice, s));
 
   std::vector<double> tlev;
   if (d.kind == SEM_MESH_BOX) {
@@ -167,11 +169,11 @@ sem_status build_mesh(const sem_mesh_desc& d, cudaStream_t s, sem_mesh* m) {
   SEM_CUDA(launch_geometry(m->xyz, m->G64, m->B64, m->D64, w_d, n, E, bad_d, s));
   // assembled diagonals for the Jacobi preconditioner: dK = QQ^T diag(stiffness), dB = QQ^T B
   launch_local_diag(m->G64, m->dK, m->D64, n, E, s);
-  SEM_CUDA(launch_gs<double>(m->dK, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, 0, nullptr, s));
+  SEM_CUDA(launch_gs<double>(m->dK, gs_dev(m), 0, nullptr, s));
   SEM_CUDA(cudaMemcpyAsync(m->dB, m->B64, P * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  SEM_CUDA(launch_gs<double>(m->dB, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, 0, nullptr, s));
+  SEM_CUDA(launch_gs<double>(m->dB, gs_dev(m), 0, nullptr, s));
   launch_split_f64(m->G64, m->G32, m->G32lo, 6 * P, s);
-  launch_split_f64(m->B64, m->B32, nullptr, P, s);
+  launch_split_f64(m->B64, m->B32, m->B32lo, P, s);
   SEM_CUDA(cudaGetLastError());
   count_launches(7);
   int bad = 0;
@@ -331,9 +333,9 @@ sem_status sem_gs(const sem_mesh* m, void* v_dev, sem_prec prec, int apply_mask,
   }
   cudaStream_t s = (cudaStream_t)stream;
   if (prec == SEM_FP64) {
-    SEM_CUDA(launch_gs<double>((double*)v_dev, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, apply_mask, nullptr, s));
+    SEM_CUDA(launch_gs<double>((double*)v_dev, gs_dev(m), apply_mask, nullptr, s));
   } else if (prec == SEM_FP32) {
-    SEM_CUDA(launch_gs<float>((float*)v_dev, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, apply_mask, nullptr, s));
+    SEM_CUDA(launch_gs<float>((float*)v_dev, gs_dev(m), apply_mask, nullptr, s));
   } else {
     set_error("sem_gs: prec must be SEM_FP64 or SEM_FP32");
     return SEM_ERR_INVALID;
@@ -350,7 +352,7 @@ sem_status sem_rhs(const sem_mesh* m, const double* f_dev, double* b_dev, void* 
   cudaStream_t s = (cudaStream_t)stream;
   launch_mul(b_dev, m->B64, f_dev, m->n_local, s);
   SEM_CUDA(cudaGetLastError());
-  SEM_CUDA(launch_gs<double>(b_dev, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, 1, nullptr, s));
+  SEM_CUDA(launch_gs<double>(b_dev, gs_dev(m), 1, nullptr, s));
   count_launches(2);
   return SEM_OK;
 }
@@ -363,7 +365,7 @@ sem_status sem_apply(const sem_mesh* m, const double* x_dev, double* y_dev, doub
   cudaStream_t s = (cudaStream_t)stream;
   sem_status st = apply_local(m, x_dev, y_dev, h1, h2, SEM_FP64, s);
   if (st != SEM_OK) return st;
-  SEM_CUDA(launch_gs<double>(y_dev, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, 1, nullptr, s));
+  SEM_CUDA(launch_gs<double>(y_dev, gs_dev(m), 1, nullptr, s));
   count_launches(1);
   return SEM_OK;
 }

@@ -37,6 +37,16 @@ __device__ __forceinline__ DF split64(double x) {
 
 __device__ __forceinline__ double join64(DF a) { return (double)a.h + (double)a.l; }
 
+// Product of two double-float numbers (Dekker), renormalised.
+__device__ __forceinline__ DF mul_df(DF a, DF b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  const float t = __fadd_rn(p, e);
+  return DF{t, __fsub_rn(e, __fsub_rn(t, p))};
+}
+
 // Lazily-compensated dot-product accumulator.
 struct Acc {
   float s, c;
@@ -166,9 +176,11 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_ax_df(const AxDFParam
   }
   __syncthreads();
 
-  double pw = 0.0;
+  Acc pw;  // this thread's part of <p, A_L p>, in double-float
+  pw.zero();
   if (act) {
     const DF h1 = split64(P.h1);
+    const DF h2 = split64(P.h2);
 #pragma unroll
     for (int k = 0; k < n; ++k) {
       Acc acc = rw[k];
@@ -183,15 +195,20 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_ax_df(const AxDFParam
       Acc sc;
       sc.zero();
       sc.madd(h1.h, h1.l, s.h, s.l);
-      double out = join64(sc.result());
-      if (P.helm) out += P.h2 * P.B[base + k * n2] * ud[k];
-      P.w[base + k * n2] = out;
-      if (FUSED) pw += ud[k] * out;
+      if (P.helm) {
+        // + h2 B u, with B = Bhi + Blo and u = (hi, lo)
+        const DF hb = mul_df(h2, DF{P.Bhi[base + k * n2], P.Blo[base + k * n2]});
+        sc.madd(hb.h, hb.l, ru[k].h, ru[k].l);
+      }
+      const DF o = sc.result();
+      P.w[base + k * n2] = join64(o);
+      if (FUSED) pw.madd(ru[k].h, ru[k].l, o.h, o.l);
     }
   }
 
   if (FUSED) {
-    const double s = block_sum(pw, sred);
+    const DF pr = pw.result();
+    const double s = block_sum((double)pr.h + (double)pr.l, sred);
     if (tid == 0) P.partial[blockIdx.x] = s;
     if (last_block(&P.st->cnt[0])) {
       const double pAp = sum_partials(P.partial, gridDim.x, 1, 0, sred);

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_ax(const AxParams<T> 
   }
   __syncthreads();
 
-  double pw = 0.0;
+  T pw = T(0);  // this thread's part of <p, A_L p> (n terms, accumulated in T)
   if (act) {
 #pragma unroll
     for (int k = 0; k < n; ++k) {
@@ -105,12 +105,12 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_ax(const AxParams<T> 
       T out = P.h1 * acc;
       if (P.helm) out += P.h2 * P.B[base + k * n2] * ru[k];
       P.w[base + k * n2] = out;
-      if (FUSED) pw += (double)(ru[k] * out);
+      if (FUSED) pw += ru[k] * out;
     }
   }
 
   if (FUSED) {
-    const double s = block_sum(pw, sred);
+    const double s = block_sum((double)pw, sred);
     if (tid == 0) P.partial[blockIdx.x] = s;
     if (last_block(&P.st->cnt[0])) {
       const double pAp = sum_partials(P.partial, gridDim.x, 1, 0, sred);

@@ -20,9 +20,12 @@ struct PcgState {
   double bb;     // <b, b> of the system being solved
   double tol2;   // tol^2
   double aux;    // scratch scalar (outer residual norms)
+  double rr_max; // largest <r, r> since the last reliable update
+  double delta2; // reliable-update trigger: pause when <r,r> <= delta2 * rr_max (0 = never)
   int iter;
   int maxit;
-  int done;      // 1 once converged / failed: later kernels of the chunk return at once
+  int done;      // 1 once converged / failed / paused: later kernels of the chunk return at once
+  int ru;        // 1 when paused for a reliable update (FP64 residual replacement)
   int status;    // sem_status of the run
   unsigned int cnt[4];  // arrival counters of the grid reductions
 };

@@ -48,7 +48,8 @@ struct AxDFParams {
   double* w;
   const float* Ghi;
   const float* Glo;
-  const double* B;
+  const float* Bhi;  // B = Bhi + Blo (Helmholtz term)
+  const float* Blo;
   const float* Dhi;
   const float* Dlo;
   double h1, h2;
@@ -70,9 +71,15 @@ cudaError_t launch_ax_df(int N, int variant, bool fused, const AxDFParams& p, cu
 int ax_df_available(int N);
 
 // ---- gather-scatter (gs.cu) ----
+// Device view of the class-based plan (see GsPlan in sem_internal.h).
+struct GsDev {
+  const int32_t* idx;
+  const int32_t* gptr;
+  int64_t off[9];
+  int64_t cnt[9];
+};
 template <typename T>
-cudaError_t launch_gs(T* v, const int32_t* seg_ptr, const int32_t* seg_idx, const uint8_t* seg_dir, int64_t nseg,
-                      int apply_mask, const PcgState* st, cudaStream_t s);
+cudaError_t launch_gs(T* v, const GsDev& g, int apply_mask, const PcgState* st, cudaStream_t s);
 
 // ---- PCG vector kernels (pcg.cu) ----
 template <typename T>
@@ -94,6 +101,9 @@ template <typename T>
 cudaError_t launch_pcg_update(const VecParams<T>& p, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pcg_init(const VecParams<T>& p, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pcg_restart(const VecParams<T>& p, cudaStream_t s);
+void launch_set_bb(PcgState* st, double bb, double delta2, cudaStream_t s);
 
 void launch_mul(double* out, const double* a, const double* b, int64_t n, cudaStream_t s);
 void launch_mask(double* x, const uint8_t* wm, int64_t n, cudaStream_t s);

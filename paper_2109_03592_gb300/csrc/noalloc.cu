@@ -119,7 +119,7 @@ extern "C" sem_status sem_pcg_solve_noalloc(const sem_mesh* m, const double* b_d
   // r = b - A x0
   st = apply_local(m, x_dev, w, h1, h2, SEM_FP64, s);
   if (st != SEM_OK) return st;
-  SEM_CUDA(launch_gs<double>(w, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, 1, nullptr, s));
+  SEM_CUDA(launch_gs<double>(w, gs_dev(m), 1, nullptr, s));
   SEM_CUDA(launch_residual(r, b_dev, w, m->wm, n, dst, part_vec, 1, s));
   VecParams<double> v{x_dev, r, z, p, w, minv, b_dev, m->wm, n, dst, part_vec};
   SEM_CUDA(launch_pcg_init<double>(v, s));
@@ -127,7 +127,7 @@ extern "C" sem_status sem_pcg_solve_noalloc(const sem_mesh* m, const double* b_d
 
   auto fp64_ax = [&]() -> cudaError_t {
     if (m->fp64_df) {
-      AxDFParams a{nullptr, w, m->G32, m->G32lo, m->B64, m->D32, m->D32lo, h1, h2, h2 != 0.0, m->E, z, p, dst,
+      AxDFParams a{nullptr, w, m->G32, m->G32lo, m->B32, m->B32lo, m->D32, m->D32lo, h1, h2, h2 != 0.0, m->E, z, p, dst,
                    part_ax};
       return launch_ax_df(m->N, m->ax_var[2], true, a, s, nullptr);
     }
@@ -147,7 +147,7 @@ extern "C" sem_status sem_pcg_solve_noalloc(const sem_mesh* m, const double* b_d
   for (int c = 0; c < max_chunks && !cur.done; ++c) {
     for (int k = 0; k < kChunk; ++k) {
       SEM_CUDA(fp64_ax());
-      SEM_CUDA(launch_gs<double>(w, m->seg_ptr, m->seg_idx, m->seg_dir, m->n_seg, 1, dst, s));
+      SEM_CUDA(launch_gs<double>(w, gs_dev(m), 1, dst, s));
       SEM_CUDA(launch_pcg_update<double>(v, s));
     }
     count_launches(3 * kChunk);

@@ -52,11 +52,43 @@ __device__ __forceinline__ void fill_inv_mult(T* sinv) {
   for (int m = threadIdx.x; m < 128; m += blockDim.x) sinv[m] = m ? T(1) / T(m) : T(0);
 }
 
+// 16-byte vectors of T and the matching multiplicity bytes.
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using V = float4;
+  using M = uchar4;
+  static constexpr int W = 4;
+  __device__ static float get(const V& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+  __device__ static void set(V& v, int k, float a) {
+    if (k == 0) v.x = a; else if (k == 1) v.y = a; else if (k == 2) v.z = a; else v.w = a;
+  }
+  __device__ static unsigned char getm(const M& m, int k) { return k == 0 ? m.x : k == 1 ? m.y : k == 2 ? m.z : m.w; }
+};
+template <>
+struct Vec16<double> {
+  using V = double2;
+  using M = uchar2;
+  static constexpr int W = 2;
+  __device__ static double get(const V& v, int k) { return k == 0 ? v.x : v.y; }
+  __device__ static void set(V& v, int k, double a) {
+    if (k == 0) v.x = a; else v.y = a;
+  }
+  __device__ static unsigned char getm(const M& m, int k) { return k == 0 ? m.x : m.y; }
+};
+
 // x += alpha p; r -= alpha w; z = M^{-1} r; then <r, z>, <r, r>; the last block
 // checks ||r|| <= tol ||b||, else forms beta = <r,z>_new / <r,z>_old.
+// Each thread moves 16-byte vectors (4 floats / 2 doubles per array), so a
+// resident block keeps 5 x 16 B loads per thread in flight.
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_pcg_update(const VecParams<T> P) {
   using Acc = typename AccOf<T>::type;
+  using VT = Vec16<T>;
+  using V = typename VT::V;
+  using M = typename VT::M;
+  constexpr int W = VT::W;
   __shared__ double sred[32];
   __shared__ T sinv[128];
   __shared__ int sdone;
@@ -66,10 +98,35 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(const VecParams<T> P
   if (sdone) return;
   const T alpha = (T)P.st->alpha;
   Acc rz, rr;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P.n; q += (int64_t)gridDim.x * blockDim.x) {
-    const T pq = P.p[q], wq = P.w[q];
-    const T rq = P.r[q] - alpha * wq;
-    P.x[q] = P.x[q] + alpha * pq;
+  const int64_t nv = P.n / W;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t q = t0; q < nv; q += stride) {
+    const V pv = reinterpret_cast<const V*>(P.p)[q];
+    const V wv = reinterpret_cast<const V*>(P.w)[q];
+    V rv = reinterpret_cast<const V*>(P.r)[q];
+    V xv = reinterpret_cast<const V*>(P.x)[q];
+    const V mv = reinterpret_cast<const V*>(P.minv)[q];
+    const M wm = reinterpret_cast<const M*>(P.wm)[q];
+    V zv;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      const T rq = VT::get(rv, k) - alpha * VT::get(wv, k);
+      VT::set(xv, k, VT::get(xv, k) + alpha * VT::get(pv, k));
+      VT::set(rv, k, rq);
+      const T zq = VT::get(mv, k) * rq;
+      VT::set(zv, k, zq);
+      const T im = sinv[VT::getm(wm, k) & 0x7f];
+      rz.add(rq * zq * im);
+      rr.add(rq * rq * im);
+    }
+    reinterpret_cast<V*>(P.x)[q] = xv;
+    reinterpret_cast<V*>(P.r)[q] = rv;
+    reinterpret_cast<V*>(P.z)[q] = zv;
+  }
+  for (int64_t q = nv * W + t0; q < P.n; q += stride) {  // tail (n not a multiple of W)
+    const T rq = P.r[q] - alpha * P.w[q];
+    P.x[q] = P.x[q] + alpha * P.p[q];
     P.r[q] = rq;
     const T zq = P.minv[q] * rq;
     P.z[q] = zq;
@@ -99,7 +156,11 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(const VecParams<T> P
       } else if (st->iter >= st->maxit) {
         st->done = 1;
         st->status = 4;  // SEM_ERR_NOT_CONVERGED
+      } else if (st->delta2 > 0.0 && rr_t <= st->delta2 * st->rr_max) {
+        st->done = 1;  // pause: the host replaces r by the FP64 true residual
+        st->ru = 1;
       } else {
+        if (rr_t > st->rr_max) st->rr_max = rr_t;
         st->beta = rz_t / st->rho;
         st->rho = rz_t;
       }
@@ -150,10 +211,61 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_init(const VecParams<T> P) 
       st->iter = 0;
       st->status = 0;
       st->done = (bb_t == 0.0) || (rr_t <= st->tol2 * bb_t);
+      st->rr_max = rr_t;
+      st->ru = 0;
       st->cnt[2] = 0;
     }
   }
 }
+
+// Continue CG after the residual r was replaced (reliable update):
+// z = M^{-1} r, rho_new = <r,z>, beta = rho_new / rho, rr_max = <r,r>; p is kept.
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_pcg_restart(const VecParams<T> P) {
+  using Acc = typename AccOf<T>::type;
+  __shared__ double sred[32];
+  __shared__ T sinv[128];
+  fill_inv_mult(sinv);
+  __syncthreads();
+  Acc rz, rr;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P.n; q += (int64_t)gridDim.x * blockDim.x) {
+    const T rq = P.r[q];
+    const T zq = P.minv[q] * rq;
+    P.z[q] = zq;
+    const T im = sinv[P.wm[q] & 0x7f];
+    rz.add(rq * zq * im);
+    rr.add(rq * rq * im);
+  }
+  const double a = block_sum(rz.get(), sred);
+  const double b = block_sum(rr.get(), sred);
+  if (threadIdx.x == 0) {
+    P.partial[2 * blockIdx.x] = a;
+    P.partial[2 * blockIdx.x + 1] = b;
+  }
+  if (last_block(&P.st->cnt[2])) {
+    const double rz_t = sum_partials(P.partial, gridDim.x, 2, 0, sred);
+    const double rr_t = sum_partials(P.partial, gridDim.x, 2, 1, sred);
+    if (threadIdx.x == 0) {
+      PcgState* st = P.st;
+      st->beta = rz_t / st->rho;
+      st->rho = rz_t;
+      st->rr = rr_t;
+      st->rr_max = rr_t;
+      st->ru = 0;
+      st->done = 0;
+      st->status = 0;
+      st->cnt[2] = 0;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_pcg_restart(const VecParams<T>& p, cudaStream_t s) {
+  k_pcg_restart<T><<<kVecBlocks, kVecThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+template cudaError_t launch_pcg_restart<float>(const VecParams<float>&, cudaStream_t);
+template cudaError_t launch_pcg_restart<double>(const VecParams<double>&, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_pcg_update(const VecParams<T>& p, cudaStream_t s) {
@@ -253,6 +365,12 @@ __global__ void k_accumulate(double* x, const float* d32, double sc, int64_t n) 
 void launch_accumulate(double* x, const float* d32, double sc, int64_t n, cudaStream_t s) {
   k_accumulate<<<kVecBlocks, kVecThreads, 0, s>>>(x, d32, sc, n);
 }
+
+__global__ void k_set_bb(PcgState* st, double bb, double delta2) {
+  st->bb = bb;
+  st->delta2 = delta2;
+}
+void launch_set_bb(PcgState* st, double bb, double delta2, cudaStream_t s) { k_set_bb<<<1, 1, 0, s>>>(st, bb, delta2); }
 
 __global__ void k_zero_f32(float* a, int64_t n) {
   GRID_STRIDE(q, n) a[q] = 0.f;

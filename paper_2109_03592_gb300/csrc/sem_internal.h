@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/sem.h"
+#include "kernels.h"
 
 namespace sem {
 
@@ -43,14 +44,20 @@ struct Topology {
 };
 sem_status build_numbering(int64_t E, int N, const int64_t* vert, Topology& t);
 
+// Gather-scatter plan.  Nodes with m > 1 copies, in ascending global id,
+// are grouped by m: for m = 2..8 (classes 0..6) each node is a fixed tuple
+// of its m local indices in ascending order; nodes with m > 8 form a CSR
+// class (7); Dirichlet nodes with a single copy form class 8 (one index
+// each).  Bit 31 of a node's first index flags a Dirichlet node.  Every
+// class starts at a multiple of 4 entries of `idx` (16-byte aligned).
+constexpr int kGsClasses = 9;
 struct GsPlan {
-  // Segments are the global nodes with more than one copy or on a Dirichlet
-  // face, in ascending global id.  seg_ptr[s]..seg_ptr[s+1] index seg_idx,
-  // which lists the segment's local points in ascending local index.
-  std::vector<int32_t> seg_ptr;
-  std::vector<int32_t> seg_idx;
-  std::vector<uint8_t> seg_dir;  // 1 if the node is Dirichlet
-  std::vector<uint8_t> wm;       // per local point: multiplicity | 0x80 if Dirichlet
+  std::vector<int32_t> idx;
+  std::vector<int32_t> gptr;             // CSR offsets (relative to the class start) of class 7
+  int64_t off[kGsClasses] = {0};         // class start in idx
+  int64_t cnt[kGsClasses] = {0};         // nodes per class
+  int64_t n_nodes = 0, n_points = 0;     // shared-or-Dirichlet nodes and their local points
+  std::vector<uint8_t> wm;               // per local point: multiplicity | 0x80 if Dirichlet
 };
 sem_status build_gs_plan(const Topology& t, const uint8_t* dirichlet_face, GsPlan& plan);
 
@@ -75,13 +82,14 @@ struct sem_mesh {
   double* B64 = nullptr;     // [E][n3]
   float* G32 = nullptr;      // [E][6][n3] round-to-nearest of G64 (the "hi" part)
   float* G32lo = nullptr;    // [E][6][n3] float(G64 - G32): G64 ~ G32 + G32lo to 2^-48
-  float* B32 = nullptr;      // [E][n3]
+  float* B32 = nullptr;      // [E][n3] round-to-nearest of B64
+  float* B32lo = nullptr;    // [E][n3] float(B64 - B32)
   double* dK = nullptr;      // [n_local] QQ^T diag of the stiffness (h1 = 1, h2 = 0)
   double* dB = nullptr;      // [n_local] QQ^T B
   uint8_t* wm = nullptr;     // [n_local] multiplicity | 0x80 Dirichlet
-  int32_t* seg_ptr = nullptr;
-  int32_t* seg_idx = nullptr;
-  uint8_t* seg_dir = nullptr;
+  int32_t* gs_idx = nullptr;   // GsPlan::idx
+  int32_t* gs_ptr = nullptr;   // GsPlan::gptr
+  int64_t gs_off[9] = {0}, gs_cnt[9] = {0};
   double* D64 = nullptr;     // [n*n] D (row i: d/dr at xi_i)
   float* D32 = nullptr;
   float* D32lo = nullptr;
@@ -96,3 +104,16 @@ struct sem_mesh {
   std::mutex ws_mutex;
   sem::Workspace* ws = nullptr;  // cached solver workspace
 };
+
+namespace sem {
+inline GsDev gs_dev(const sem_mesh* m) {
+  GsDev g;
+  g.idx = m->gs_idx;
+  g.gptr = m->gs_ptr;
+  for (int c = 0; c < 9; ++c) {
+    g.off[c] = m->gs_off[c];
+    g.cnt[c] = m->gs_cnt[c];
+  }
+  return g;
+}
+}  // namespace sem

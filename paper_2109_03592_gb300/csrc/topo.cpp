@@ -394,30 +394,56 @@ sem_status build_gs_plan(const Topology& t, const uint8_t* dface, GsPlan& plan) 
     if (m > 127) { set_error("gs plan: a node has more than 127 copies"); return SEM_ERR_BAD_MESH; }
     plan.wm[l] = (uint8_t)(m | (dir[t.glo[l]] ? 0x80 : 0));
   }
-  std::vector<int32_t> seg_of(t.n_global, -1);
-  int64_t nseg = 0, npts = 0;
-  for (int64_t g = 0; g < t.n_global; ++g)
-    if (count[g] > 1 || dir[g]) {
-      seg_of[g] = (int32_t)nseg++;
-      npts += count[g];
-    }
-  if (npts >= (1LL << 31) - 1 || t.n_local >= (1LL << 31) - 1) {
+  // class of every node: 0..6 for m = 2..8, 7 for m > 8, 8 for a Dirichlet singleton, -1 none
+  auto cls_of = [&](int64_t g) -> int {
+    const int32_t m = count[g];
+    if (m >= 2 && m <= 8) return m - 2;
+    if (m > 8) return 7;
+    return dir[g] ? 8 : -1;
+  };
+  int64_t entries[kGsClasses] = {0};
+  for (int64_t g = 0; g < t.n_global; ++g) {
+    const int c = cls_of(g);
+    if (c < 0) continue;
+    plan.cnt[c]++;
+    entries[c] += count[g];
+  }
+  int64_t total = 0;
+  for (int c = 0; c < kGsClasses; ++c) {
+    plan.off[c] = total;
+    total += (entries[c] + 3) / 4 * 4;
+    plan.n_nodes += plan.cnt[c];
+    plan.n_points += entries[c];
+  }
+  if (total >= (1LL << 31) - 1 || t.n_local >= (1LL << 31) - 1) {
     set_error("gs plan: more than 2^31 local points");
     return SEM_ERR_INVALID;
   }
-  plan.seg_ptr.assign(nseg + 1, 0);
-  plan.seg_dir.assign(nseg, 0);
-  for (int64_t g = 0; g < t.n_global; ++g)
-    if (seg_of[g] >= 0) {
-      plan.seg_ptr[seg_of[g] + 1] = count[g];
-      plan.seg_dir[seg_of[g]] = dir[g];
+  plan.idx.assign(total, 0);
+  plan.gptr.assign(plan.cnt[7] + 1, 0);
+  // position of each node's tuple, in ascending global id within its class
+  std::vector<int64_t> pos(t.n_global, -1);
+  int64_t fill[kGsClasses];
+  for (int c = 0; c < kGsClasses; ++c) fill[c] = plan.off[c];
+  int64_t gnode = 0;
+  for (int64_t g = 0; g < t.n_global; ++g) {
+    const int c = cls_of(g);
+    if (c < 0) continue;
+    pos[g] = fill[c];
+    fill[c] += count[g];
+    if (c == 7) {
+      plan.gptr[gnode + 1] = plan.gptr[gnode] + count[g];
+      ++gnode;
     }
-  for (int64_t s = 0; s < nseg; ++s) plan.seg_ptr[s + 1] += plan.seg_ptr[s];
-  std::vector<int32_t> fill(plan.seg_ptr.begin(), plan.seg_ptr.end() - 1);
-  plan.seg_idx.resize(npts);
+  }
+  // local points in ascending local index fill each tuple in ascending order
+  std::vector<int32_t> seen(t.n_global, 0);
   for (int64_t l = 0; l < t.n_local; ++l) {
-    const int32_t s = seg_of[t.glo[l]];
-    if (s >= 0) plan.seg_idx[fill[s]++] = (int32_t)l;
+    const int64_t g = t.glo[l];
+    if (pos[g] < 0) continue;
+    int32_t v = (int32_t)l;
+    if (seen[g] == 0 && dir[g]) v |= (int32_t)0x80000000u;
+    plan.idx[pos[g] + seen[g]++] = v;
   }
   return SEM_OK;
 }

@@ -45,7 +45,8 @@ class MeshInfo(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("h1", C.c_double), ("h2", C.c_double), ("inner_tol", C.c_double),
-                ("maxit", C.c_int), ("max_outer", C.c_int), ("prec", C.c_int)]
+                ("maxit", C.c_int), ("max_outer", C.c_int), ("prec", C.c_int), ("refine", C.c_int),
+                ("delta", C.c_double)]
 
 
 class SolveResult(C.Structure):
@@ -182,10 +183,11 @@ def make_desc(desc):
     return d, keep
 
 
-def _opts(tol=1e-10, h1=1.0, h2=0.0, prec=FP64, inner_tol=0.0, maxit=0, max_outer=0):
+def _opts(tol=1e-10, h1=1.0, h2=0.0, prec=FP64, inner_tol=0.0, maxit=0, max_outer=0, refine=0, delta=0.0):
     o = SolveOpts()
     o.tol, o.h1, o.h2, o.inner_tol = float(tol), float(h1), float(h2), float(inner_tol)
     o.maxit, o.max_outer, o.prec = int(maxit), int(max_outer), int(prec)
+    o.refine, o.delta = int(refine), float(delta)
     return o
 
 

@@ -33,7 +33,7 @@ def _pipe_near(E):
     best = None
     for nc, nr in _PIPE_XS:
         per = nc * (nc + 4 * nr)
-        nzp = max(2, round(E / per))
+        nzp = max(3, round(E / per))
         err = abs(math.log(per * nzp / E))
         if best is None or err < best[0]:
             best = (err, dict(kind="pipe", nc=nc, nr=nr, nzp=nzp, R=1.0, L=8.0, a=0.5, beta=2.0, periodic=True))

@@ -260,3 +260,28 @@ def test_ax_fp64_both_kernels(kernel, name, monkeypatch):
     x = torch.zeros(m.shape, dtype=torch.float64, device="cuda")
     res = m.solve(to_gpu(b), x, tol=1e-10)
     assert res["status"] == 0 and _residual(P, b, x.cpu().numpy()) <= 1.1e-10
+
+
+@pytest.mark.parametrize("refine", [0, 1])
+@pytest.mark.parametrize("name,h2", [("pipe_n5", 0.0), ("box4_n7", 0.0), ("pipe_open_n4", 1.5)])
+def test_mixed_variants_match_oracle(refine, name, h2):
+    """Reliable updates (refine=0, the default) and restarted refinement
+    (refine=1) against the oracle's versions of the same algorithms."""
+    import torch
+    import paper_2109_03592_gb300 as sem
+    m, _ = setup(name)
+    P = solver.Problem(_oracle_mesh(CASES[name]), 1.0, h2)
+    b = P.rhs(forcing.evaluate(P.mesh.xyz, forcing.random_modes(12, L=2.0)))
+    if refine == 0:
+        ref = solver.pcg_mixed_reliable(P, b, tol=1e-10)
+    else:
+        ref = solver.pcg_mixed(P, b, tol=1e-10, inner_tol=1e-4)
+    x = torch.zeros(m.shape, dtype=torch.float64, device="cuda")
+    res = m.solve(to_gpu(b), x, tol=1e-10, h1=1.0, h2=h2, prec=sem.MIXED, refine=refine, inner_tol=1e-4)
+    assert res["status"] == 0, res
+    assert _residual(P, b, x.cpu().numpy()) <= 1e-10
+    # FP32 rounding differs between numpy and the GPU: counts agree to ~10%
+    assert abs(res["iters"] - ref.iters) <= 0.1 * ref.iters + 3, (res, ref.iters)
+    fp64 = solver.pcg(P, b, tol=1e-10)
+    if refine == 0:
+        assert res["iters"] <= 1.3 * fp64.iters + 5

@@ -87,3 +87,22 @@ def test_mixed_precision_refinement(inner_tol):
     err = np.sqrt(P.dot(res.x - ref, res.x - ref) / P.dot(ref, ref))
     assert err < 1e-8
     assert res.outer_iters >= 2  # FP32 alone cannot reach 1e-10
+
+
+def test_mixed_reliable_updates():
+    m = mesh.pipe(2, 1, 3, 5, L=2.0)
+    P = solver.Problem(m, 1.0, 0.3)
+    b = P.rhs(forcing.evaluate(m.xyz, forcing.random_modes(4, L=2.0)))
+    ref = solver.pcg(P, b, tol=1e-10)
+    res = solver.pcg_mixed_reliable(P, b, tol=1e-10)
+    assert res.status == solver.CONVERGED
+    r = b - P.A(res.x)
+    assert np.sqrt(P.dot(r, r) / P.dot(b, b)) <= 1e-10
+    # keeping the Krylov direction: close to the FP64 iteration count, far
+    # below restarted refinement
+    assert res.iters <= 1.25 * ref.iters + 5, (res.iters, ref.iters)
+    restarted = solver.pcg_mixed(P, b, tol=1e-10, inner_tol=1e-4)
+    assert res.iters < restarted.iters
+    assert res.outer_iters >= 2
+    err = np.sqrt(P.dot(res.x - ref.x, res.x - ref.x) / P.dot(ref.x, ref.x))
+    assert err < 1e-8
