@@ -285,6 +285,19 @@ sem_status sem_mesh_vertices(const sem_mesh_desc* desc, int64_t* vert_host, int6
  * creation: 1 = double-float (FP32-pair) arithmetic, 0 = native FP64. */
 int sem_mesh_fp64_kernel(const sem_mesh* mesh);
 
+/* Local-operator kernel variant the autotuner chose for `prec` (SEM_FP64
+ * or SEM_FP32): 0 / 1 register kernels with ~256 / ~128 threads per CTA,
+ * 2 / 3 (FP32) persistent kernels fed by bulk copies into a shared-memory
+ * ring.  -1 for a bad argument. */
+int sem_mesh_ax_variant(const sem_mesh* mesh, sem_prec prec);
+
+/* Synchronise `stream` and report whether a local-operator kernel launched
+ * on this mesh gave up a bounded device-side wait (the bulk-copy pipelined
+ * kernels wait on shared-memory barriers with an iteration limit):
+ * SEM_ERR_DEVICE_TIMEOUT if so (the affected output is invalid; the flag is
+ * cleared), else SEM_OK.  Solves report such a timeout in their status. */
+sem_status sem_mesh_check(const sem_mesh* mesh, void* stream);
+
 /* Number of CUDA kernels the library has launched in this process (a graph
  * replay counts each of its kernel nodes).  Monotone; thread-safe. */
 uint64_t sem_kernel_launches(void);

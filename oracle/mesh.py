@@ -49,13 +49,14 @@ def _lerp(a, b, xi):
     return a * (1.0 - xi) * 0.5 + b * (1.0 + xi) * 0.5
 
 
-def box(nx, ny, nz, N, lx=1.0, ly=1.0, lz=1.0):
+def box(nx, ny, nz, N, lx=1.0, ly=1.0, lz=1.0, elements=None):
     """Affine box [0,lx]x[0,ly]x[0,lz] with nx*ny*nz elements, element index
-    e = ex + nx (ey + ny ez), Dirichlet on all six faces."""
+    e = ex + nx (ey + ny ez), Dirichlet on all six faces.  ``elements``
+    (optional index array) builds only those elements, in that order."""
     xi, _ = gll.nodes_weights(N)
     n = N + 1
-    E = nx * ny * nz
-    e = np.arange(E)
+    e = np.arange(nx * ny * nz) if elements is None else np.asarray(elements)
+    E = e.size
     ex, ey, ez = e % nx, (e // nx) % ny, e // (nx * ny)
     x = _lerp((lx * ex / nx)[:, None], (lx * (ex + 1) / nx)[:, None], xi[None, :])  # [E, n] over i
     y = _lerp((ly * ey / ny)[:, None], (ly * (ey + 1) / ny)[:, None], xi[None, :])  # over j
@@ -91,7 +92,7 @@ def _rotate(px, py, q):
     return py, -px
 
 
-def pipe(nc, nr, nzp, N, R=1.0, L=8.0, a=None, beta=2.0, periodic=True):
+def pipe(nc, nr, nzp, N, R=1.0, L=8.0, a=None, beta=2.0, periodic=True, elements=None):
     """O-grid straight pipe of radius R and length L (see module docstring).
 
     Element order: e = layer * n2d + e2d, n2d = nc (nc + 4 nr).  In a layer the
@@ -100,7 +101,8 @@ def pipe(nc, nr, nzp, N, R=1.0, L=8.0, a=None, beta=2.0, periodic=True):
     tangential and r the radial index; local i runs outward (t), j along the
     tangential coordinate s, which keeps every element right-handed).  Local k
     runs along z.  Dirichlet: the wall face (i = N of the outermost ring), and
-    the end caps when the pipe is not periodic.
+    the end caps when the pipe is not periodic.  ``elements`` (optional index
+    array) builds only those elements, in that order.
     """
     if a is None:
         a = 0.5 * R
@@ -131,8 +133,10 @@ def pipe(nc, nr, nzp, N, R=1.0, L=8.0, a=None, beta=2.0, periodic=True):
                 py = (1.0 - t) * a * s + t * R * np.sin(th)
                 xy[e2, 0], xy[e2, 1] = _rotate(px, py, q)
                 wall[e2] = r == nr - 1
-    layer = np.arange(E) // n2d
-    e2d = np.arange(E) % n2d
+    eidx = np.arange(E) if elements is None else np.asarray(elements)
+    E = eidx.size
+    layer = eidx // n2d
+    e2d = eidx % n2d
     z = _lerp((L * layer / nzp)[:, None], (L * (layer + 1) / nzp)[:, None], xi[None, :])  # [E, k]
     xyz = np.empty((E, 3, n, n, n))
     xyz[:, 0] = xy[e2d, 0][:, None, :, :]

@@ -60,6 +60,7 @@ void free_mesh_arrays(sem_mesh* m) {
   dev_free(m->gs_idx);
   dev_free(m->gs_ptr);
   dev_free(m->D64);
+  dev_free(m->dev_err);
   dev_free(m->D32);
   dev_free(m->D32lo);
 }
@@ -120,6 +121,7 @@ sem_status build_mesh(const sem_mesh_desc& d, cudaStream_t s, sem_mesh* m) {
   SEM_TRY(dev_alloc(&m->gs_idx, plan.idx.size(), tb));
   SEM_TRY(dev_alloc(&m->gs_ptr, plan.gptr.size(), tb));
   SEM_TRY(dev_alloc(&m->D64, n * n, tb));
+  SEM_TRY(dev_alloc(&m->dev_err, 1, tb));
   SEM_TRY(dev_alloc(&m->D32, n * n, tb));
   SEM_TRY(dev_alloc(&m->D32lo, n * n, tb));
 
@@ -148,6 +150,7 @@ sem_status build_mesh(const sem_mesh_desc& d, cudaStream_t s, sem_mesh* m) {
   SEM_CUDA(cudaMemcpyAsync(m->D32, D32.data(), n * n * sizeof(float), cudaMemcpyHostToDevice, s));
   SEM_CUDA(cudaMemcpyAsync(m->D32lo, D32lo.data(), n * n * sizeof(float), cudaMemcpyHostToDevice, s));
   SEM_CUDA(cudaMemsetAsync(bad_d, 0, sizeof(int), s));
+  SEM_CUDA(cudaMemsetAsync(m->dev_err, 0, sizeof(int), s));
   SEM_CUDA(cudaMemcpyAsync(m->wm, plan.wm.data(), P, cudaMemcpyHostToDevice, s));
   if (!plan.idx.empty())
     SEM_CUDA(cudaMemcpyAsync(m->gs_idx, plan.idx.data(), plan.idx.size() * 4, cudaMemcpyHostToDevice, s));
@@ -199,6 +202,31 @@ const char* sem_last_error(void) { return g_last_error.c_str(); }
 int sem_version(void) { return 1; }
 
 int sem_mesh_fp64_kernel(const sem_mesh* m) { return m ? m->fp64_df : -1; }
+
+int sem_mesh_ax_variant(const sem_mesh* m, sem_prec prec) {
+  if (!m) return -1;
+  if (prec == SEM_FP64) return m->fp64_df ? m->ax_var[2] : m->ax_var[0];
+  if (prec == SEM_FP32) return m->ax_var[1];
+  return -1;
+}
+
+sem_status sem_mesh_check(const sem_mesh* m, void* stream) {
+  if (!m) {
+    set_error("sem_mesh_check: null mesh");
+    return SEM_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int err = 0;
+  SEM_CUDA(cudaMemcpyAsync(&err, m->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA(cudaStreamSynchronize(s));
+  if (err) {
+    SEM_CUDA(cudaMemsetAsync(m->dev_err, 0, sizeof(int), s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    set_error("a bounded device-side wait of a local-operator kernel gave up; its output is invalid");
+    return SEM_ERR_DEVICE_TIMEOUT;
+  }
+  return SEM_OK;
+}
 
 uint64_t sem_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 

@@ -252,6 +252,7 @@ constexpr int epb_df(int N, int variant) {
 
 template <int N>
 inline cudaError_t dispatch_df_n(int variant, bool fused, const AxDFParams& p, cudaStream_t s, int* grid_out) {
+  if (variant >= 2) return cudaErrorNotSupported;
   if (variant == 0)
     return fused ? launch_df_t<N, epb_df(N, 0), true>(p, s, grid_out)
                  : launch_df_t<N, epb_df(N, 0), false>(p, s, grid_out);

@@ -37,10 +37,10 @@ cudaError_t ax64_n11(int, bool, const AxParams<double>&, cudaStream_t, int*);
 cudaError_t ax32_n11(int, bool, const AxParams<float>&, cudaStream_t, int*);
 cudaError_t axdf_n11(int, bool, const AxDFParams&, cudaStream_t, int*);
 
-int ax_num_variants() { return 2; }
+int ax_num_variants() { return 4; }
 
 int ax_elems_per_block(int N, int variant) {
-  const int t = variant == 0 ? 256 : 128, per = (N + 1) * (N + 1);
+  const int t = (variant == 0 || variant == 3) ? 256 : 128, per = (N + 1) * (N + 1);
   return t / per < 1 ? 1 : t / per;
 }
 

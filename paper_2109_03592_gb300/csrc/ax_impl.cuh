@@ -16,6 +16,9 @@
 // back-contractions instead of to wr, ws, wt.
 #pragma once
 
+#include <type_traits>
+
+#include "ax_tma.cuh"
 #include "kernels.h"
 
 namespace sem {
@@ -161,6 +164,17 @@ constexpr int epb_for(int N, int variant) {
 
 template <typename T, int N>
 cudaError_t dispatch_ax_n(int variant, bool fused, const AxParams<T>& p, cudaStream_t s, int* grid_out) {
+  if (variant >= 2) {
+    if constexpr (std::is_same<T, float>::value && (N % 2 == 1)) {
+      if (variant == 2)
+        return fused ? tma::launch_ax_tma_t<N, epb_for(N, 1), 3, true>(p, p.err, s, grid_out)
+                     : tma::launch_ax_tma_t<N, epb_for(N, 1), 3, false>(p, p.err, s, grid_out);
+      if (variant == 3)
+        return fused ? tma::launch_ax_tma_t<N, epb_for(N, 0), 2, true>(p, p.err, s, grid_out)
+                     : tma::launch_ax_tma_t<N, epb_for(N, 0), 2, false>(p, p.err, s, grid_out);
+    }
+    return cudaErrorNotSupported;
+  }
   if (variant == 0) {
     return fused ? launch_ax_t<N, T, epb_for(N, 0), true>(p, s, grid_out)
                  : launch_ax_t<N, T, epb_for(N, 0), false>(p, s, grid_out);

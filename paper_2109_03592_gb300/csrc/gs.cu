@@ -2,10 +2,10 @@
 // "exchange of element face values" between neighbouring elements), then the
 // Dirichlet mask.
 //
-// One thread per node.  Nodes are grouped by their number of copies m: for
-// m = 2..8 a node is a fixed tuple of m local indices (ascending), so a
-// thread loads its tuple and then the values -- one dependent step, no
-// segment-pointer stream.  Nodes with more copies use a CSR class; Dirichlet
+// Nodes are grouped by their number of copies m: for m = 2..8 a node is a
+// fixed tuple of m local indices (ascending), so a thread loads its tuples
+// and then the values -- one dependent step, no segment-pointer stream --
+// for several nodes at once.  Nodes with more copies use a CSR class; Dirichlet
 // nodes with a single copy only need zeroing.  The copies are summed in
 // ascending local index, left to right, with explicit round-to-nearest adds
 // (no contraction, no reordering), so the result is bit-identical to the
@@ -24,26 +24,49 @@ struct GsLaunch {
   int64_t blk[10];  // first block of each class; blk[9] = grid size
 };
 
-template <typename T, int M>
-__device__ __forceinline__ void gs_tuple(T* __restrict__ v, const int32_t* __restrict__ id, int apply_mask) {
-  int32_t ix[M];
+// Nodes per thread of class m: several independent nodes per thread keep
+// more loads in flight (the kernel is bound by load latency, not bandwidth).
+__host__ __device__ constexpr int gs_npt(int M) { return M <= 2 ? 4 : (M <= 4 ? 2 : 1); }
+
+// NPT nodes of m = M copies each: node q at id + q * stride * M.
+template <typename T, int M, int NPT>
+__device__ __forceinline__ void gs_tuples(T* __restrict__ v, const int32_t* __restrict__ id, int64_t first_node,
+                                          int64_t count, int apply_mask) {
+  int32_t ix[NPT][M];
+  bool ok[NPT];
 #pragma unroll
-  for (int c = 0; c < M; ++c) ix[c] = id[c];
-  const bool dir = ix[0] < 0;
-  ix[0] &= 0x7fffffff;
-  if (apply_mask && dir) {
+  for (int q = 0; q < NPT; ++q) {
+    const int64_t node = first_node + (int64_t)q * kGsThreads;
+    ok[q] = node < count;
+    if (ok[q]) {
 #pragma unroll
-    for (int c = 0; c < M; ++c) v[ix[c]] = T(0);
-    return;
+      for (int c = 0; c < M; ++c) ix[q][c] = id[node * M + c];
+    }
   }
-  T val[M];
+  T val[NPT][M];
 #pragma unroll
-  for (int c = 0; c < M; ++c) val[c] = v[ix[c]];
-  T acc = val[0];
+  for (int q = 0; q < NPT; ++q) {
+    if (!ok[q]) continue;
+    const bool dir = ix[q][0] < 0;
+    ix[q][0] &= 0x7fffffff;
+    if (apply_mask && dir) {
+      ok[q] = false;
 #pragma unroll
-  for (int c = 1; c < M; ++c) acc = add_rn(acc, val[c]);
+      for (int c = 0; c < M; ++c) v[ix[q][c]] = T(0);
+      continue;
+    }
 #pragma unroll
-  for (int c = 0; c < M; ++c) v[ix[c]] = acc;
+    for (int c = 0; c < M; ++c) val[q][c] = v[ix[q][c]];
+  }
+#pragma unroll
+  for (int q = 0; q < NPT; ++q) {
+    if (!ok[q]) continue;
+    T acc = val[q][0];
+#pragma unroll
+    for (int c = 1; c < M; ++c) acc = add_rn(acc, val[q][c]);
+#pragma unroll
+    for (int c = 0; c < M; ++c) v[ix[q][c]] = acc;
+  }
 }
 
 template <typename T>
@@ -53,18 +76,26 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(T* __restrict__ v, const GsLa
   const int64_t b = blockIdx.x;
   int c = 0;
   while (c < 8 && b >= L.blk[c + 1]) ++c;
-  const int64_t t = (b - L.blk[c]) * kGsThreads + threadIdx.x;
-  if (t >= L.g.cnt[c]) return;
+  const int64_t rel = b - L.blk[c];
   const int32_t* base = L.g.idx + L.g.off[c];
+  const int64_t cnt = L.g.cnt[c];
+#define GS_CASE(CLS, M)                                                                             \
+  case CLS: {                                                                                       \
+    constexpr int NPT = gs_npt(M);                                                                  \
+    gs_tuples<T, M, NPT>(v, base, rel * kGsThreads * NPT + threadIdx.x, cnt, apply_mask);           \
+    break;                                                                                          \
+  }
   switch (c) {
-    case 0: gs_tuple<T, 2>(v, base + 2 * t, apply_mask); break;
-    case 1: gs_tuple<T, 3>(v, base + 3 * t, apply_mask); break;
-    case 2: gs_tuple<T, 4>(v, base + 4 * t, apply_mask); break;
-    case 3: gs_tuple<T, 5>(v, base + 5 * t, apply_mask); break;
-    case 4: gs_tuple<T, 6>(v, base + 6 * t, apply_mask); break;
-    case 5: gs_tuple<T, 7>(v, base + 7 * t, apply_mask); break;
-    case 6: gs_tuple<T, 8>(v, base + 8 * t, apply_mask); break;
+    GS_CASE(0, 2)
+    GS_CASE(1, 3)
+    GS_CASE(2, 4)
+    GS_CASE(3, 5)
+    GS_CASE(4, 6)
+    GS_CASE(5, 7)
+    GS_CASE(6, 8)
     case 7: {  // more than 8 copies
+      const int64_t t = rel * kGsThreads + threadIdx.x;
+      if (t >= cnt) break;
       const int32_t b0 = L.g.gptr[t], e0 = L.g.gptr[t + 1];
       const int32_t first = base[b0];
       const bool dir = first < 0;
@@ -79,10 +110,13 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(T* __restrict__ v, const GsLa
       for (int32_t q = b0 + 1; q < e0; ++q) v[base[q]] = acc;
       break;
     }
-    default:  // Dirichlet node with one copy
-      if (apply_mask) v[base[t] & 0x7fffffff] = T(0);
+    default: {  // Dirichlet node with one copy
+      const int64_t t = rel * kGsThreads + threadIdx.x;
+      if (t < cnt && apply_mask) v[base[t] & 0x7fffffff] = T(0);
       break;
+    }
   }
+#undef GS_CASE
 }
 
 template <typename T>
@@ -92,7 +126,8 @@ cudaError_t launch_gs(T* v, const GsDev& g, int apply_mask, const PcgState* st, 
   int64_t nb = 0;
   for (int c = 0; c < 9; ++c) {
     L.blk[c] = nb;
-    nb += (g.cnt[c] + kGsThreads - 1) / kGsThreads;
+    const int64_t per_block = (int64_t)kGsThreads * (c < 7 ? gs_npt(c + 2) : 1);
+    nb += (g.cnt[c] + per_block - 1) / per_block;
   }
   L.blk[9] = nb;
   if (nb == 0) return cudaSuccess;

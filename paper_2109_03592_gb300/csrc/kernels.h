@@ -39,6 +39,7 @@ struct AxParams {
   T* p;
   PcgState* st;
   double* partial;   // [gridDim.x]
+  int* err;          // device error word (bounded-wait timeouts of the bulk-copy kernels)
 };
 
 // Double-float (FP32 pair) FP64-accurate variant: G = Ghi + Glo, D = Dhi + Dlo,
@@ -61,8 +62,11 @@ struct AxDFParams {
   double* partial;
 };
 
-// Kernel variants of the local operator for one (N, precision); `variant`
-// indexes an elements-per-block choice (see ax_variants()).
+// Kernel variants of the local operator for one (N, precision): 0 and 1 are
+// the register/shared-memory kernels with ~256 / ~128 threads per CTA; 2 and
+// 3 (FP32, even n only) the persistent bulk-copy pipelined kernels with
+// ~128 threads x 3 stages / ~256 threads x 2 stages.  A launch of a variant
+// that does not exist for (N, precision) returns cudaErrorNotSupported.
 int ax_num_variants();
 int ax_elems_per_block(int N, int variant);
 cudaError_t launch_ax_f64(int N, int variant, bool fused, const AxParams<double>& p, cudaStream_t s, int* grid_out);

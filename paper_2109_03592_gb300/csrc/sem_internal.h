@@ -90,6 +90,7 @@ struct sem_mesh {
   int32_t* gs_idx = nullptr;   // GsPlan::idx
   int32_t* gs_ptr = nullptr;   // GsPlan::gptr
   int64_t gs_off[9] = {0}, gs_cnt[9] = {0};
+  int* dev_err = nullptr;    // device error word of the bulk-copy kernels (0 = ok)
   double* D64 = nullptr;     // [n*n] D (row i: d/dr at xi_i)
   float* D32 = nullptr;
   float* D32lo = nullptr;
@@ -99,7 +100,7 @@ struct sem_mesh {
   // and whether FP64 requests run the double-float kernel.
   int ax_var[3] = {0, 0, 0};
   int fp64_df = 0;
-  float ax_ms[3][2] = {{0}};
+  float ax_ms[3][4] = {{0}};
 
   std::mutex ws_mutex;
   sem::Workspace* ws = nullptr;  // cached solver workspace

@@ -18,6 +18,7 @@
 // thread and FP64 across threads), and the FP32 correction is added to x in
 // FP64; repeated until the FP64 residual meets the tolerance.
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <functional>
@@ -121,8 +122,12 @@ static cudaError_t ax64(const sem_mesh* m, const double* u, double* w, double h1
 
 static cudaError_t ax32(const sem_mesh* m, const float* u, float* w, double h1, double h2, bool fused,
                         const float* z, float* p, PcgState* st, double* part, cudaStream_t s) {
-  AxParams<float> a{u, w, m->G32, m->B32, m->D32, (float)h1, (float)h2, h2 != 0.0, m->E, z, p, st, part};
-  return launch_ax_f32(m->N, m->ax_var[1], fused, a, s, nullptr);
+  AxParams<float> a{u, w, m->G32, m->B32, m->D32, (float)h1, (float)h2, h2 != 0.0, m->E, z, p, st, part, m->dev_err};
+  int var = m->ax_var[1];
+  // the bulk-copy kernels read u with 16-byte aligned copies: a caller's
+  // unaligned u takes the faster of the register kernels instead
+  if (var >= 2 && u && ((uintptr_t)u & 15u)) var = m->ax_ms[1][1] < m->ax_ms[1][0] ? 1 : 0;
+  return launch_ax_f32(m->N, var, fused, a, s, nullptr);
 }
 
 sem_status apply_local(const sem_mesh* m, const void* u, void* w, double h1, double h2, sem_prec prec,
@@ -157,7 +162,7 @@ struct TuneKey {
 struct TuneVal {
   int var[3];
   int df;
-  float ms[3][2];
+  float ms[3][4];
 };
 std::mutex g_tune_mutex;
 std::vector<std::pair<TuneKey, TuneVal>> g_tune;
@@ -185,7 +190,7 @@ static sem_status autotune_measure(sem_mesh* m, cudaStream_t s) {
           err = launch_ax_f64(m->N, v, false, pa, s, nullptr);
         } else if (kind == 1) {
           AxParams<float> pa{m->B32, (float*)w, m->G32, m->B32, m->D32, 1.f, 0.f, 0, m->E,
-                             nullptr, nullptr, nullptr, nullptr};
+                             nullptr, nullptr, nullptr, nullptr, m->dev_err};
           err = launch_ax_f32(m->N, v, false, pa, s, nullptr);
         } else {
           AxDFParams pa{m->B64, w, m->G32, m->G32lo, m->B32, m->B32lo, m->D32, m->D32lo, 1.0, 0.0, 0, m->E,
@@ -193,12 +198,14 @@ static sem_status autotune_measure(sem_mesh* m, cudaStream_t s) {
           err = launch_ax_df(m->N, v, false, pa, s, nullptr);
         }
         cudaEventRecord(b, s);
+        if (err == cudaErrorNotSupported) break;  // no such variant for this (N, precision)
         count_launches(1);
         if (err == cudaSuccess) err = cudaEventSynchronize(b);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, a, b);
         if (rep > 0) total += ms;  // first run is a warm-up
       }
+      if (err == cudaErrorNotSupported) continue;
       if (err != cudaSuccess) {
         status = cuda_fail(err, "autotune");
         break;
@@ -220,7 +227,8 @@ static sem_status autotune_measure(sem_mesh* m, cudaStream_t s) {
 // Times every elements-per-block variant of the FP64, FP32 and double-float
 // local operator on this mesh (the mesh's own factors as input) and keeps
 // the fastest; FP64 requests use the double-float kernel when it is faster.
-// SEM_FP64_KERNEL=native|df forces the FP64 choice.
+// SEM_FP64_KERNEL=native|df forces the FP64 choice and SEM_FP32_VARIANT=v
+// an FP32 variant that exists for this order.
 sem_status autotune_mesh(sem_mesh* m, cudaStream_t s) {
   int lg = 0;
   while ((1LL << (lg + 1)) <= m->E) ++lg;
@@ -249,6 +257,10 @@ forced:
   if (const char* f = std::getenv("SEM_FP64_KERNEL")) {
     if (!std::strcmp(f, "native")) m->fp64_df = 0;
     if (!std::strcmp(f, "df") && ax_df_available(m->N)) m->fp64_df = 1;
+  }
+  if (const char* f = std::getenv("SEM_FP32_VARIANT")) {
+    const int v = std::atoi(f);
+    if (v >= 0 && v < ax_num_variants() && m->ax_ms[1][v] > 0.f) m->ax_var[1] = v;
   }
   return SEM_OK;
 }

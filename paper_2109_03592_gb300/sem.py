@@ -100,6 +100,8 @@ SIGNATURES = {
     "sem_version": (C.c_int, []),
     "sem_kernel_launches": (C.c_uint64, []),
     "sem_mesh_fp64_kernel": (C.c_int, [_P]),
+    "sem_mesh_check": (C.c_int, [_P, _P]),
+    "sem_mesh_ax_variant": (C.c_int, [_P, C.c_int]),
 }
 
 _lib = None
@@ -220,6 +222,14 @@ class Mesh:
     def fp64_double_float(self):
         """True if FP64 requests on this mesh run the double-float kernel."""
         return bool(lib().sem_mesh_fp64_kernel(self._h))
+
+    def check(self, stream=None):
+        """sem_mesh_check: raise if a bounded device-side wait gave up."""
+        _check(lib().sem_mesh_check(self._h, _stream(stream)), "sem_mesh_check")
+
+    def ax_variant(self, prec=FP32):
+        """Kernel variant the autotuner chose for `prec` (0/1 register kernels, 2/3 bulk-copy pipelined)."""
+        return int(lib().sem_mesh_ax_variant(self._h, int(prec)))
 
     def global_ids(self):
         out = np.empty(self.n_local, dtype=np.int64)

@@ -285,3 +285,47 @@ def test_mixed_variants_match_oracle(refine, name, h2):
     fp64 = solver.pcg(P, b, tol=1e-10)
     if refine == 0:
         assert res["iters"] <= 1.3 * fp64.iters + 5
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("name", ["box_ragged_n7", "pipe_n5", "pipe_n11", "box4_n7", "box_n1"])
+def test_fp32_variants(variant, name, monkeypatch):
+    """Every FP32 local-operator variant (register kernels 0/1, bulk-copy
+    pipelined kernels 2/3 for even n) against the oracle, plain and inside
+    the fused CG iteration (mixed-precision solve)."""
+    import torch
+    import paper_2109_03592_gb300 as sem
+    monkeypatch.setenv("SEM_FP32_VARIANT", str(variant))
+    m = sem.Mesh(CASES[name])
+    if m.ax_variant(sem.FP32) != variant:
+        assert variant >= 2 and m.n % 2 == 1  # bulk-copy kernels exist for even n only
+        pytest.skip("variant not available for odd n")
+    _, P = setup(name)
+    u = vectors.local_field(41, m.E, m.n, np.float32)
+    w = torch.empty(m.shape, dtype=torch.float32, device="cuda")
+    for h1, h2 in [(1.0, 0.0), (0.4, 3.0)]:
+        m.ax(to_gpu(u), w, h1, h2, prec=sem.FP32)
+        m.check()
+        ref = operator.ax_local(u.astype(np.float64), P.G, P.B, P.D, h1, h2)
+        assert relerr(w.cpu().numpy().astype(np.float64), ref) < AX32_TOL
+    b = P.rhs(forcing.evaluate(P.mesh.xyz, forcing.random_modes(4, L=3.0)))
+    x = torch.zeros(m.shape, dtype=torch.float64, device="cuda")
+    res = m.solve(to_gpu(b), x, tol=1e-10, prec=sem.MIXED)
+    assert res["status"] == 0 and _residual(P, b, x.cpu().numpy()) <= 1e-10
+
+
+def test_fp32_bulk_copy_kernel_unaligned_input():
+    """A caller's u that is not 16-byte aligned falls back to a register kernel."""
+    import torch
+    import paper_2109_03592_gb300 as sem
+    m, P = setup("box4_n7")
+    u = vectors.local_field(43, m.E, m.n, np.float32)
+    buf = torch.zeros(u.size + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = to_gpu(u).reshape(-1)
+    uu = buf[1:]
+    assert uu.data_ptr() % 16 != 0
+    w = torch.empty(u.size, dtype=torch.float32, device="cuda")
+    m.ax(uu, w, 1.0, 0.0, prec=sem.FP32)
+    m.check()
+    ref = operator.ax_local(u.astype(np.float64), P.G, P.B, P.D)
+    assert relerr(w.cpu().numpy().reshape(u.shape).astype(np.float64), ref) < AX32_TOL
