@@ -31,12 +31,18 @@ def reference_gradient(D, f):
 
 
 def jacobian(mesh):
-    """J[e, k, j, i, a, b] = d x_a / d r_b at every GLL point."""
+    """J[e, k, j, i, a, b] = d x_a / d r_b at every GLL point.
+
+    D applied to the coordinates relative to the element's first node: D
+    annihilates constants, so this is the same J, without the O(|x|/h)
+    cancellation that absolute coordinates cause for small elements far
+    from the origin."""
     D = gll.derivative_matrix(mesh.N)
     E, n = mesh.E, mesh.n
     J = np.empty((E, n, n, n, 3, 3))
     for a in range(3):
-        fr, fs, ft = reference_gradient(D, mesh.xyz[:, a])
+        x = mesh.xyz[:, a] - mesh.xyz[:, a, :1, :1, :1]
+        fr, fs, ft = reference_gradient(D, x)
         J[..., a, 0] = fr
         J[..., a, 1] = fs
         J[..., a, 2] = ft

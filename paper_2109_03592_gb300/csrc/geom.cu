@@ -75,7 +75,9 @@ __global__ void k_geometry(const double* __restrict__ xyz, double* __restrict__ 
   const int n3 = n * n * n;
   const int64_t e = blockIdx.x;
   if (e >= E) return;
-  for (int q = threadIdx.x; q < 3 * n3; q += blockDim.x) sx[q] = xyz[e * 3 * n3 + q];
+  // coordinates relative to the element's first node: D annihilates constants,
+  // and this avoids cancelling O(|x|) terms into an O(h) derivative
+  for (int q = threadIdx.x; q < 3 * n3; q += blockDim.x) sx[q] = xyz[e * 3 * n3 + q] - xyz[e * 3 * n3 + (q / n3) * n3];
   __syncthreads();
   for (int p = threadIdx.x; p < n3; p += blockDim.x) {
     const int i = p % n, j = (p / n) % n, k = p / (n * n);

@@ -10,6 +10,8 @@
 // ascending local index, left to right, with explicit round-to-nearest adds
 // (no contraction, no reordering), so the result is bit-identical to the
 // same sum written as a plain loop.
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace sem {
@@ -24,9 +26,31 @@ struct GsLaunch {
   int64_t blk[10];  // first block of each class; blk[9] = grid size
 };
 
-// Nodes per thread of class m: several independent nodes per thread keep
-// more loads in flight (the kernel is bound by load latency, not bandwidth).
-__host__ __device__ constexpr int gs_npt(int M) { return M <= 2 ? 4 : (M <= 4 ? 2 : 1); }
+// Nodes per thread of class m (one: more nodes per thread throttled the
+// load/store queue on GB300 and ran slower).
+__host__ __device__ constexpr int gs_npt(int) { return 1; }
+
+// The m indices of one node; tuples of 2, 4, 6 and 8 are 8-byte aligned
+// (every class starts 16-byte aligned) and load as int2 / int4 vectors.
+template <int M>
+__device__ __forceinline__ void load_tuple(const int32_t* __restrict__ id, int32_t (&ix)[M]) {
+  if constexpr (M % 4 == 0) {
+#pragma unroll
+    for (int c = 0; c < M; c += 4) {
+      const int4 q = *reinterpret_cast<const int4*>(id + c);
+      ix[c] = q.x; ix[c + 1] = q.y; ix[c + 2] = q.z; ix[c + 3] = q.w;
+    }
+  } else if constexpr (M % 2 == 0) {
+#pragma unroll
+    for (int c = 0; c < M; c += 2) {
+      const int2 q = *reinterpret_cast<const int2*>(id + c);
+      ix[c] = q.x; ix[c + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < M; ++c) ix[c] = id[c];
+  }
+}
 
 // NPT nodes of m = M copies each: node q at id + q * stride * M.
 template <typename T, int M, int NPT>
@@ -38,10 +62,7 @@ __device__ __forceinline__ void gs_tuples(T* __restrict__ v, const int32_t* __re
   for (int q = 0; q < NPT; ++q) {
     const int64_t node = first_node + (int64_t)q * kGsThreads;
     ok[q] = node < count;
-    if (ok[q]) {
-#pragma unroll
-      for (int c = 0; c < M; ++c) ix[q][c] = id[node * M + c];
-    }
+    if (ok[q]) load_tuple<M>(id + node * M, ix[q]);
   }
   T val[NPT][M];
 #pragma unroll
