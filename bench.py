@@ -182,6 +182,46 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- serving leg
+
+def serving_stream(count, rate, seed=4):
+    """Request stream through the batching server: Poisson arrivals at `rate`
+    per second; box or pipe meshes with E log-uniform in [512, 4096]; N in
+    {5, 7, 9}; Poisson or Helmholtz (h2 log-uniform in [1e-2, 1e2]); mixed
+    precision to 1e-10.  Latency = submit -> result visible to poll."""
+    import numpy as np
+    import paper_2109_03592_gb300 as sem
+    from sem_inputs import serving
+    stream = serving.request_stream(seed=seed, count=count, rate=rate, log2_e=(9.0, 12.0))
+    srv = sem.Server(max_slots=8)
+    pending = {}
+    t0 = time.perf_counter()
+    for req in stream:
+        now = time.perf_counter() - t0
+        if req["arrival"] > now:
+            time.sleep(req["arrival"] - now)
+        d = req["desc"]
+        n = d["N"] + 1
+        E = d["nx"] * d["ny"] * d["nz"] if d["kind"] == "box" else d["nc"] * (d["nc"] + 4 * d["nr"]) * d["nzp"]
+        f = np.random.default_rng(req["seed"]).standard_normal(E * n ** 3)
+        rid = srv.submit(d, f, tol=1e-10, h1=1.0, h2=req["h2"], prec=sem.MIXED)
+        pending[rid] = (time.perf_counter(), E * n ** 3)
+    lat, worst = [], 0.0
+    for rid, (ts, nl) in pending.items():
+        st, x, res = srv.poll(rid, timeout_ms=-1)
+        if st != sem.SEM_OK:
+            raise RuntimeError(f"serving request failed: {st} {res}")
+        lat.append(time.perf_counter() - ts)
+        worst = max(worst, res["rel_res"])
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat_ms = sorted(v * 1e3 for v in lat)
+    return {"requests": count, "arrival_rate_per_s": rate, "throughput_solves_per_s": count / wall,
+            "latency_ms": {"p50": pct(lat_ms, 50), "p99": pct(lat_ms, 99), "max": lat_ms[-1]},
+            "max_rel_res": worst, "mode": "batched per order (one CUDA graph per order per step)",
+            "mix": "box/pipe, E log-uniform in [512, 4096], N in {5,7,9}, Poisson/Helmholtz, tol 1e-10"}
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def run_gpu(args):
@@ -285,6 +325,10 @@ def run_gpu(args):
         e2e_ms.append(r["ms"])
     e2e_value = world * len(e2e_ms) / (sum(e2e_ms) / 1e3)
 
+    serving = None
+    if not args.no_serving:
+        serving = serving_stream(args.serving_requests, args.serving_rate)
+
     line = None
     if rank == 0:
         cpu = None
@@ -310,6 +354,7 @@ def run_gpu(args):
                    "fp32_hbm_frac": ax32_gbs / hbm},
             "gs": {"fp64_ms": gs64_ms, "fp32_ms": gs32_ms},
             "fp64_pcg": fp64,
+            "serving": serving,
             "roofline": {"bound": "hbm", "kernel": "k_ax<7,float> (FP32 local operator, inner CG)",
                          "achieved": ax32_gbs, "peak": hbm, "unit": "GB/s", "frac": ax32_gbs / hbm,
                          "peak_kind": peak_kind, "traffic": None,
@@ -335,6 +380,9 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--quick", action="store_true", help="skip the FP64 PCG comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-serving", action="store_true", help="skip the request-stream leg")
+    ap.add_argument("--serving-requests", type=int, default=64)
+    ap.add_argument("--serving-rate", type=float, default=20.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -200,6 +200,20 @@ sem_status sem_pcg_solve(const sem_mesh* mesh, const double* b_dev, double* x_de
 sem_status sem_pcg_solve_host(const sem_mesh* mesh, const double* b_host, double* x_host,
                               const sem_solve_opts* opts, sem_solve_result* result, void* stream);
 
+/* Many solves of one odd polynomial order N at once (the serving form of the
+ * hot path): ragged meshes, each with its own b_dev[k] / x_dev[k] (as for
+ * sem_pcg_solve) and opts[k] (prec must be SEM_MIXED with refine = 0).  Up to
+ * 32 requests are active at a time; one CUDA graph per step advances every
+ * active request by 8 CG iterations with batched kernels (a persistent
+ * bulk-copy pipelined FP32 local operator over the concatenated element
+ * tiles, per-request alpha, batched QQ^T and update); requests beyond 32
+ * join as others finish.  Each request's arithmetic depends only on its own
+ * data, so its result equals that of a batch of one.  Synchronous.  A mesh
+ * may appear once per call.  Returns SEM_OK, or the first request's failing
+ * status (results[k].status has each). */
+sem_status sem_pcg_solve_batch(const sem_mesh* const* meshes, const double* const* b_dev, double* const* x_dev,
+                               const sem_solve_opts* opts, sem_solve_result* results, int count, void* stream);
+
 /* ---- solve without device allocation -------------------------------------- */
 
 /* Largest mesh (local points) sem_pcg_solve_noalloc accepts. */
@@ -233,6 +247,10 @@ typedef struct {
   int max_slots;           /* requests solved concurrently (each on its own stream); <= 0 means 8 */
   int max_queue;           /* admitted-but-waiting requests; <= 0 means 4096 */
   int device;              /* CUDA device ordinal */
+  int batch;               /* 0 (default): mixed-precision requests of odd order N run in per-order
+                              batches (one CUDA graph of batched kernels advances them together;
+                              requests join and leave between graph launches); 1: every request
+                              is solved alone on its slot's stream */
 } sem_server_opts;
 
 typedef struct sem_server sem_server;

@@ -3,12 +3,17 @@
 // Requests are queued by sem_server_submit and admitted in arrival order
 // (first fit) whenever a slot is idle and the request's estimated device
 // footprint fits in what is left of the HBM budget.  Each slot is a worker
-// thread with its own CUDA stream; it builds the request's mesh, forms
-// b = mask QQ^T (B f), runs the solve and copies x back.  Slots run
-// concurrently, so the kernels of different requests overlap on the device,
-// and a new request starts as soon as a slot and memory free up.  Every
-// request uses only its own buffers and reductions, so its result does not
-// depend on what else is running.
+// thread with its own CUDA stream; it builds the request's mesh and forms
+// b = mask QQ^T (B f).  Then:
+//   * mixed-precision requests of an odd order N (the serving form) are
+//     handed to the engine thread of that order, which admits them into its
+//     running batch (continuous batching): one CUDA graph of batched kernels
+//     advances all of that order's requests together, and a request joins or
+//     leaves between graph launches;
+//   * every other request is solved by the slot itself on its own stream.
+// Slots and engines run concurrently, so requests overlap on the device.
+// Every request uses only its own buffers and reductions, so its result does
+// not depend on what else is running.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -18,6 +23,7 @@
 #include <thread>
 #include <unordered_map>
 
+#include "batch.h"
 #include "sem_internal.h"
 
 namespace {
@@ -37,6 +43,10 @@ struct Request {
   sem_status status = SEM_OK;
   bool done = false;
   std::string error;
+  // batched path: device state kept until the engine finishes the request
+  sem_mesh* mesh = nullptr;
+  double *f_dev = nullptr, *b_dev = nullptr, *x_dev = nullptr;
+  sem::batch::Req breq;
 };
 
 int64_t local_points(const sem_mesh_desc& d) {
@@ -55,8 +65,17 @@ size_t estimate_bytes(const sem_mesh_desc& d) { return (size_t)local_points(d) *
 
 }  // namespace
 
+struct EngineThread {
+  int N = 0;
+  std::thread th;
+  std::deque<std::shared_ptr<Request>> ready;  // built, waiting for a batch slot
+  std::vector<std::shared_ptr<Request>> active;
+};
+
 struct sem_server {
   sem_server_opts opts{};
+  std::vector<std::unique_ptr<EngineThread>> engines;  // one per order, created on demand
+  std::condition_variable cv_engine;
   size_t budget = 0, in_use = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -64,12 +83,143 @@ struct sem_server {
   std::unordered_map<uint64_t, std::shared_ptr<Request>> reqs;
   std::vector<std::thread> workers;
   bool stopping = false;
+  bool batch = true;
   uint64_t next_id = 1;
   uint64_t submitted = 0, completed = 0, rejected = 0, cancelled = 0;
   int running = 0;
 };
 
 namespace {
+
+void free_request_device(Request& q) {
+  if (q.f_dev) cudaFree(q.f_dev);
+  if (q.b_dev) cudaFree(q.b_dev);
+  if (q.x_dev) cudaFree(q.x_dev);
+  q.f_dev = q.b_dev = q.x_dev = nullptr;
+  if (q.mesh) sem_mesh_destroy(q.mesh);
+  q.mesh = nullptr;
+}
+
+bool batchable(const Request& q) {
+  return q.opts.prec == SEM_MIXED && q.opts.refine == 0 && (q.desc.N % 2) == 1;
+}
+
+void complete(sem_server* srv, const std::shared_ptr<Request>& q, sem_status st) {
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    q->status = st;
+    if (st != SEM_OK && q->error.empty()) q->error = sem_last_error();
+    q->done = true;
+    srv->in_use -= q->footprint;
+    srv->running--;
+    srv->completed++;
+  }
+  srv->cv_done.notify_all();
+  srv->cv_work.notify_all();
+}
+
+void engine_main(sem_server* srv, EngineThread* et) {
+  cudaSetDevice(srv->opts.device);
+  cudaStream_t s = nullptr;
+  cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  sem::batch::Engine eng(et->N);
+  sem_status init_st = eng.init(s);
+  for (;;) {
+    std::vector<std::shared_ptr<Request>> incoming;
+    {
+      std::unique_lock<std::mutex> lk(srv->mu);
+      srv->cv_engine.wait(lk, [&] { return srv->stopping || !et->ready.empty() || !et->active.empty(); });
+      if (srv->stopping && et->ready.empty() && et->active.empty()) break;
+      while (!et->ready.empty() && et->active.size() + incoming.size() < 32) {
+        incoming.push_back(et->ready.front());
+        et->ready.pop_front();
+      }
+    }
+    for (auto& q : incoming) {
+      sem_status st = init_st;
+      if (st == SEM_OK) st = eng.add(&q->breq);
+      if (st != SEM_OK) {
+        q->x.clear();
+        free_request_device(*q);
+        complete(srv, q, st);
+        continue;
+      }
+      et->active.push_back(q);
+    }
+    if (!eng.idle()) {
+      sem_status st = eng.step();
+      if (st != SEM_OK) {  // a CUDA failure: fail every request of this engine
+        for (auto& q : et->active) {
+          free_request_device(*q);
+          complete(srv, q, st);
+        }
+        et->active.clear();
+        init_st = st;
+        continue;
+      }
+    }
+    for (size_t k = 0; k < et->active.size();) {
+      auto q = et->active[k];
+      if (!q->breq.finished) {
+        ++k;
+        continue;
+      }
+      q->x.resize(q->n_local);
+      cudaMemcpy(q->x.data(), q->x_dev, (size_t)q->n_local * sizeof(double), cudaMemcpyDeviceToHost);
+      free_request_device(*q);
+      complete(srv, q, q->breq.status);
+      et->active[k] = et->active.back();
+      et->active.pop_back();
+    }
+  }
+  cudaStreamDestroy(s);
+}
+
+// Build the mesh and b of a batchable request and hand it to its order's engine.
+sem_status stage_for_batch(sem_server* srv, const std::shared_ptr<Request>& q, cudaStream_t s) {
+  sem_mesh_desc d = q->desc;
+  if (d.kind == SEM_MESH_EXPLICIT) {
+    d.xyz = q->xyz.data();
+    d.vert = q->vert.data();
+    d.dirichlet_face = q->dface.data();
+  }
+  sem_status st = sem_mesh_create(&d, s, &q->mesh);
+  if (st != SEM_OK) return st;
+  const size_t bytes = (size_t)q->n_local * sizeof(double);
+  cudaError_t e = cudaMalloc((void**)&q->f_dev, bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&q->b_dev, bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&q->x_dev, bytes);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(q->f_dev, q->f.data(), bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(q->x_dev, 0, bytes, s);
+  if (e != cudaSuccess) return sem::cuda_fail(e, "server buffers");
+  st = sem_rhs(q->mesh, q->f_dev, q->b_dev, s);
+  if (st != SEM_OK) return st;
+  SEM_CUDA(cudaStreamSynchronize(s));
+  q->breq = sem::batch::Req();
+  q->breq.m = q->mesh;
+  q->breq.b = q->b_dev;
+  q->breq.x = q->x_dev;
+  q->breq.o = q->opts;
+  if (!(q->breq.o.tol > 0.0)) q->breq.o.tol = 1e-10;
+  if (q->breq.o.maxit <= 0) q->breq.o.maxit = 20000;
+  if (!(q->breq.o.delta > 0.0)) q->breq.o.delta = 0.1;
+  q->breq.out = &q->res;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    EngineThread* et = nullptr;
+    for (auto& p : srv->engines)
+      if (p->N == q->desc.N) et = p.get();
+    if (!et) {
+      srv->engines.emplace_back(new EngineThread());
+      et = srv->engines.back().get();
+      et->N = q->desc.N;
+      et->th = std::thread(engine_main, srv, et);
+    }
+    et->ready.push_back(q);
+  }
+  srv->cv_engine.notify_all();
+  return SEM_OK;
+}
 
 sem_status run_request(sem_server* srv, Request& q, cudaStream_t s) {
   (void)srv;
@@ -133,18 +283,17 @@ void worker_main(sem_server* srv) {
       }
       if (!q) break;
     }
-    sem_status st = run_request(srv, *q, s);
-    {
-      std::lock_guard<std::mutex> lk(srv->mu);
-      q->status = st;
-      if (st != SEM_OK) q->error = sem_last_error();
-      q->done = true;
-      srv->in_use -= q->footprint;
-      srv->running--;
-      srv->completed++;
+    if (srv->batch && batchable(*q)) {
+      sem_status st = stage_for_batch(srv, q, s);
+      if (st != SEM_OK) {
+        cudaStreamSynchronize(s);
+        free_request_device(*q);
+        complete(srv, q, st);
+      }
+      continue;  // the engine thread completes it
     }
-    srv->cv_done.notify_all();
-    srv->cv_work.notify_all();
+    sem_status st = run_request(srv, *q, s);
+    complete(srv, q, st);
   }
   cudaStreamDestroy(s);
 }
@@ -167,6 +316,7 @@ sem_status sem_server_create(const sem_server_opts* opts, sem_server** out) {
   srv->opts = *opts;
   if (srv->opts.max_slots <= 0) srv->opts.max_slots = 8;
   if (srv->opts.max_queue <= 0) srv->opts.max_queue = 4096;
+  srv->batch = opts->batch == 0;  // 0 (default): batch the serving form; 1: per-request streams only
   srv->budget = opts->hbm_budget_bytes;
   if (srv->budget == 0) {
     size_t fr = 0, tot = 0;
@@ -306,6 +456,8 @@ sem_status sem_server_destroy(sem_server* srv) {
   srv->cv_work.notify_all();
   srv->cv_done.notify_all();
   for (auto& t : srv->workers) t.join();
+  srv->cv_engine.notify_all();
+  for (auto& e : srv->engines) e->th.join();  // they finish their requests first
   delete srv;
   return SEM_OK;
 }

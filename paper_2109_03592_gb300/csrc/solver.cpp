@@ -31,26 +31,6 @@ namespace sem {
 
 constexpr int kChunk = 8;  // CG iterations per graph launch
 
-struct GraphSlot {
-  cudaGraphExec_t exec = nullptr;
-  double h1 = NAN, h2 = NAN;
-  int var = -1, df = -1;
-};
-
-struct Workspace {
-  int64_t n = 0;
-  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr, *minv = nullptr, *b = nullptr;
-  float *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *w32 = nullptr, *minv32 = nullptr;
-  PcgState* st = nullptr;
-  PcgState* sth = nullptr;  // pinned host [2]
-  double* part_ax = nullptr;
-  double* part_vec = nullptr;
-  cudaStream_t s = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr, eu = nullptr, ev[2] = {nullptr, nullptr};
-  double minv_h1 = NAN, minv_h2 = NAN;
-  GraphSlot g64, g32;
-};
-
 static void destroy_ws(Workspace* ws) {
   if (!ws) return;
   if (ws->s) cudaStreamSynchronize(ws->s);
@@ -79,7 +59,7 @@ static int max_ax_grid(const sem_mesh* m) {
   return (int)((m->E + epb - 1) / epb);
 }
 
-static sem_status alloc_ws(sem_mesh* m, Workspace** out) {
+sem_status alloc_ws(sem_mesh* m, Workspace** out) {
   Workspace* ws = new Workspace();
   ws->n = m->n_local;
   const size_t n = (size_t)m->n_local;
@@ -110,7 +90,7 @@ static sem_status alloc_ws(sem_mesh* m, Workspace** out) {
 
 // ---- local operator dispatch ---------------------------------------------------
 
-static cudaError_t ax64(const sem_mesh* m, const double* u, double* w, double h1, double h2, bool fused,
+cudaError_t ax64(const sem_mesh* m, const double* u, double* w, double h1, double h2, bool fused,
                         const double* z, double* p, PcgState* st, double* part, cudaStream_t s) {
   if (m->fp64_df) {
     AxDFParams a{u, w, m->G32, m->G32lo, m->B32, m->B32lo, m->D32, m->D32lo, h1, h2, h2 != 0.0, m->E, z, p, st, part};
@@ -284,7 +264,7 @@ static sem_status iter32(sem_mesh* m, Workspace* ws, double h1, double h2) {
   return SEM_OK;
 }
 
-static sem_status put_state(Workspace* ws, double tol, int maxit, int done) {
+sem_status put_state(Workspace* ws, double tol, int maxit, int done) {
   PcgState h;
   std::memset(&h, 0, sizeof(h));
   h.tol2 = tol * tol;
@@ -296,7 +276,7 @@ static sem_status put_state(Workspace* ws, double tol, int maxit, int done) {
   return SEM_OK;
 }
 
-static sem_status read_state(Workspace* ws, PcgState& out) {
+sem_status read_state(Workspace* ws, PcgState& out) {
   SEM_CUDA(cudaMemcpyAsync(&ws->sth[0], ws->st, sizeof(PcgState), cudaMemcpyDeviceToHost, ws->s));
   SEM_CUDA(cudaStreamSynchronize(ws->s));
   out = ws->sth[0];
@@ -408,6 +388,8 @@ static sem_status pcg_mixed(sem_mesh* m, Workspace* ws, const sem_solve_opts& o,
                             int max_outer, SolveOut& res) {
   sem_status st = get_graph(m, ws, true, o.h1, o.h2);
   if (st != SEM_OK) return st;
+  st = put_state(ws, inner_tol, maxit, 0);  // zero arrival counters before the first reduction
+  if (st != SEM_OK) return st;
   for (int outer = 0;; ++outer) {
     SEM_CUDA(ax64(m, ws->x, ws->w, o.h1, o.h2, false, nullptr, nullptr, nullptr, nullptr, ws->s));
     SEM_CUDA(launch_gs<double>(ws->w, gs_dev(m), 1, nullptr, ws->s));
@@ -465,6 +447,8 @@ static sem_status pcg_mixed(sem_mesh* m, Workspace* ws, const sem_solve_opts& o,
 static sem_status pcg_mixed_reliable(sem_mesh* m, Workspace* ws, const sem_solve_opts& o, int maxit,
                                      double delta, SolveOut& res) {
   sem_status st = get_graph(m, ws, true, o.h1, o.h2);
+  if (st != SEM_OK) return st;
+  st = put_state(ws, o.tol, maxit, 0);  // zero arrival counters before the first reduction
   if (st != SEM_OK) return st;
   SEM_CUDA(ax64(m, ws->x, ws->w, o.h1, o.h2, false, nullptr, nullptr, nullptr, nullptr, ws->s));
   SEM_CUDA(launch_gs<double>(ws->w, gs_dev(m), 1, nullptr, ws->s));

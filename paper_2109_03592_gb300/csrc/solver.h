@@ -5,6 +5,34 @@
 
 namespace sem {
 
+struct GraphSlot {
+  cudaGraphExec_t exec = nullptr;
+  double h1 = NAN, h2 = NAN;
+  int var = -1, df = -1;
+};
+
+struct Workspace {
+  int64_t n = 0;
+  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr, *minv = nullptr, *b = nullptr;
+  float *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *w32 = nullptr, *minv32 = nullptr;
+  PcgState* st = nullptr;
+  PcgState* sth = nullptr;  // pinned host [2]
+  double* part_ax = nullptr;
+  double* part_vec = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, eu = nullptr, ev[2] = {nullptr, nullptr};
+  double minv_h1 = NAN, minv_h2 = NAN;
+  GraphSlot g64, g32;
+};
+
+sem_status alloc_ws(sem_mesh* m, Workspace** out);
+// FP64 local operator with the mesh's tuned kernel (native or double-float).
+cudaError_t ax64(const sem_mesh* m, const double* u, double* w, double h1, double h2, bool fused, const double* z,
+                 double* p, PcgState* st, double* part, cudaStream_t s);
+// Write a fresh PcgState (tol, maxit, done) to ws->st / read it back (both synchronise ws->s).
+sem_status put_state(Workspace* ws, double tol, int maxit, int done);
+sem_status read_state(Workspace* ws, PcgState& out);
+
 // w = A_L u with the mesh's tuned kernel for `prec` (SEM_FP64 or SEM_FP32).
 sem_status apply_local(const sem_mesh* m, const void* u, void* w, double h1, double h2, sem_prec prec,
                        cudaStream_t s);

@@ -60,7 +60,7 @@ class SolveResult(C.Structure):
 
 class ServerOpts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_slots", C.c_int), ("max_queue", C.c_int),
-                ("device", C.c_int)]
+                ("device", C.c_int), ("batch", C.c_int)]
 
 
 class ServerStats(C.Structure):
@@ -87,6 +87,7 @@ SIGNATURES = {
     "sem_pcg_solve": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
     "sem_pcg_solve_host": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
     "sem_pcg_solve_noalloc": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
+    "sem_pcg_solve_batch": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), C.c_int, _P]),
     "sem_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(_P)]),
     "sem_server_submit": (C.c_int, [_P, C.POINTER(MeshDesc), _P, C.POINTER(SolveOpts), C.POINTER(C.c_uint64)]),
     "sem_server_poll": (C.c_int, [_P, C.c_uint64, C.c_int, _P, C.POINTER(SolveResult)]),
@@ -325,6 +326,25 @@ class Mesh:
         return r.as_dict()
 
 
+def solve_batch(meshes, bs, xs, opts_list=None, stream=None, **opts):
+    """sem_pcg_solve_batch: mixed-precision solves of one odd order N together.
+    meshes, bs, xs: lists (CUDA float64 tensors); opts_list: per-request dicts
+    (defaults to the keyword options for all).  Returns (status, [result dicts])."""
+    import torch
+    k = len(meshes)
+    if opts_list is None:
+        opts_list = [opts] * k
+    Mh = (C.c_void_p * k)(*[m._h.value for m in meshes])
+    Bp = (C.c_void_p * k)(*[_dptr(b, torch.float64, m.n_local).value for b, m in zip(bs, meshes)])
+    Xp = (C.c_void_p * k)(*[_dptr(x, torch.float64, m.n_local).value for x, m in zip(xs, meshes)])
+    Op = (SolveOpts * k)(*[_opts(**dict({"prec": MIXED}, **o)) for o in opts_list])
+    Rs = (SolveResult * k)()
+    st = lib().sem_pcg_solve_batch(Mh, Bp, Xp, Op, Rs, k, _stream(stream))
+    if st in (SEM_ERR_INVALID, SEM_ERR_CUDA, SEM_ERR_OOM):
+        _check(st, "sem_pcg_solve_batch")
+    return st, [Rs[q].as_dict() for q in range(k)]
+
+
 def kernel_launches():
     """Kernels launched by the library so far in this process (graph replays
     count every kernel node)."""
@@ -354,9 +374,10 @@ def mesh_vertices(desc):
 class Server:
     """Request server (sem_server_*)."""
 
-    def __init__(self, hbm_budget_bytes=0, max_slots=8, max_queue=4096, device=0):
+    def __init__(self, hbm_budget_bytes=0, max_slots=8, max_queue=4096, device=0, batch=True):
         o = ServerOpts()
         o.hbm_budget_bytes, o.max_slots, o.max_queue, o.device = int(hbm_budget_bytes), max_slots, max_queue, device
+        o.batch = 0 if batch else 1
         h = C.c_void_p()
         _check(lib().sem_server_create(C.byref(o), C.byref(h)), "sem_server_create")
         self._h = h

@@ -1,7 +1,8 @@
-"""Parity at the benchmark's full size (O-grid pipe, E = 262,144, N = 7, the
-configuration bench.py times): outputs the oracle can compute one element at
-a time are compared on sampled elements; the rest through properties that
-hold at any size."""
+"""Parity at full size: the benchmark's O-grid pipe (E = 262,144, N = 7, the
+configuration bench.py times) and the large cases (E = 131,072 at N = 11;
+E = 1,048,576 at N = 7, ~3.6e8 global nodes).  Outputs the oracle can compute
+one element at a time are compared on sampled elements; the rest through
+properties that hold at any size."""
 
 import numpy as np
 import pytest
@@ -11,15 +12,15 @@ from sem_inputs import configs, forcing
 
 pytestmark = pytest.mark.gpu
 
-NAME = "pipe262144_n7"
+BENCH = "pipe262144_n7"
 SAMPLE = 48
 
 
-@pytest.fixture(scope="module")
-def big():
+@pytest.fixture(scope="module", params=[BENCH, "pipe131072_n11", "pipe1048576_n7"])
+def big(request):
     import torch
     import paper_2109_03592_gb300 as sem
-    desc = configs.mesh_desc(NAME)
+    desc = configs.mesh_desc(request.param)
     m = sem.Mesh(desc)
     rng = np.random.default_rng(7)
     els = np.sort(rng.choice(m.E, SAMPLE, replace=False))
@@ -29,6 +30,9 @@ def big():
     D = gll.derivative_matrix(desc["N"])
     yield m, desc, els, om, G, B, D
     m.close()
+    del m
+    import gc
+    gc.collect()
     torch.cuda.empty_cache()
 
 
@@ -47,6 +51,7 @@ def test_numbering_properties(big):
     hist = np.bincount(mult)
     # 3: z-edges through the O-grid square corners (3 elements in the plane); 6: their vertices
     assert hist[6] > 0 and hist[3] > 0 and set(np.nonzero(hist)[0]) <= {1, 2, 3, 4, 6, 8}
+    del mult, hist
     # sampled elements: the library's ids, relabelled in first-touch order over
     # the sample, equal the oracle's coordinate-based numbering of the sample
     from oracle import numbering
@@ -123,6 +128,8 @@ def test_gs_properties_full_size(big):
 
 
 def test_mixed_solve_sampled_residual(big):
+    if big[1] != configs.mesh_desc(BENCH):
+        pytest.skip("the solve is checked on the benchmark configuration")
     """The bench's solve (mixed precision, reliable updates, tol 1e-10): the
     residual at element-interior points of sampled elements, recomputed by the
     oracle from x, is bounded by ||r|| <= 1e-10 ||b|| (an interior point has

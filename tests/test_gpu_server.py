@@ -49,16 +49,20 @@ def _solve_all(srv, inputs, prec):
     return out
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_results_same_alone_and_in_the_mix(inputs, prec):
+@pytest.mark.parametrize("prec,batch", [("mixed", True), ("mixed", False), ("fp64", True)])
+def test_results_same_alone_and_in_the_mix(inputs, prec, batch):
+    """Mixed precision with batching: odd-order requests share per-order
+    batches (one graph of batched kernels); without batching, and for FP64,
+    each request runs on its slot's stream.  Either way a request's result is
+    bitwise the same alone and among 11 others."""
     import paper_2109_03592_gb300 as sem
     pr = sem.MIXED if prec == "mixed" else sem.FP64
     alone = []
-    srv1 = sem.Server(max_slots=1)
+    srv1 = sem.Server(max_slots=1, batch=batch)
     for item in inputs:  # one request at a time on an idle server
         alone += _solve_all(srv1, [item], pr)
     srv1.close()
-    srv = sem.Server(max_slots=4)
+    srv = sem.Server(max_slots=4, batch=batch)
     mixed = _solve_all(srv, inputs + inputs, pr)  # 12 requests, 4 in flight
     st = srv.stats()
     srv.close()
@@ -83,8 +87,9 @@ def test_admission_queue_cancel_and_timeout(inputs):
     assert ei.value.status == sem.SEM_ERR_OOM
     assert srv.stats()["rejected"] == 1
     srv.close()
-    # one slot, a short queue: later submissions wait, the queue bounds them
-    srv = sem.Server(max_slots=1, max_queue=3)
+    # one slot solving every request itself (no batching), a short queue:
+    # later submissions wait, the queue bounds them
+    srv = sem.Server(max_slots=1, max_queue=3, batch=False)
     big = dict(kind="pipe", nc=4, nr=2, nzp=24, N=7, L=8.0)
     fbig = np.zeros(4 * 12 * 24 * 512)
     fbig[:] = 1.0
