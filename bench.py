@@ -118,6 +118,20 @@ def time_kernel(fn, reps, stream):
     return a.elapsed_time(b) / reps
 
 
+def aggregate(local_seconds, steps, world, dist=None):
+    """Whole-job throughput of N independent replicas: every rank solved
+    `steps` systems in `local_seconds`; the job time is the maximum over
+    ranks (one all-reduce; the data path has no collective)."""
+    t = float(local_seconds)
+    if world > 1 and dist is not None:
+        import torch
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        tt = torch.tensor([t], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt)
+    return world * steps / t, t
+
+
 # ---------------------------------------------------------------- oracle arm
 
 def oracle_sample(budget_s=20.0, iters=None):
@@ -284,11 +298,7 @@ def run_gpu(args):
         barrier()
         wall_s = time.perf_counter() - t_start
     launches = sem.kernel_launches() - launches0
-    t_max = torch.tensor([dev_ms / 1e3], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    t_max = float(t_max)
-    value = world * args.steps / t_max
+    value, t_max = aggregate(dev_ms / 1e3, args.steps, world, dist if world > 1 else None)
 
     # ---- kernel-level measurements (same mesh, same stream the kernels run on)
     P = m.n_local

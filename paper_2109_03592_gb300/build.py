@@ -5,6 +5,7 @@ paper_2109_03592_gb300/libsem.so."""
 import concurrent.futures as cf
 import hashlib
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -41,7 +42,8 @@ def _headers_digest():
 
 def _compile(src, cuda, hdr):
     path = os.path.join(CSRC, src)
-    digest = hashlib.sha256(open(path, "rb").read() + hdr.encode()).hexdigest()[:16]
+    # objects are cached by source, headers and host machine (x86_64 vs aarch64)
+    digest = hashlib.sha256(open(path, "rb").read() + hdr.encode() + platform.machine().encode()).hexdigest()[:16]
     obj = os.path.join(BUILD, f"{src}.{digest}.o")
     if os.path.exists(obj):
         return obj
@@ -72,6 +74,10 @@ def build(verbose=False):
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    keep = {os.path.basename(o) for o in objs}
+    for f in os.listdir(BUILD):
+        if f.endswith(".o") and f not in keep:
+            os.remove(os.path.join(BUILD, f))
     if verbose:
         print("built", LIB)
     return LIB

@@ -1,0 +1,46 @@
+"""The multi-GPU form of bench.py is N independent replicas; its only
+collective is the max-over-ranks job time.  Checked with two gloo ranks on
+the CPU (no GPU involved)."""
+
+import os
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _rank(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    value, t = bench.aggregate(1.0 + rank, steps=3, world=world, dist=dist)
+    out.put((rank, value, t))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_aggregate_with_the_slowest_rank():
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = 29500 + os.getpid() % 1000
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(out.get(timeout=10) for _ in range(2))
+    for rank, value, t in res:
+        assert t == 2.0                      # max over ranks
+        assert value == pytest.approx(3.0)   # 2 ranks x 3 solves / 2 s
+
+
+def test_single_rank_aggregate():
+    sys.path.insert(0, ROOT)
+    import bench
+    value, t = bench.aggregate(4.0, steps=2, world=1)
+    assert t == 4.0 and value == 0.5
