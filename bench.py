@@ -238,6 +238,18 @@ def serving_stream(count, rate, seed=4):
 
 # ---------------------------------------------------------------- GPU arm
 
+def fp32_kernel_name(N, variant):
+    """The FP32 local-operator kernel the autotuner chose (variants 0/1:
+    register kernels with ~256/~128 threads per CTA; 2/3: persistent
+    bulk-copy pipelined kernels with 3/2 stages)."""
+    n2 = (N + 1) ** 2
+    epb = max(1, (256 if variant in (0, 3) else 128) // n2)
+    if variant >= 2:
+        return f"tma::k_ax_tma<{N}, {epb}, {3 if variant == 2 else 2}, false> (FP32 local operator, bulk-copy pipelined)"
+    return f"k_ax<{N}, float, {epb}, false> (FP32 local operator)"
+
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -365,7 +377,9 @@ def run_gpu(args):
             "gs": {"fp64_ms": gs64_ms, "fp32_ms": gs32_ms},
             "fp64_pcg": fp64,
             "serving": serving,
-            "roofline": {"bound": "hbm", "kernel": "k_ax<7,float> (FP32 local operator, inner CG)",
+            "roofline": {"bound": "hbm", "kernel": fp32_kernel_name(m.N, m.ax_variant(sem.FP32)),
+                         "timed": "sem_ax FP32 launches on the bench mesh, CUDA events on the launching stream, "
+                                  "after the timed solves (the inner CG runs the fused form of the same kernel)",
                          "achieved": ax32_gbs, "peak": hbm, "unit": "GB/s", "frac": ax32_gbs / hbm,
                          "peak_kind": peak_kind, "traffic": None,
                          "algorithmic_bytes_per_launch": AX_BYTES["fp32"] * P},

@@ -63,6 +63,8 @@ void free_mesh_arrays(sem_mesh* m) {
   dev_free(m->dev_err);
   dev_free(m->D32);
   dev_free(m->D32lo);
+  dev_free(m->eo64);
+  dev_free(m->eodf);
 }
 
 #define SEM_TRY(expr)                   \
@@ -106,6 +108,25 @@ sem_status build_mesh(const sem_mesh_desc& d, cudaStream_t s, sem_mesh* m) {
     D32[q] = (float)D[q];
     D32lo[q] = (float)(D[q] - (double)D32[q]);
   }
+  // even-odd tables (D is centro-antisymmetric; n even only)
+  const int hh = n / 2;
+  std::vector<double> eo64((n % 2 == 0) ? 4 * hh * hh : 0);
+  std::vector<float> eodf(eo64.size() * 2);
+  for (int dir = 0; dir < 2 && n % 2 == 0; ++dir)
+    for (int i = 0; i < hh; ++i)
+      for (int l = 0; l < hh; ++l) {
+        // dir 0: D[i][l], D[i][n-1-l]; dir 1 (D^T): D[l][i], D[n-1-l][i]
+        const double x = dir == 0 ? D[i * n + l] : D[l * n + i];
+        const double y = dir == 0 ? D[i * n + (n - 1 - l)] : D[(n - 1 - l) * n + i];
+        const int q = (dir * hh + i) * hh + l;
+        eo64[2 * q] = (x + y) / 2;
+        eo64[2 * q + 1] = (x - y) / 2;
+        for (int c = 0; c < 2; ++c) {
+          const float hi = (float)eo64[2 * q + c];
+          eodf[4 * q + 2 * c] = hi;
+          eodf[4 * q + 2 * c + 1] = (float)(eo64[2 * q + c] - (double)hi);
+        }
+      }
 
   size_t& tb = m->dev_bytes;
   SEM_TRY(dev_alloc(&m->xyz, 3 * P, tb));
@@ -124,6 +145,10 @@ sem_status build_mesh(const sem_mesh_desc& d, cudaStream_t s, sem_mesh* m) {
   SEM_TRY(dev_alloc(&m->dev_err, 1, tb));
   SEM_TRY(dev_alloc(&m->D32, n * n, tb));
   SEM_TRY(dev_alloc(&m->D32lo, n * n, tb));
+  if (!eo64.empty()) {
+    SEM_TRY(dev_alloc(&m->eo64, eo64.size(), tb));
+    SEM_TRY(dev_alloc(&m->eodf, eodf.size(), tb));
+  }
 
   size_t tmp_bytes = 0;
   double *xi_d = nullptr, *w_d = nullptr, *tlev_d = nullptr;
@@ -149,6 +174,10 @@ sem_status build_mesh(const sem_mesh_desc& d, cudaStream_t s, sem_mesh* m) {
   SEM_CUDA(cudaMemcpyAsync(m->D64, D.data(), n * n * sizeof(double), cudaMemcpyHostToDevice, s));
   SEM_CUDA(cudaMemcpyAsync(m->D32, D32.data(), n * n * sizeof(float), cudaMemcpyHostToDevice, s));
   SEM_CUDA(cudaMemcpyAsync(m->D32lo, D32lo.data(), n * n * sizeof(float), cudaMemcpyHostToDevice, s));
+  if (!eo64.empty()) {
+    SEM_CUDA(cudaMemcpyAsync(m->eo64, eo64.data(), eo64.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    SEM_CUDA(cudaMemcpyAsync(m->eodf, eodf.data(), eodf.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+  }
   SEM_CUDA(cudaMemsetAsync(bad_d, 0, sizeof(int), s));
   SEM_CUDA(cudaMemsetAsync(m->dev_err, 0, sizeof(int), s));
   SEM_CUDA(cudaMemcpyAsync(m->wm, plan.wm.data(), P, cudaMemcpyHostToDevice, s));

@@ -1,6 +1,6 @@
 // Local-operator kernels instantiated for polynomial orders 11.
 // (One translation unit per order keeps the parallel build short.)
-#include "ax_df_impl.cuh"
+#include "ax_eo_impl.cuh"
 #include "ax_impl.cuh"
 
 namespace sem {
@@ -12,7 +12,7 @@ cudaError_t ax32_n11(int v, bool f, const AxParams<float>& p, cudaStream_t s, in
   return dispatch_ax_n<float, 11>(v, f, p, s, g);
 }
 cudaError_t axdf_n11(int v, bool f, const AxDFParams& p, cudaStream_t s, int* g) {
-  return df_detail::dispatch_df_n<11>(v, f, p, s, g);
+  return dispatch_fp64df_n<11>(v, f, p, s, g);
 }
 
 }  // namespace sem

@@ -1,6 +1,6 @@
 // Local-operator kernels instantiated for polynomial orders 1, 2, 3, 4.
 // (One translation unit per order keeps the parallel build short.)
-#include "ax_df_impl.cuh"
+#include "ax_eo_impl.cuh"
 #include "ax_impl.cuh"
 
 namespace sem {
@@ -12,7 +12,7 @@ cudaError_t ax32_n1(int v, bool f, const AxParams<float>& p, cudaStream_t s, int
   return dispatch_ax_n<float, 1>(v, f, p, s, g);
 }
 cudaError_t axdf_n1(int v, bool f, const AxDFParams& p, cudaStream_t s, int* g) {
-  return df_detail::dispatch_df_n<1>(v, f, p, s, g);
+  return dispatch_fp64df_n<1>(v, f, p, s, g);
 }
 
 cudaError_t ax64_n2(int v, bool f, const AxParams<double>& p, cudaStream_t s, int* g) {
@@ -22,7 +22,7 @@ cudaError_t ax32_n2(int v, bool f, const AxParams<float>& p, cudaStream_t s, int
   return dispatch_ax_n<float, 2>(v, f, p, s, g);
 }
 cudaError_t axdf_n2(int v, bool f, const AxDFParams& p, cudaStream_t s, int* g) {
-  return df_detail::dispatch_df_n<2>(v, f, p, s, g);
+  return dispatch_fp64df_n<2>(v, f, p, s, g);
 }
 
 cudaError_t ax64_n3(int v, bool f, const AxParams<double>& p, cudaStream_t s, int* g) {
@@ -32,7 +32,7 @@ cudaError_t ax32_n3(int v, bool f, const AxParams<float>& p, cudaStream_t s, int
   return dispatch_ax_n<float, 3>(v, f, p, s, g);
 }
 cudaError_t axdf_n3(int v, bool f, const AxDFParams& p, cudaStream_t s, int* g) {
-  return df_detail::dispatch_df_n<3>(v, f, p, s, g);
+  return dispatch_fp64df_n<3>(v, f, p, s, g);
 }
 
 cudaError_t ax64_n4(int v, bool f, const AxParams<double>& p, cudaStream_t s, int* g) {
@@ -42,7 +42,7 @@ cudaError_t ax32_n4(int v, bool f, const AxParams<float>& p, cudaStream_t s, int
   return dispatch_ax_n<float, 4>(v, f, p, s, g);
 }
 cudaError_t axdf_n4(int v, bool f, const AxDFParams& p, cudaStream_t s, int* g) {
-  return df_detail::dispatch_df_n<4>(v, f, p, s, g);
+  return dispatch_fp64df_n<4>(v, f, p, s, g);
 }
 
 }  // namespace sem

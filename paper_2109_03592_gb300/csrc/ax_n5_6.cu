@@ -1,6 +1,6 @@
 // Local-operator kernels instantiated for polynomial orders 5, 6.
 // (One translation unit per order keeps the parallel build short.)
-#include "ax_df_impl.cuh"
+#include "ax_eo_impl.cuh"
 #include "ax_impl.cuh"
 
 namespace sem {
@@ -12,7 +12,7 @@ cudaError_t ax32_n5(int v, bool f, const AxParams<float>& p, cudaStream_t s, int
   return dispatch_ax_n<float, 5>(v, f, p, s, g);
 }
 cudaError_t axdf_n5(int v, bool f, const AxDFParams& p, cudaStream_t s, int* g) {
-  return df_detail::dispatch_df_n<5>(v, f, p, s, g);
+  return dispatch_fp64df_n<5>(v, f, p, s, g);
 }
 
 cudaError_t ax64_n6(int v, bool f, const AxParams<double>& p, cudaStream_t s, int* g) {
@@ -22,7 +22,7 @@ cudaError_t ax32_n6(int v, bool f, const AxParams<float>& p, cudaStream_t s, int
   return dispatch_ax_n<float, 6>(v, f, p, s, g);
 }
 cudaError_t axdf_n6(int v, bool f, const AxDFParams& p, cudaStream_t s, int* g) {
-  return df_detail::dispatch_df_n<6>(v, f, p, s, g);
+  return dispatch_fp64df_n<6>(v, f, p, s, g);
 }
 
 }  // namespace sem

@@ -60,12 +60,15 @@ struct AxDFParams {
   double* p;
   PcgState* st;
   double* partial;
+  const double* eo64;  // even-odd coefficient tables (even n; see sem_mesh::eo64)
+  const float* eodf;
 };
 
 // Kernel variants of the local operator for one (N, precision): 0 and 1 are
 // the register/shared-memory kernels with ~256 / ~128 threads per CTA; 2 and
 // 3 (FP32, even n only) the persistent bulk-copy pipelined kernels with
-// ~128 threads x 3 stages / ~256 threads x 2 stages.  A launch of a variant
+// ~128 threads x 3 stages / ~256 threads x 2 stages; for the double-float
+// FP64 operator 2 and 3 are the even-odd kernels (even n only).  A launch of a variant
 // that does not exist for (N, precision) returns cudaErrorNotSupported.
 int ax_num_variants();
 int ax_elems_per_block(int N, int variant);

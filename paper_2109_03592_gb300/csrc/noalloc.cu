@@ -128,7 +128,7 @@ extern "C" sem_status sem_pcg_solve_noalloc(const sem_mesh* m, const double* b_d
   auto fp64_ax = [&]() -> cudaError_t {
     if (m->fp64_df) {
       AxDFParams a{nullptr, w, m->G32, m->G32lo, m->B32, m->B32lo, m->D32, m->D32lo, h1, h2, h2 != 0.0, m->E, z, p, dst,
-                   part_ax};
+                   part_ax, m->eo64, m->eodf};
       return launch_ax_df(m->N, m->ax_var[2], true, a, s, nullptr);
     }
     AxParams<double> a{nullptr, w, m->G64, m->B64, m->D64, h1, h2, h2 != 0.0, m->E, z, p, dst, part_ax};

@@ -94,6 +94,11 @@ struct sem_mesh {
   double* D64 = nullptr;     // [n*n] D (row i: d/dr at xi_i)
   float* D32 = nullptr;
   float* D32lo = nullptr;
+  // even-odd coefficients of D and D^T (even n only), [2][h][h] with h = n/2:
+  // (Ep, Em) = (D[i][l] +- D[i][n-1-l]) / 2 for D, then the same for D^T;
+  // eo64 in FP64 (pairs), eodf split into (Ep.hi, Ep.lo, Em.hi, Em.lo)
+  double* eo64 = nullptr;
+  float* eodf = nullptr;
 
   // local-operator kernel choice, set by the autotuner at creation:
   // variant index per precision (0 FP64 native, 1 FP32, 2 FP64 double-float)

@@ -93,7 +93,8 @@ sem_status alloc_ws(sem_mesh* m, Workspace** out) {
 cudaError_t ax64(const sem_mesh* m, const double* u, double* w, double h1, double h2, bool fused,
                         const double* z, double* p, PcgState* st, double* part, cudaStream_t s) {
   if (m->fp64_df) {
-    AxDFParams a{u, w, m->G32, m->G32lo, m->B32, m->B32lo, m->D32, m->D32lo, h1, h2, h2 != 0.0, m->E, z, p, st, part};
+    AxDFParams a{u,      w, m->G32, m->G32lo, m->B32, m->B32lo, m->D32, m->D32lo, h1,     h2,
+                 h2 != 0.0, m->E, z, p, st, part, m->eo64, m->eodf};
     return launch_ax_df(m->N, m->ax_var[2], fused, a, s, nullptr);
   }
   AxParams<double> a{u, w, m->G64, m->B64, m->D64, h1, h2, h2 != 0.0, m->E, z, p, st, part};
@@ -174,7 +175,7 @@ static sem_status autotune_measure(sem_mesh* m, cudaStream_t s) {
           err = launch_ax_f32(m->N, v, false, pa, s, nullptr);
         } else {
           AxDFParams pa{m->B64, w, m->G32, m->G32lo, m->B32, m->B32lo, m->D32, m->D32lo, 1.0, 0.0, 0, m->E,
-                        nullptr, nullptr, nullptr, nullptr};
+                        nullptr, nullptr, nullptr, nullptr, m->eo64, m->eodf};
           err = launch_ax_df(m->N, v, false, pa, s, nullptr);
         }
         cudaEventRecord(b, s);
@@ -207,8 +208,9 @@ static sem_status autotune_measure(sem_mesh* m, cudaStream_t s) {
 // Times every elements-per-block variant of the FP64, FP32 and double-float
 // local operator on this mesh (the mesh's own factors as input) and keeps
 // the fastest; FP64 requests use the double-float kernel when it is faster.
-// SEM_FP64_KERNEL=native|df forces the FP64 choice and SEM_FP32_VARIANT=v
-// an FP32 variant that exists for this order.
+// SEM_FP64_KERNEL=native|df forces the FP64 choice, SEM_FP32_VARIANT=v an
+// FP32 variant and SEM_FP64_DF_VARIANT=v a double-float variant (which then
+// serves FP64 requests) that exists for this order.
 sem_status autotune_mesh(sem_mesh* m, cudaStream_t s) {
   int lg = 0;
   while ((1LL << (lg + 1)) <= m->E) ++lg;
@@ -241,6 +243,13 @@ forced:
   if (const char* f = std::getenv("SEM_FP32_VARIANT")) {
     const int v = std::atoi(f);
     if (v >= 0 && v < ax_num_variants() && m->ax_ms[1][v] > 0.f) m->ax_var[1] = v;
+  }
+  if (const char* f = std::getenv("SEM_FP64_DF_VARIANT")) {
+    const int v = std::atoi(f);
+    if (v >= 0 && v < ax_num_variants() && m->ax_ms[2][v] > 0.f) {
+      m->ax_var[2] = v;
+      m->fp64_df = 1;
+    }
   }
   return SEM_OK;
 }

@@ -1,7 +1,7 @@
 """Seeded request stream for the serving workload.
 
 Each request is a Poisson or Helmholtz solve on a box or pipe mesh:
-log2 E_target ~ U[9, 15] snapped to the nearest achievable mesh, box/pipe
+log2 E_target ~ U[9, 15] snapped to the nearest achievable near-cubic box or pipe, box/pipe
 50/50, N uniform in {5, 7, 9}, Poisson/Helmholtz 50/50 with h1 = 1 and
 h2 log-uniform in [1e-2, 1e2], Poisson-process arrivals at ``rate`` per
 second, forcing from ``forcing.random_modes`` with a per-request seed.
@@ -16,12 +16,12 @@ _PIPE_XS = [(2, 1), (4, 1), (4, 2), (8, 2)]
 
 
 def _box_near(E):
+    """Near-cubic nx <= ny <= nz <= 2 nx on the unit cube (elements of aspect
+    ratio <= 2) with nx*ny*nz closest to E."""
     best = None
-    for nx in range(1, 40):
-        for ny in range(nx, 40):
-            nz = max(1, round(E / (nx * ny)))
-            if nz < ny:
-                continue
+    for nx in range(1, 64):
+        for ny in range(nx, 2 * nx + 1):
+            nz = max(ny, min(2 * nx, round(E / (nx * ny))))
             cand = nx * ny * nz
             err = abs(math.log(cand / E))
             if best is None or err < best[0]:

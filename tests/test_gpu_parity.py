@@ -314,6 +314,37 @@ def test_fp32_variants(variant, name, monkeypatch):
     assert res["status"] == 0 and _residual(P, b, x.cpu().numpy()) <= 1e-10
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("name", ["box_ragged_n7", "box4_n7", "pipe_n3", "pipe_n5", "pipe_n9", "pipe_n11", "box_n1",
+                                  "pipe_open_n4"])
+def test_fp64_double_float_variants(variant, name, monkeypatch):
+    """Every double-float FP64 local-operator variant (direct kernels 0/1,
+    even-odd kernels 2/3 for even n) meets the FP64 bound, plain (h1 = 1 uses
+    the pre-split coefficient table, h1 != 1 the FP64 one) and inside the
+    fused CG iteration of the FP64 solve."""
+    import torch
+    import paper_2109_03592_gb300 as sem
+    monkeypatch.setenv("SEM_FP64_DF_VARIANT", str(variant))
+    m = sem.Mesh(CASES[name])
+    if m.ax_variant(sem.FP64) != variant:
+        assert variant >= 2 and m.n % 2 == 1  # even-odd kernels exist for even n only
+        pytest.skip("variant not available for odd n")
+    assert m.fp64_double_float()
+    _, P = setup(name)
+    u = vectors.local_field(43, m.E, m.n)
+    w = torch.empty(m.shape, dtype=torch.float64, device="cuda")
+    for h1, h2 in [(1.0, 0.0), (0.3, 7.0), (2.5, 0.0), (1.0, 1e-2)]:
+        m.ax(to_gpu(u), w, h1, h2)
+        ref = operator.ax_local(u, P.G, P.B, P.D, h1, h2)
+        assert relerr(w.cpu().numpy(), ref) < AX_TOL, (h1, h2)
+    b = P.rhs(forcing.evaluate(P.mesh.xyz, forcing.random_modes(4, L=3.0)))
+    x = torch.zeros(m.shape, dtype=torch.float64, device="cuda")
+    res = m.solve(to_gpu(b), x, tol=1e-10)
+    assert res["status"] == 0 and _residual(P, b, x.cpu().numpy()) <= 1.1e-10
+    ref = solver.pcg(P, b, tol=1e-10)
+    assert abs(res["iters"] - ref.iters) <= 2
+
+
 def test_fp32_bulk_copy_kernel_unaligned_input():
     """A caller's u that is not 16-byte aligned falls back to a register kernel."""
     import torch
