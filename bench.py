@@ -238,6 +238,23 @@ def serving_stream(count, rate, seed=4):
 
 # ---------------------------------------------------------------- GPU arm
 
+# DRAM bytes (read + write) of one launch of the plain FP32 bulk-copy kernel
+# tma::k_ax_tma<7, 2, 3, false>, from ncu on the E = 32,768 pipe (N = 7):
+# 469,868,800 + 55,497,728 bytes.  The kernel streams its elements once
+# (no reuse across elements), so a launch over E elements moves E / 32,768
+# times that; profiles/k_ax_tma_fp32_pipe32768_n7.md has the command.
+TRAFFIC_E32768_N7 = 469_868_800 + 55_497_728
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of tma::k_ax_tma<7, 2, 3, false> on the "
+                  "E = 32,768 pipe, scaled by the element count")
+
+
+def fp32_ax_traffic(m):
+    import paper_2109_03592_gb300 as sem
+    if m.N != 7 or m.ax_variant(sem.FP32) != 2:  # the FP32 requests must run the measured kernel
+        return None
+    return TRAFFIC_E32768_N7 * m.E / 32768
+
+
 def fp32_kernel_name(N, variant):
     """The FP32 local-operator kernel the autotuner chose (variants 0/1:
     register kernels with ~256/~128 threads per CTA; 2/3: persistent
@@ -381,7 +398,8 @@ def run_gpu(args):
                          "timed": "sem_ax FP32 launches on the bench mesh, CUDA events on the launching stream, "
                                   "after the timed solves (the inner CG runs the fused form of the same kernel)",
                          "achieved": ax32_gbs, "peak": hbm, "unit": "GB/s", "frac": ax32_gbs / hbm,
-                         "peak_kind": peak_kind, "traffic": None,
+                         "peak_kind": peak_kind, "traffic": fp32_ax_traffic(m),
+                         "traffic_source": TRAFFIC_SOURCE,
                          "algorithmic_bytes_per_launch": AX_BYTES["fp32"] * P},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 2 * 8 * P,

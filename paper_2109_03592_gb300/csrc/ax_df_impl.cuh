@@ -100,11 +100,20 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_ax_df(const AxDFParam
   float2* swse = sws + le * n * PL;
   const int64_t base = e * n3 + ij;
 
+  // u - u0 with u0 the value at the element's first point: the stiffness part
+  // annihilates constants, and the shift keeps a smooth field's large mean out
+  // of the contractions' rounding; the mass term and <p, A_L p> add u0 back.
   double ud[n];
   DF ru[n];
+  double u0 = 0.0, beta = 0.0;
+  if (act && FUSED) {
+    beta = P.st->beta;
+    u0 = P.z[e * n3] + beta * P.p[e * n3];
+  }
+  // every thread has read p at the element's first point before its owner overwrites it
+  if (FUSED) __syncthreads();
   if (act) {
     if (FUSED) {
-      const double beta = P.st->beta;
 #pragma unroll
       for (int k = 0; k < n; ++k) {
         const double v = P.z[base + k * n2] + beta * P.p[base + k * n2];
@@ -112,12 +121,13 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_ax_df(const AxDFParam
         ud[k] = v;
       }
     } else {
+      u0 = P.u[e * n3];
 #pragma unroll
       for (int k = 0; k < n; ++k) ud[k] = P.u[base + k * n2];
     }
 #pragma unroll
     for (int k = 0; k < n; ++k) {
-      ru[k] = split64(ud[k]);
+      ru[k] = split64(ud[k] - u0);
       sue[k * PL + j * RP + i] = make_float2(ru[k].h, ru[k].l);
     }
   }
@@ -181,6 +191,7 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_ax_df(const AxDFParam
   if (act) {
     const DF h1 = split64(P.h1);
     const DF h2 = split64(P.h2);
+    const DF c0 = split64(FUSED ? P.p[e * n3] : P.u[e * n3]);  // u0 again (not kept live in registers)
 #pragma unroll
     for (int k = 0; k < n; ++k) {
       Acc acc = rw[k];
@@ -196,13 +207,17 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_ax_df(const AxDFParam
       sc.zero();
       sc.madd(h1.h, h1.l, s.h, s.l);
       if (P.helm) {
-        // + h2 B u, with B = Bhi + Blo and u = (hi, lo)
+        // + h2 B (u - u0) + h2 B u0, with B = Bhi + Blo
         const DF hb = mul_df(h2, DF{P.Bhi[base + k * n2], P.Blo[base + k * n2]});
         sc.madd(hb.h, hb.l, ru[k].h, ru[k].l);
+        sc.madd(hb.h, hb.l, c0.h, c0.l);
       }
       const DF o = sc.result();
       P.w[base + k * n2] = join64(o);
-      if (FUSED) pw.madd(ru[k].h, ru[k].l, o.h, o.l);
+      if (FUSED) {
+        pw.madd(ru[k].h, ru[k].l, o.h, o.l);
+        pw.madd(c0.h, c0.l, o.h, o.l);
+      }
     }
   }
 

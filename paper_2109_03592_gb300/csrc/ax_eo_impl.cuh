@@ -23,7 +23,10 @@
 // rounding errors of the magnitudes summed into s; such a pair enters the
 // next product exactly like a normalised one, so the error stays ~2^-48 of
 // the sum of the magnitudes of each contraction's terms.  h1 is folded into
-// the forward coefficients (an FP64 product, split once per CTA).  All float
+// the forward coefficients (an FP64 product, split once per CTA).  u is split
+// into its float pair from the bit pattern (split_bits), keeping the narrow
+// FP64 pipe for the final hi + lo of w (measured 10% faster at N = 7 than
+// FP64 conversions).  All float
 // operations are explicit _rn intrinsics: the compiler may neither contract
 // nor reorder them.
 #pragma once
@@ -65,6 +68,28 @@ __device__ __forceinline__ void madd(Pair& A, float ah, float al, float bh, floa
   A.c = __fadd_rn(cc, e);
 }
 
+// x = hi + lo from x's bit pattern with integer and FP32 operations only (the
+// FP64 conversions of split64 run on GB300's narrow FP64 pipe): hi is x with
+// its significand truncated to 24 bits, lo the remaining 29 bits rounded to
+// nearest float, so |x - hi - lo| <= 2^-48 |x| for 2^-74 <= |x| < 2^128.
+// Below 2^-74 lo is 0 and below 2^-126 hi is 0 too (entries that small do
+// not change an FP64 result at the 1e-12 level unless the whole field is
+// that small); |x| >= 2^128, infinities and NaNs give a NaN.
+__device__ __forceinline__ Pair split_bits(double x) {
+  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  const unsigned sign = hw & 0x80000000u, ah = hw & 0x7fffffffu;
+  const unsigned hb = __funnelshift_l(lw, ah - (896u << 20), 3) | sign;  // float exponent + 23 significand bits
+  float hi = ah >= (897u << 20) ? __uint_as_float(hb) : 0.f;
+  hi = ah >= (1151u << 20) ? __uint_as_float(0x7fc00000u) : hi;
+  // the 29 remaining significand bits as 23 + 6 exact floats, joined by one rounding
+  const float r1 = __fsub_rn(__uint_as_float(0x4b000000u | ((lw >> 6) & 0x7fffffu)), 8388608.f);
+  const float r0 = __fsub_rn(__uint_as_float(0x4b000000u | (lw & 0x3fu)), 8388608.f);
+  const float r = __fmaf_rn(r1, 64.f, r0);
+  const unsigned sb = (((ah - (948u << 20)) << 3) & 0x7f800000u) | sign;  // +-2^(E-1075), E the biased exponent
+  const float lo = ah >= (949u << 20) ? __fmul_rn(r, __uint_as_float(sb)) : 0.f;
+  return Pair{hi, lo};
+}
+
 // a + b and a - b (TwoSum on the high parts)
 __device__ __forceinline__ Pair add(Pair a, Pair b) {
   const float t = __fadd_rn(a.s, b.s);
@@ -100,8 +125,13 @@ constexpr int eo_threads_per_element() {
   return eo_threads_per_element_v(N);
 }
 
+// Register budget: 640 resident threads per SM (96 registers at 128 threads
+// per CTA, 128 at 256) measured fastest at N = 7 and 11.
+constexpr int eo_min_blocks(int threads) { return 640 / threads < 1 ? 1 : 640 / threads; }
+
 template <int N, int EPB, bool FUSED>
-__global__ void __launch_bounds__(EPB* eo_threads_per_element<N>()) k_ax_eo(const AxDFParams P) {
+__global__ void __launch_bounds__(EPB* eo_threads_per_element<N>(), eo_min_blocks(EPB* eo_threads_per_element<N>()))
+    k_ax_eo(const AxDFParams P) {
   static_assert((N & 1) == 1, "even-odd kernel needs an even number of points per direction");
   constexpr int n = N + 1, h = n / 2, T = h * h * h, n2 = n * n, n3 = n2 * n;
   using L = EoLayout<n>;
@@ -139,10 +169,23 @@ __global__ void __launch_bounds__(EPB* eo_threads_per_element<N>()) k_ax_eo(cons
   // octant point q = da + 2 db + 4 dc is (I[da], J[db], K[dc])
   const int64_t base = e * n3;
 
+  // u - u0 with u0 the value at the element's first point: the stiffness part
+  // annihilates constants, and without the shift a smooth field with a large
+  // mean loses its low-order bits in the contractions (measured 2e-12 instead
+  // of 2e-13 against the FP64 oracle).  The mass term and <p, A_L p> add u0 back.
   Pair u[8];
+  double u0 = 0.0, beta = 0.0;
   if (act) {
-    double beta = 0.0;
-    if (FUSED) beta = P.st->beta;
+    if (FUSED) {
+      beta = P.st->beta;
+      u0 = P.z[base] + beta * P.p[base];
+    } else {
+      u0 = P.u[base];
+    }
+  }
+  // every thread has read p at the element's first point before its owner overwrites it
+  if (FUSED) __syncthreads();
+  if (act) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int64_t g = base + I[q & 1] + n * J[(q >> 1) & 1] + n2 * K[q >> 2];
@@ -153,8 +196,7 @@ __global__ void __launch_bounds__(EPB* eo_threads_per_element<N>()) k_ax_eo(cons
       } else {
         v = P.u[g];
       }
-      const DF d = split64(v);
-      u[q] = Pair{d.h, d.l};
+      u[q] = split_bits(v - u0);
     }
   } else {
 #pragma unroll
@@ -325,20 +367,27 @@ __global__ void __launch_bounds__(EPB* eo_threads_per_element<N>()) k_ax_eo(cons
       }
   }
 
-  Pair pw{0.f, 0.f};  // this thread's part of <p, A_L p>
+  Pair pw{0.f, 0.f};  // this thread's part of <p, A_L p> = <p - u0, w> + u0 * sum(w)
+  Pair sw{0.f, 0.f};
   if (act) {
     const DF h2 = split64(P.h2);
+    const Pair c0 = split_bits(FUSED ? P.p[base] : P.u[base]);  // u0 again (not kept live in registers)
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int64_t gi = base + I[q & 1] + n * J[(q >> 1) & 1] + n2 * K[q >> 2];
       Pair r = o[q];
-      if (P.helm) {  // + h2 B u, B = Bhi + Blo
+      if (P.helm) {  // + h2 B (u - u0) + h2 B u0, B = Bhi + Blo
         const DF hb = mul_df(h2, DF{P.Bhi[gi], P.Blo[gi]});
         r = add(r, prod(hb.h, hb.l, u[q].s, u[q].c));
+        r = add(r, prod(hb.h, hb.l, c0.s, c0.c));
       }
       P.w[gi] = join64(DF{r.s, r.c});
-      if (FUSED) madd(pw, u[q].s, u[q].c, r.s, r.c);
+      if (FUSED) {
+        madd(pw, u[q].s, u[q].c, r.s, r.c);
+        sw = add(sw, r);
+      }
     }
+    if (FUSED) madd(pw, c0.s, c0.c, sw.s, sw.c);
   }
 
   if (FUSED) {

@@ -476,7 +476,7 @@ class EngineImpl {
     launch_minv(ws->minv, ws->minv32, m->dK, m->dB, m->wm, q->o.h1, q->o.h2, ws->n, ws->s);
     ws->minv_h1 = q->o.h1;
     ws->minv_h2 = q->o.h2;
-    SEM_CUDA(ax64(m, ws->x, ws->w, q->o.h1, q->o.h2, false, nullptr, nullptr, nullptr, nullptr, ws->s));
+    SEM_CUDA(ax64_exact(m, ws->x, ws->w, q->o.h1, q->o.h2, ws->s));
     SEM_CUDA(launch_gs<double>(ws->w, gs_dev(m), 1, nullptr, ws->s));
     SEM_CUDA(launch_residual(ws->r, ws->b, ws->w, m->wm, ws->n, ws->st, ws->part_vec, 1, ws->s));
     count_launches(5);
@@ -550,7 +550,7 @@ class EngineImpl {
     if (err || fin.status == SEM_ERR_DEVICE_TIMEOUT) return finish(q, SEM_ERR_DEVICE_TIMEOUT, 0.0, fin.iter);
     if (fin.status == SEM_ERR_BREAKDOWN || fin.status == SEM_ERR_NOT_CONVERGED)
       return finish(q, (sem_status)fin.status, std::sqrt(fin.rr), fin.iter);
-    SEM_CUDA(ax64(m, ws->x, ws->w, q->o.h1, q->o.h2, false, nullptr, nullptr, nullptr, nullptr, ws->s));
+    SEM_CUDA(ax64_exact(m, ws->x, ws->w, q->o.h1, q->o.h2, ws->s));
     SEM_CUDA(launch_gs<double>(ws->w, gs_dev(m), 1, nullptr, ws->s));
     SEM_CUDA(launch_residual(ws->r, ws->b, ws->w, m->wm, ws->n, ws->st, ws->part_vec, 0, ws->s));
     count_launches(3);

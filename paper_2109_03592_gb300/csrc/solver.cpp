@@ -101,6 +101,17 @@ cudaError_t ax64(const sem_mesh* m, const double* u, double* w, double h1, doubl
   return launch_ax_f64(m->N, m->ax_var[0], fused, a, s, nullptr);
 }
 
+// The native FP64 operator.  The residuals b - A x that decide convergence
+// (the outer residuals of the mixed-precision solvers and the final check of
+// the FP64 solver) use it: near convergence b - A x cancels to ~1e-10 of the
+// terms summed, so the double-float kernel's ~2^-48 rounding, 30x coarser
+// than FP64's, would set the attainable residual (measured: the E = 262,144
+// pipe stalled above 1e-10 with a 2^-46 input split).
+cudaError_t ax64_exact(const sem_mesh* m, const double* u, double* w, double h1, double h2, cudaStream_t s) {
+  AxParams<double> a{u, w, m->G64, m->B64, m->D64, h1, h2, h2 != 0.0, m->E, nullptr, nullptr, nullptr, nullptr};
+  return launch_ax_f64(m->N, m->ax_var[0], false, a, s, nullptr);
+}
+
 static cudaError_t ax32(const sem_mesh* m, const float* u, float* w, double h1, double h2, bool fused,
                         const float* z, float* p, PcgState* st, double* part, cudaStream_t s) {
   AxParams<float> a{u, w, m->G32, m->B32, m->D32, (float)h1, (float)h2, h2 != 0.0, m->E, z, p, st, part, m->dev_err};
@@ -360,35 +371,55 @@ struct SolveOut {
   double rel = 0.0;
 };
 
-// Plain FP64 PCG on ws->b with initial guess ws->x.
+// Plain FP64 PCG on ws->b with initial guess ws->x.  The CG recurrences
+// run with the autotuned (double-float or native) fused operator; when the
+// recurrence meets the tolerance, the true residual b - A x is recomputed with
+// the native FP64 operator and, if it is still above the tolerance (the
+// recurrence drifted), CG restarts from x (at most kMaxRestarts times, within
+// maxit iterations in total).  res.rel is that true residual.
 static sem_status pcg64(sem_mesh* m, Workspace* ws, const sem_solve_opts& o, int maxit, SolveOut& res) {
+  constexpr int kMaxRestarts = 3;
   sem_status st = get_graph(m, ws, false, o.h1, o.h2);
   if (st != SEM_OK) return st;
-  st = put_state(ws, o.tol, maxit, 0);
-  if (st != SEM_OK) return st;
-  SEM_CUDA(ax64(m, ws->x, ws->w, o.h1, o.h2, false, nullptr, nullptr, nullptr, nullptr, ws->s));
-  SEM_CUDA(launch_gs<double>(ws->w, gs_dev(m), 1, nullptr, ws->s));
-  SEM_CUDA(launch_residual(ws->r, ws->b, ws->w, m->wm, ws->n, ws->st, ws->part_vec, 1, ws->s));
-  VecParams<double> v{ws->x, ws->r, ws->z, ws->p, ws->w, ws->minv, ws->b, m->wm, ws->n, ws->st, ws->part_vec};
-  SEM_CUDA(launch_pcg_init<double>(v, ws->s));
-  count_launches(4);
-  PcgState s0;
-  st = read_state(ws, s0);
-  if (st != SEM_OK) return st;
-  if (s0.bb == 0.0) {
-    SEM_CUDA(cudaMemsetAsync(ws->x, 0, ws->n * sizeof(double), ws->s));
-    res.rel = 0.0;
-    return SEM_OK;
-  }
-  PcgState fin = s0;
-  if (!s0.done) {
-    st = run_chunks(ws, ws->g64.exec, maxit, fin);
+  res.iters = 0;
+  for (int pass = 0;; ++pass) {
+    st = put_state(ws, o.tol, maxit - res.iters, 0);
     if (st != SEM_OK) return st;
+    SEM_CUDA(ax64_exact(m, ws->x, ws->w, o.h1, o.h2, ws->s));
+    SEM_CUDA(launch_gs<double>(ws->w, gs_dev(m), 1, nullptr, ws->s));
+    SEM_CUDA(launch_residual(ws->r, ws->b, ws->w, m->wm, ws->n, ws->st, ws->part_vec, 1, ws->s));
+    VecParams<double> v{ws->x, ws->r, ws->z, ws->p, ws->w, ws->minv, ws->b, m->wm, ws->n, ws->st, ws->part_vec};
+    SEM_CUDA(launch_pcg_init<double>(v, ws->s));
+    count_launches(4);
+    PcgState s0;
+    st = read_state(ws, s0);
+    if (st != SEM_OK) return st;
+    if (s0.bb == 0.0) {
+      SEM_CUDA(cudaMemsetAsync(ws->x, 0, ws->n * sizeof(double), ws->s));
+      res.rel = 0.0;
+      res.status = SEM_OK;
+      return SEM_OK;
+    }
+    res.rel = std::sqrt(s0.aux / s0.bb);  // true residual of the current x
+    res.outer = pass;
+    if (res.rel <= o.tol) {
+      res.status = SEM_OK;
+      return SEM_OK;
+    }
+    if (pass > kMaxRestarts || res.iters >= maxit) {
+      res.status = SEM_ERR_NOT_CONVERGED;
+      return SEM_OK;
+    }
+    PcgState fin = s0;
+    st = run_chunks(ws, ws->g64.exec, maxit - res.iters, fin);
+    if (st != SEM_OK) return st;
+    res.iters += fin.iter;
+    if (fin.status != SEM_OK) {  // breakdown, or maxit without meeting the tolerance
+      res.rel = std::sqrt(fin.rr / fin.bb);
+      res.status = fin.status;
+      return SEM_OK;
+    }
   }
-  res.iters = fin.iter;
-  res.rel = std::sqrt(fin.rr / fin.bb);
-  res.status = fin.status;
-  return SEM_OK;
 }
 
 // FP64 refinement around FP32 inner PCG (max_outer = 1 and inner_tol = tol
@@ -400,7 +431,7 @@ static sem_status pcg_mixed(sem_mesh* m, Workspace* ws, const sem_solve_opts& o,
   st = put_state(ws, inner_tol, maxit, 0);  // zero arrival counters before the first reduction
   if (st != SEM_OK) return st;
   for (int outer = 0;; ++outer) {
-    SEM_CUDA(ax64(m, ws->x, ws->w, o.h1, o.h2, false, nullptr, nullptr, nullptr, nullptr, ws->s));
+    SEM_CUDA(ax64_exact(m, ws->x, ws->w, o.h1, o.h2, ws->s));
     SEM_CUDA(launch_gs<double>(ws->w, gs_dev(m), 1, nullptr, ws->s));
     SEM_CUDA(launch_residual(ws->r, ws->b, ws->w, m->wm, ws->n, ws->st, ws->part_vec, 1, ws->s));
     count_launches(3);
@@ -459,7 +490,7 @@ static sem_status pcg_mixed_reliable(sem_mesh* m, Workspace* ws, const sem_solve
   if (st != SEM_OK) return st;
   st = put_state(ws, o.tol, maxit, 0);  // zero arrival counters before the first reduction
   if (st != SEM_OK) return st;
-  SEM_CUDA(ax64(m, ws->x, ws->w, o.h1, o.h2, false, nullptr, nullptr, nullptr, nullptr, ws->s));
+  SEM_CUDA(ax64_exact(m, ws->x, ws->w, o.h1, o.h2, ws->s));
   SEM_CUDA(launch_gs<double>(ws->w, gs_dev(m), 1, nullptr, ws->s));
   SEM_CUDA(launch_residual(ws->r, ws->b, ws->w, m->wm, ws->n, ws->st, ws->part_vec, 1, ws->s));
   count_launches(3);
@@ -500,7 +531,7 @@ static sem_status pcg_mixed_reliable(sem_mesh* m, Workspace* ws, const sem_solve
       res.status = fin.status;
       return SEM_OK;
     }
-    SEM_CUDA(ax64(m, ws->x, ws->w, o.h1, o.h2, false, nullptr, nullptr, nullptr, nullptr, ws->s));
+    SEM_CUDA(ax64_exact(m, ws->x, ws->w, o.h1, o.h2, ws->s));
     SEM_CUDA(launch_gs<double>(ws->w, gs_dev(m), 1, nullptr, ws->s));
     SEM_CUDA(launch_residual(ws->r, ws->b, ws->w, m->wm, ws->n, ws->st, ws->part_vec, 0, ws->s));
     count_launches(3);

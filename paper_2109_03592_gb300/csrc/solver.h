@@ -27,6 +27,8 @@ struct Workspace {
 
 sem_status alloc_ws(sem_mesh* m, Workspace** out);
 // FP64 local operator with the mesh's tuned kernel (native or double-float).
+// w = A_L u with the native FP64 kernel (exact FP64 arithmetic)
+cudaError_t ax64_exact(const sem_mesh* m, const double* u, double* w, double h1, double h2, cudaStream_t s);
 cudaError_t ax64(const sem_mesh* m, const double* u, double* w, double h1, double h2, bool fused, const double* z,
                  double* p, PcgState* st, double* part, cudaStream_t s);
 // Write a fresh PcgState (tol, maxit, done) to ws->st / read it back (both synchronise ws->s).

@@ -345,6 +345,36 @@ def test_fp64_double_float_variants(variant, name, monkeypatch):
     assert abs(res["iters"] - ref.iters) <= 2
 
 
+@pytest.mark.parametrize("kernel", ["native", "df0", "df1", "df2", "df3"])
+@pytest.mark.parametrize("name", ["box4_n7", "pipe_n5", "pipe_n11", "box_ragged_n7"])
+def test_ax_fp64_smooth_fields(kernel, name, monkeypatch):
+    """A smooth field with a mean: the stiffness part cancels the mean, so
+    rounding of its low-order bits is amplified; every FP64 kernel must still
+    meet the FP64 bound (the double-float kernels shift by the element's first
+    value before contracting).  A mean of 2 costs FP64 arithmetic itself ~1e-13
+    here; much larger means are not a 1e-12 test of anything, because the
+    oracle's rounded D no longer annihilates constants to that level."""
+    import torch
+    import paper_2109_03592_gb300 as sem
+    if kernel == "native":
+        monkeypatch.setenv("SEM_FP64_KERNEL", "native")
+    else:
+        monkeypatch.setenv("SEM_FP64_DF_VARIANT", kernel[2])
+    m = sem.Mesh(CASES[name])
+    if kernel != "native" and m.ax_variant(sem.FP64) != int(kernel[2]):
+        pytest.skip("variant not available for odd n")
+    assert m.fp64_double_float() == (kernel != "native")
+    _, P = setup(name)
+    x, y, z = (P.mesh.xyz[:, a] for a in range(3))
+    for off in (0.0, 2.0):
+        u = np.sin(np.pi * x) * np.cos(0.5 * np.pi * y) * np.sin(0.7 * z + 0.3) + off
+        w = torch.empty(m.shape, dtype=torch.float64, device="cuda")
+        for h1, h2 in [(1.0, 0.0), (0.3, 7.0)]:
+            m.ax(to_gpu(u), w, h1, h2)
+            ref = operator.ax_local(u, P.G, P.B, P.D, h1, h2)
+            assert relerr(w.cpu().numpy(), ref) < AX_TOL, (off, h1, h2, relerr(w.cpu().numpy(), ref))
+
+
 def test_fp32_bulk_copy_kernel_unaligned_input():
     """A caller's u that is not 16-byte aligned falls back to a register kernel."""
     import torch
