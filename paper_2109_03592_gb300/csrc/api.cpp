@@ -59,6 +59,7 @@ void free_mesh_arrays(sem_mesh* m) {
   dev_free(m->wm);
   dev_free(m->gs_idx);
   dev_free(m->gs_ptr);
+  dev_free(m->gs_units);
   dev_free(m->D64);
   dev_free(m->dev_err);
   dev_free(m->D32);
@@ -141,6 +142,8 @@ sem_status build_mesh(const sem_mesh_desc& d, cudaStream_t s, sem_mesh* m) {
   SEM_TRY(dev_alloc(&m->wm, P, tb));
   SEM_TRY(dev_alloc(&m->gs_idx, plan.idx.size(), tb));
   SEM_TRY(dev_alloc(&m->gs_ptr, plan.gptr.size(), tb));
+  SEM_TRY(dev_alloc(&m->gs_units, std::max<size_t>(plan.units.size(), 4), tb));
+  m->gs_nunits = (int64_t)plan.units.size() / 4;
   SEM_TRY(dev_alloc(&m->D64, n * n, tb));
   SEM_TRY(dev_alloc(&m->dev_err, 1, tb));
   SEM_TRY(dev_alloc(&m->D32, n * n, tb));
@@ -184,6 +187,8 @@ sem_status build_mesh(const sem_mesh_desc& d, cudaStream_t s, sem_mesh* m) {
   if (!plan.idx.empty())
     SEM_CUDA(cudaMemcpyAsync(m->gs_idx, plan.idx.data(), plan.idx.size() * 4, cudaMemcpyHostToDevice, s));
   SEM_CUDA(cudaMemcpyAsync(m->gs_ptr, plan.gptr.data(), plan.gptr.size() * 4, cudaMemcpyHostToDevice, s));
+  if (!plan.units.empty())
+    SEM_CUDA(cudaMemcpyAsync(m->gs_units, plan.units.data(), plan.units.size() * 4, cudaMemcpyHostToDevice, s));
 
   std::vector<double> tlev;
   if (d.kind == SEM_MESH_BOX) {

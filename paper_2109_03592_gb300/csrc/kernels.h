@@ -84,6 +84,8 @@ struct GsDev {
   const int32_t* gptr;
   int64_t off[9];
   int64_t cnt[9];
+  const int4* units;  // {class, first node, count, 0} in processing order
+  int64_t nunits;
 };
 template <typename T>
 cudaError_t launch_gs(T* v, const GsDev& g, int apply_mask, const PcgState* st, cudaStream_t s);

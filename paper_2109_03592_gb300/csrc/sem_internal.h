@@ -51,12 +51,22 @@ sem_status build_numbering(int64_t E, int N, const int64_t* vert, Topology& t);
 // each).  Bit 31 of a node's first index flags a Dirichlet node.  Every
 // class starts at a multiple of 4 entries of `idx` (16-byte aligned).
 constexpr int kGsClasses = 9;
+constexpr int kGsUnitNodes = 256;        // nodes per work unit (one per thread of a CTA)
+constexpr int64_t kGsWindow = 1 << 21;   // global ids per ordering window
 struct GsPlan {
   std::vector<int32_t> idx;
   std::vector<int32_t> gptr;             // CSR offsets (relative to the class start) of class 7
   int64_t off[kGsClasses] = {0};         // class start in idx
   int64_t cnt[kGsClasses] = {0};         // nodes per class
   int64_t n_nodes = 0, n_points = 0;     // shared-or-Dirichlet nodes and their local points
+  // Work units of the gather-scatter kernel, in processing order: up to
+  // kGsUnitNodes consecutive nodes of one class, {class, first node within
+  // the class, node count, 0}.  Units are ordered window by window over the
+  // global ids (kGsWindow ids each) and class by class inside a window, so the
+  // face, edge and vertex nodes that share the same rows of the same
+  // elements are processed close together in time (their sectors are still
+  // in L2), instead of in one pass per class over the whole vector.
+  std::vector<int32_t> units;
   std::vector<uint8_t> wm;               // per local point: multiplicity | 0x80 if Dirichlet
 };
 sem_status build_gs_plan(const Topology& t, const uint8_t* dirichlet_face, GsPlan& plan);
@@ -89,6 +99,8 @@ struct sem_mesh {
   uint8_t* wm = nullptr;     // [n_local] multiplicity | 0x80 Dirichlet
   int32_t* gs_idx = nullptr;   // GsPlan::idx
   int32_t* gs_ptr = nullptr;   // GsPlan::gptr
+  int32_t* gs_units = nullptr; // GsPlan::units
+  int64_t gs_nunits = 0;
   int64_t gs_off[9] = {0}, gs_cnt[9] = {0};
   int* dev_err = nullptr;    // device error word of the bulk-copy kernels (0 = ok)
   double* D64 = nullptr;     // [n*n] D (row i: d/dr at xi_i)
@@ -116,6 +128,8 @@ inline GsDev gs_dev(const sem_mesh* m) {
   GsDev g;
   g.idx = m->gs_idx;
   g.gptr = m->gs_ptr;
+  g.units = reinterpret_cast<const int4*>(m->gs_units);
+  g.nunits = m->gs_nunits;
   for (int c = 0; c < 9; ++c) {
     g.off[c] = m->gs_off[c];
     g.cnt[c] = m->gs_cnt[c];

@@ -436,6 +436,46 @@ sem_status build_gs_plan(const Topology& t, const uint8_t* dface, GsPlan& plan) 
       ++gnode;
     }
   }
+  // work units, window by window over the global ids, class by class inside
+  {
+    int64_t done[kGsClasses] = {0};  // nodes of each class with a global id below the window's end
+    const int64_t win = kGsWindow;
+    for (int64_t g0 = 0; g0 < t.n_global; g0 += win) {
+      const int64_t g1 = std::min<int64_t>(t.n_global, g0 + win);
+      int64_t upto[kGsClasses];
+      for (int c = 0; c < kGsClasses; ++c) upto[c] = done[c];
+      for (int64_t g = g0; g < g1; ++g) {
+        const int c = cls_of(g);
+        if (c >= 0) ++upto[c];
+      }
+      for (int c = 0; c < kGsClasses; ++c) {
+        for (int64_t q = done[c]; q < upto[c]; q += kGsUnitNodes) {
+          plan.units.push_back(c);
+          plan.units.push_back((int32_t)q);
+          plan.units.push_back((int32_t)std::min<int64_t>(kGsUnitNodes, upto[c] - q));
+          plan.units.push_back(0);
+        }
+        done[c] = upto[c];
+      }
+    }
+    // the units of each class tile its nodes exactly, in order (the kernel
+    // indexes tuples by them without further checks)
+    int64_t next[kGsClasses] = {0};
+    for (size_t u = 0; u + 3 < plan.units.size(); u += 4) {
+      const int c = plan.units[u];
+      if (c < 0 || c >= kGsClasses || plan.units[u + 1] != next[c] || plan.units[u + 2] < 1 ||
+          plan.units[u + 2] > kGsUnitNodes) {
+        set_error("gs plan: inconsistent work units");
+        return SEM_ERR_INVALID;
+      }
+      next[c] += plan.units[u + 2];
+    }
+    for (int c = 0; c < kGsClasses; ++c)
+      if (next[c] != plan.cnt[c]) {
+        set_error("gs plan: work units do not cover every node");
+        return SEM_ERR_INVALID;
+      }
+  }
   // local points in ascending local index fill each tuple in ascending order
   std::vector<int32_t> seen(t.n_global, 0);
   for (int64_t l = 0; l < t.n_local; ++l) {
