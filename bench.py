@@ -236,6 +236,52 @@ def serving_stream(count, rate, seed=4):
             "mix": "box/pipe, E log-uniform in [512, 4096], N in {5,7,9}, Poisson/Helmholtz, tol 1e-10"}
 
 
+# ---------------------------------------------------------------- projection leg
+
+def projection_leg(count=6, max_vectors=8, workload="pipe32768_n7"):
+    """Successive solves with slowly varying right-hand sides (as over time
+    steps): the 64-mode random field with every phase advancing at its own
+    rate, f_j = sum_m a_m cos(k_m x + phi_m + w_m t_j), w_m ~ U[0.5, 1.5],
+    t_j = 0.05 j (the right-hand sides leave any finite span); mixed precision
+    to 1e-10, with and without the projection space of earlier solutions
+    (sem_proj_*)."""
+    import numpy as np
+    import torch
+    import paper_2109_03592_gb300 as sem
+    from sem_inputs import configs, forcing
+    desc = configs.mesh_desc(workload)
+    m = sem.Mesh(desc)
+    xyz = m.coords()
+    a, k, phi = forcing.random_modes(5, L=desc.get("L", 8.0))
+    w = np.random.default_rng(7).uniform(0.5, 1.5, a.size)
+    proj = sem.Projection(m, max_vectors=max_vectors)
+    b = torch.empty(m.shape, dtype=torch.float64, device="cuda")
+    x = torch.empty_like(b)
+    out = {"with": {"iters": [], "ms": []}, "without": {"iters": [], "ms": []}}
+    for j in range(count):
+        m.rhs(forcing.evaluate_torch(xyz, (a, k, phi + w * 0.05 * j)), b)
+        r = proj.solve(b, x, tol=1e-10, prec=sem.MIXED)
+        if r["status"] != 0:
+            raise RuntimeError(f"projected solve failed: {r}")
+        out["with"]["iters"].append(r["iters"])
+        out["with"]["ms"].append(r["ms"])
+        x.zero_()
+        r = m.solve(b, x, tol=1e-10, prec=sem.MIXED)
+        out["without"]["iters"].append(r["iters"])
+        out["without"]["ms"].append(r["ms"])
+    del xyz
+    proj.close()
+    m.close()
+    tw, to = sum(out["with"]["ms"]), sum(out["without"]["ms"])
+    return {"workload": f"{workload}: E={desc_elements(desc)} N={desc['N']}", "solves": count,
+            "max_vectors": max_vectors, **out, "time_ratio": tw / to if to > 0 else None,
+            "note": "first solve has an empty space; ms includes projection and basis update"}
+
+
+def desc_elements(d):
+    return d["nx"] * d["ny"] * d["nz"] if d["kind"] == "box" else d["nc"] * (d["nc"] + 4 * d["nr"]) * d["nzp"]
+
+
 # ---------------------------------------------------------------- GPU arm
 
 # DRAM bytes (read + write) of one launch of the plain FP32 bulk-copy kernel
@@ -367,6 +413,9 @@ def run_gpu(args):
     serving = None
     if not args.no_serving:
         serving = serving_stream(args.serving_requests, args.serving_rate)
+    proj = None
+    if not args.no_projection:
+        proj = projection_leg()
 
     line = None
     if rank == 0:
@@ -394,6 +443,7 @@ def run_gpu(args):
             "gs": {"fp64_ms": gs64_ms, "fp32_ms": gs32_ms},
             "fp64_pcg": fp64,
             "serving": serving,
+            "projection": proj,
             "roofline": {"bound": "hbm", "kernel": fp32_kernel_name(m.N, m.ax_variant(sem.FP32)),
                          "timed": "sem_ax FP32 launches on the bench mesh, CUDA events on the launching stream, "
                                   "after the timed solves (the inner CG runs the fused form of the same kernel)",
@@ -422,6 +472,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--quick", action="store_true", help="skip the FP64 PCG comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-projection", action="store_true", help="skip the projection leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream leg")
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--serving-rate", type=float, default=20.0)

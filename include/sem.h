@@ -240,6 +240,43 @@ sem_status sem_pcg_solve_batch(const sem_mesh* const* meshes, const double* cons
 sem_status sem_pcg_solve_noalloc(const sem_mesh* mesh, const double* b_dev, double* x_dev,
                                  const sem_solve_opts* opts, sem_solve_result* result, void* stream);
 
+/* ---- projection onto previous solutions --------------------------------- */
+/* Sec. 2 (the velocity and pressure solves) accelerates successive solves
+ * with one operator by projecting each new solution onto the space spanned by
+ * earlier ones (the paper cites Fischer 1998 for it).  A space holds an
+ * A-orthonormal basis x_1..x_l of earlier solutions (global inner product,
+ * x_i^T A x_j = delta_ij) and A x_i, in library-owned device memory; a solve
+ * starts CG from xbar = sum_i (x_i^T b) x_i, the best approximation to
+ * A^{-1} b from the space in the A-norm, then A-orthogonalises the increment
+ * x - xbar against the basis (two Gram-Schmidt passes), A-normalises it and
+ * appends it; a full basis restarts from the newest solution alone. */
+typedef struct sem_proj sem_proj;
+
+/* Projection space for the operator (h1, h2) of one mesh: max_vectors in
+ * 1..SEM_PROJ_MAX_VECTORS; allocates 2 * max_vectors + 3 local vectors of
+ * doubles on the mesh's device.  The mesh must outlive the space.  Errors:
+ * SEM_ERR_INVALID (null mesh/out, bad count, h1/h2 as in sem_pcg_solve),
+ * SEM_ERR_OOM. */
+#define SEM_PROJ_MAX_VECTORS 16
+sem_status sem_proj_create(const sem_mesh* mesh, int max_vectors, double h1, double h2, sem_proj** out);
+sem_status sem_proj_destroy(sem_proj* proj);
+
+/* Solves A x = b as sem_pcg_solve does (same b/x layout, opts and result;
+ * opts->h1, h2 must equal the space's, else SEM_ERR_INVALID), except that x_dev
+ * is output only: the initial guess is the projection of b onto the space.
+ * After a converged solve the new direction joins the space; after a failed
+ * one the space is unchanged.  result->iters counts the CG iterations after
+ * the projection; result->ms covers projection, solve and update.  Not thread
+ * safe for one space; spaces of different meshes are independent. */
+sem_status sem_proj_solve(sem_proj* proj, const double* b_dev, double* x_dev, const sem_solve_opts* opts,
+                          sem_solve_result* result, void* stream);
+
+/* Number of basis vectors held (0..max_vectors). */
+sem_status sem_proj_size(const sem_proj* proj, int* nvec);
+
+/* Empties the space (after the operator or the mesh changed). */
+sem_status sem_proj_reset(sem_proj* proj);
+
 /* ---- serving ------------------------------------------------------------ */
 
 typedef struct {

@@ -85,6 +85,11 @@ SIGNATURES = {
     "sem_apply": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, _P]),
     "sem_jacobi": (C.c_int, [_P, C.c_double, C.c_double, _P, _P]),
     "sem_pcg_solve": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
+    "sem_proj_create": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.POINTER(_P)]),
+    "sem_proj_destroy": (C.c_int, [_P]),
+    "sem_proj_solve": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
+    "sem_proj_size": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "sem_proj_reset": (C.c_int, [_P]),
     "sem_pcg_solve_host": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
     "sem_pcg_solve_noalloc": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
     "sem_pcg_solve_batch": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), C.c_int, _P]),
@@ -369,6 +374,49 @@ def mesh_vertices(desc):
     out = np.empty((E.value, 8), dtype=np.int64)
     _check(lib().sem_mesh_vertices(C.byref(d), out.ctypes.data, C.byref(E)), "sem_mesh_vertices")
     return out
+
+
+class Projection:
+    """Projection space of earlier solutions for one mesh and one operator
+    (sem_proj_*): solve() starts CG from the projection of b onto the space
+    and adds the new direction to it."""
+
+    def __init__(self, mesh, max_vectors=8, h1=1.0, h2=0.0):
+        h = C.c_void_p()
+        _check(lib().sem_proj_create(mesh._h, int(max_vectors), float(h1), float(h2), C.byref(h)), "sem_proj_create")
+        self._h, self.mesh, self.h1, self.h2 = h, mesh, float(h1), float(h2)
+
+    def solve(self, b, x, stream=None, check=False, **opts):
+        import torch
+        opts.setdefault("h1", self.h1)
+        opts.setdefault("h2", self.h2)
+        o = _opts(**opts)
+        r = SolveResult()
+        n = self.mesh.n_local
+        st = lib().sem_proj_solve(self._h, _dptr(b, torch.float64, n), _dptr(x, torch.float64, n), C.byref(o),
+                                  C.byref(r), _stream(stream))
+        if st not in (SEM_OK, SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN) or (check and st != SEM_OK):
+            _check(st, "sem_proj_solve")
+        return r.as_dict()
+
+    def size(self):
+        k = C.c_int()
+        _check(lib().sem_proj_size(self._h, C.byref(k)), "sem_proj_size")
+        return k.value
+
+    def reset(self):
+        _check(lib().sem_proj_reset(self._h), "sem_proj_reset")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sem_proj_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:
