@@ -1,0 +1,70 @@
+"""Command-line solves on the synthetic workloads, for scripting and profiling.
+
+    python -m paper_2109_03592_gb300.cli solve --workload pipe32768_n7 --prec fp64 [--repeat 2]
+    python -m paper_2109_03592_gb300.cli ax --workload pipe262144_n7 --prec fp64 [--reps 10]
+
+Prints one JSON line per solve (the sem_pcg_solve result) or per operator
+timing (CUDA events on the launching stream).
+"""
+
+import argparse
+import json
+import sys
+
+
+def _mesh_and_rhs(workload):
+    import torch
+    from sem_inputs import configs, forcing
+    from . import sem
+    desc = configs.mesh_desc(workload)
+    m = sem.Mesh(desc)
+    xyz = m.coords()
+    f = forcing.evaluate_torch(xyz, forcing.random_modes(2, L=desc.get("L", 8.0)))
+    del xyz
+    b = torch.empty_like(f)
+    m.rhs(f, b)
+    return m, b
+
+
+def main(argv=None):
+    from . import sem
+    ap = argparse.ArgumentParser(prog="python -m paper_2109_03592_gb300.cli")
+    ap.add_argument("what", choices=["solve", "ax"])
+    ap.add_argument("--workload", default="pipe32768_n7")
+    ap.add_argument("--prec", default="mixed", choices=["fp64", "fp32", "mixed"])
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--reps", type=int, default=10)
+    args = ap.parse_args(argv)
+    import torch
+    prec = {"fp64": sem.FP64, "fp32": sem.FP32, "mixed": sem.MIXED}[args.prec]
+    m, b = _mesh_and_rhs(args.workload)
+    if args.what == "solve":
+        x = torch.zeros_like(b)
+        for _ in range(args.repeat):
+            x.zero_()
+            r = m.solve(b, x, tol=args.tol, prec=prec)
+            print(json.dumps({"workload": args.workload, "prec": args.prec, **r}), flush=True)
+    else:
+        dt = torch.float32 if prec == sem.FP32 else torch.float64
+        u = torch.randn(m.shape, dtype=dt, device="cuda")
+        w = torch.empty_like(u)
+        p = sem.FP32 if prec == sem.FP32 else sem.FP64
+        for _ in range(3):
+            m.ax(u, w, prec=p)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(args.reps):
+            m.ax(u, w, prec=p)
+        e.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e) / args.reps
+        print(json.dumps({"workload": args.workload, "prec": args.prec, "ms": ms,
+                          "gdofs": m.E * m.N ** 3 / ms / 1e6, "variant": m.ax_variant(p)}), flush=True)
+    m.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
