@@ -390,23 +390,9 @@ __global__ void __launch_bounds__(EPB* eo_threads_per_element<N>(), eo_min_block
     if (FUSED) madd(pw, c0.s, c0.c, sw.s, sw.c);
   }
 
-  if (FUSED) {
+  if (FUSED) {  // this block's part of <p, A_L p>; k_pap_finish sums the parts in block order
     const double s = block_sum((double)pw.s + (double)pw.c, sred);
     if (tid == 0) P.partial[blockIdx.x] = s;
-    if (last_block(&P.st->cnt[0])) {
-      const double pAp = sum_partials(P.partial, gridDim.x, 1, 0, sred);
-      if (tid == 0) {
-        PcgState* st = P.st;
-        st->pAp = pAp;
-        if (!(pAp > 0.0)) {
-          st->done = 1;
-          st->status = 5;  // SEM_ERR_BREAKDOWN
-        } else {
-          st->alpha = st->rho / pAp;
-        }
-        st->cnt[0] = 0;
-      }
-    }
   }
 }
 
@@ -426,7 +412,11 @@ cudaError_t launch_eo_t(const AxDFParams& p, cudaStream_t s, int* grid_out) {
   if (grid_out) *grid_out = (int)grid;
   if (p.E == 0) return cudaSuccess;
   k_ax_eo<N, EPB, FUSED><<<(unsigned)grid, EPB * eo_threads_per_element<N>(), smem, s>>>(p);
-  return cudaGetLastError();
+  cudaError_t err = cudaGetLastError();
+  // a separate one-CTA sum of the block partials: the operator's 1e4-1e5
+  // blocks then need no grid-wide arrival counter (fence + atomic per block)
+  if (FUSED && err == cudaSuccess) err = launch_pap_finish(p.partial, (int)grid, p.st, s);
+  return err;
 }
 
 constexpr int epb_eo(int N, int variant) {

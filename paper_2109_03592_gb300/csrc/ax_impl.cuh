@@ -112,23 +112,9 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_ax(const AxParams<T> 
     }
   }
 
-  if (FUSED) {
+  if (FUSED) {  // this block's part of <p, A_L p>; k_pap_finish sums the parts in block order
     const double s = block_sum((double)pw, sred);
     if (tid == 0) P.partial[blockIdx.x] = s;
-    if (last_block(&P.st->cnt[0])) {
-      const double pAp = sum_partials(P.partial, gridDim.x, 1, 0, sred);
-      if (tid == 0) {
-        PcgState* st = P.st;
-        st->pAp = pAp;
-        if (!(pAp > 0.0)) {
-          st->done = 1;
-          st->status = 5;  // SEM_ERR_BREAKDOWN
-        } else {
-          st->alpha = st->rho / pAp;
-        }
-        st->cnt[0] = 0;
-      }
-    }
   }
 }
 
@@ -153,7 +139,9 @@ cudaError_t launch_ax_t(const AxParams<T>& p, cudaStream_t s, int* grid_out) {
   if (grid_out) *grid_out = (int)grid;
   if (p.E == 0) return cudaSuccess;
   k_ax<N, T, EPB, FUSED><<<(unsigned)grid, EPB * n * n, smem, s>>>(p);
-  return cudaGetLastError();
+  cudaError_t err = cudaGetLastError();
+  if (FUSED && err == cudaSuccess) err = launch_pap_finish(p.partial, (int)grid, p.st, s);
+  return err;
 }
 
 // Elements per block: about 256 threads (variant 0) or about 128 (variant 1).

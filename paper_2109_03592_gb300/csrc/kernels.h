@@ -126,5 +126,7 @@ void launch_scale_to_f32(float* r32, const double* r, double sc, int64_t n, cuda
 // x += sc * double(d32)
 void launch_accumulate(double* x, const float* d32, double sc, int64_t n, cudaStream_t s);
 void launch_zero_f32(float* a, int64_t n, cudaStream_t s);
+// pAp and alpha from the per-block partials of a fused local operator
+cudaError_t launch_pap_finish(const double* partial, int count, PcgState* st, cudaStream_t s);
 
 }  // namespace sem

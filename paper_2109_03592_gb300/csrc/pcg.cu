@@ -372,6 +372,27 @@ __global__ void k_set_bb(PcgState* st, double bb, double delta2) {
 }
 void launch_set_bb(PcgState* st, double bb, double delta2, cudaStream_t s) { k_set_bb<<<1, 1, 0, s>>>(st, bb, delta2); }
 
+// pAp = fixed-order sum of a fused local operator's per-block partials; then
+// alpha = rho / pAp, or a breakdown (one CTA, after the operator's launch)
+__global__ void __launch_bounds__(1024) k_pap_finish(const double* __restrict__ partial, int count, PcgState* st) {
+  __shared__ double sred[32];
+  if (st->done) return;
+  const double pAp = sum_partials(partial, count, 1, 0, sred);
+  if (threadIdx.x == 0) {
+    st->pAp = pAp;
+    if (!(pAp > 0.0)) {
+      st->done = 1;
+      st->status = 5;  // SEM_ERR_BREAKDOWN
+    } else {
+      st->alpha = st->rho / pAp;
+    }
+  }
+}
+cudaError_t launch_pap_finish(const double* partial, int count, PcgState* st, cudaStream_t s) {
+  k_pap_finish<<<1, 1024, 0, s>>>(partial, count, st);
+  return cudaGetLastError();
+}
+
 __global__ void k_zero_f32(float* a, int64_t n) {
   GRID_STRIDE(q, n) a[q] = 0.f;
 }

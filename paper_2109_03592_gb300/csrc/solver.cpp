@@ -330,6 +330,9 @@ static sem_status get_graph(sem_mesh* m, Workspace* ws, bool fp32, double h1, do
     return st;
   }
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  size_t nodes = 0;
+  cudaGraphGetNodes(graph, nullptr, &nodes);
+  g.nodes = (int)nodes;
   e = cudaGraphInstantiate(&g.exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
@@ -341,11 +344,12 @@ static sem_status get_graph(sem_mesh* m, Workspace* ws, bool fp32, double h1, do
 }
 
 // Replay the chunk graph until the device reports done.
-static sem_status run_chunks(Workspace* ws, cudaGraphExec_t g, int maxit, PcgState& out) {
+static sem_status run_chunks(Workspace* ws, const GraphSlot& gs, int maxit, PcgState& out) {
+  cudaGraphExec_t g = gs.exec;
   const int max_chunks = maxit / kChunk + 3;
   for (int c = 0; c < max_chunks; ++c) {
     SEM_CUDA(cudaGraphLaunch(g, ws->s));
-    count_launches(3 * kChunk);
+    count_launches(gs.nodes);
     SEM_CUDA(cudaMemcpyAsync(&ws->sth[c & 1], ws->st, sizeof(PcgState), cudaMemcpyDeviceToHost, ws->s));
     SEM_CUDA(cudaEventRecord(ws->ev[c & 1], ws->s));
     if (c > 0) {
@@ -411,7 +415,7 @@ static sem_status pcg64(sem_mesh* m, Workspace* ws, const sem_solve_opts& o, int
       return SEM_OK;
     }
     PcgState fin = s0;
-    st = run_chunks(ws, ws->g64.exec, maxit - res.iters, fin);
+    st = run_chunks(ws, ws->g64, maxit - res.iters, fin);
     if (st != SEM_OK) return st;
     res.iters += fin.iter;
     if (fin.status != SEM_OK) {  // breakdown, or maxit without meeting the tolerance
@@ -465,7 +469,7 @@ static sem_status pcg_mixed(sem_mesh* m, Workspace* ws, const sem_solve_opts& o,
     SEM_CUDA(launch_pcg_init<float>(v, ws->s));
     count_launches(3);
     PcgState fin;
-    st = run_chunks(ws, ws->g32.exec, maxit, fin);
+    st = run_chunks(ws, ws->g32, maxit, fin);
     if (st != SEM_OK) return st;
     res.iters += fin.iter;
     if (fin.status == SEM_ERR_BREAKDOWN) {
@@ -521,7 +525,7 @@ static sem_status pcg_mixed_reliable(sem_mesh* m, Workspace* ws, const sem_solve
   count_launches(4);
   for (;;) {
     PcgState fin;
-    st = run_chunks(ws, ws->g32.exec, maxit, fin);
+    st = run_chunks(ws, ws->g32, maxit, fin);
     if (st != SEM_OK) return st;
     res.iters = fin.iter;
     launch_accumulate(ws->x, ws->x32, bnorm, ws->n, ws->s);

@@ -9,6 +9,7 @@ struct GraphSlot {
   cudaGraphExec_t exec = nullptr;
   double h1 = NAN, h2 = NAN;
   int var = -1, df = -1;
+  int nodes = 0;  // kernel launches per graph launch
 };
 
 struct Workspace {
