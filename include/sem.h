@@ -209,8 +209,10 @@ sem_status sem_pcg_solve_host(const sem_mesh* mesh, const double* b_host, double
  * tiles, per-request alpha, batched QQ^T and update); requests beyond 32
  * join as others finish.  Each request's arithmetic depends only on its own
  * data, so its result equals that of a batch of one.  Synchronous.  A mesh
- * may appear once per call.  Returns SEM_OK, or the first request's failing
- * status (results[k].status has each). */
+ * may appear several times (several right-hand sides on one mesh, e.g. the
+ * three velocity components of a Helmholtz step); each repeat gets its own
+ * work vectors, allocated for the call.  Returns SEM_OK, or the first
+ * request's failing status (results[k].status has each). */
 sem_status sem_pcg_solve_batch(const sem_mesh* const* meshes, const double* const* b_dev, double* const* x_dev,
                                const sem_solve_opts* opts, sem_solve_result* results, int count, void* stream);
 

@@ -462,7 +462,22 @@ class EngineImpl {
       sem_status st = alloc_ws(m, &m->ws);
       if (st != SEM_OK) return st;
     }
-    Workspace* ws = q->ws = m->ws;
+    // the mesh's workspace, or a fresh one when another request of this
+    // batch (another right-hand side on the same mesh) already holds it
+    bool taken = false;
+    for (Req* o : slots_)
+      if (o && o->ws == m->ws) taken = true;
+    if (taken) {
+      Workspace* own = nullptr;
+      sem_status st = alloc_ws(m, &own);
+      if (st != SEM_OK) return st;
+      q->ws = own;
+      q->own_ws = true;
+    } else {
+      q->ws = m->ws;
+      q->own_ws = false;
+    }
+    Workspace* ws = q->ws;
     const size_t bytes = (size_t)ws->n * sizeof(double);
     // a fresh state (zero arrival counters) before the first reduction kernel
     sem_status st0 = put_state(ws, q->o.tol, q->o.maxit, 0);
@@ -575,6 +590,11 @@ class EngineImpl {
     Workspace* ws = q->ws;
     SEM_CUDA(cudaMemcpyAsync(q->x, ws->x, (size_t)ws->n * sizeof(double), cudaMemcpyDeviceToDevice, ws->s));
     SEM_CUDA(cudaStreamSynchronize(ws->s));
+    if (q->own_ws) {
+      free_ws(ws);
+      q->ws = nullptr;
+      q->own_ws = false;
+    }
     q->finished = true;
     q->status = status;
     if (q->out) {
@@ -772,11 +792,6 @@ extern "C" sem_status sem_pcg_solve_batch(const sem_mesh* const* meshes, const d
       set_error("sem_pcg_solve_batch: every request needs a mesh of the same order and b, x");
       return SEM_ERR_INVALID;
     }
-    for (int j = 0; j < k; ++j)
-      if (meshes[j] == m) {
-        set_error("sem_pcg_solve_batch: a mesh may appear once per batch (its workspace is per mesh)");
-        return SEM_ERR_INVALID;
-      }
     sem_solve_opts o = opts[k];
     if (o.prec != SEM_MIXED || o.refine != 0) {
       set_error("sem_pcg_solve_batch: batches run the mixed-precision reliable-update solver (prec = SEM_MIXED)");
@@ -795,8 +810,14 @@ extern "C" sem_status sem_pcg_solve_batch(const sem_mesh* const* meshes, const d
     reqs[k].o = o;
     reqs[k].out = results ? &results[k] : nullptr;
   }
+  // each distinct mesh locked once (a mesh may carry several right-hand
+  // sides), in address order so that concurrent callers cannot deadlock
+  std::vector<sem_mesh*> distinct;
+  for (auto& q : reqs) distinct.push_back(q.m);
+  std::sort(distinct.begin(), distinct.end());
+  distinct.erase(std::unique(distinct.begin(), distinct.end()), distinct.end());
   std::vector<std::unique_lock<std::mutex>> locks;
-  for (auto& q : reqs) locks.emplace_back(q.m->ws_mutex);
+  for (sem_mesh* m : distinct) locks.emplace_back(m->ws_mutex);
   batch::Engine eng(N);
   sem_status st = eng.init((cudaStream_t)stream);
   if (st != SEM_OK) return st;

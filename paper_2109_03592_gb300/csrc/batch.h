@@ -11,6 +11,7 @@ namespace batch {
 struct Req {
   sem_mesh* m = nullptr;
   struct Workspace* ws = nullptr;
+  bool own_ws = false;        // ws was allocated for this request (the mesh's was in use)
   const double* b = nullptr;  // device, FP64
   double* x = nullptr;        // device, FP64 (in: initial guess, out: solution)
   sem_solve_opts o{};         // prec SEM_MIXED, refine 0, defaults filled in

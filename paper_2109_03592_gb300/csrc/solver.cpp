@@ -47,6 +47,8 @@ static void destroy_ws(Workspace* ws) {
   delete ws;
 }
 
+void free_ws(Workspace* ws) { destroy_ws(ws); }
+
 void release_workspace(sem_mesh* m) {
   std::lock_guard<std::mutex> lk(m->ws_mutex);
   destroy_ws(m->ws);

@@ -27,6 +27,7 @@ struct Workspace {
 };
 
 sem_status alloc_ws(sem_mesh* m, Workspace** out);
+void free_ws(Workspace* ws);  // a workspace from alloc_ws that is not a mesh's
 // FP64 local operator with the mesh's tuned kernel (native or double-float).
 // w = A_L u with the native FP64 kernel (exact FP64 arithmetic)
 cudaError_t ax64_exact(const sem_mesh* m, const double* u, double* w, double h1, double h2, cudaStream_t s);

@@ -86,6 +86,31 @@ def test_batch_more_requests_than_slots(problems):
         assert res[k]["status"] == 0 and np.sqrt(P.dot(r, r) / P.dot(bn, bn)) <= 1e-10
 
 
+def test_three_right_hand_sides_on_one_mesh():
+    """The three velocity components of a Helmholtz step (h2 = b0/dt) on one
+    mesh in one batch: each equals its batch of one and meets the residual."""
+    import torch
+    import paper_2109_03592_gb300 as sem
+    d = dict(kind="pipe", nc=4, nr=2, nzp=3, N=7, L=2.0)
+    m = sem.Mesh(d)
+    P = solver.Problem(_om(d), 0.05, 30.0)  # h1 = 1/Re, h2 = b0/dt
+    bs = [torch.from_numpy(P.rhs(forcing.evaluate(P.mesh.xyz, forcing.random_modes(400 + c, L=2.0)))).cuda()
+          for c in range(3)]
+    opts = [dict(tol=1e-10, h1=0.05, h2=30.0)] * 3
+    xs = [torch.zeros_like(b) for b in bs]
+    st, res = sem.solve_batch([m, m, m], bs, xs, opts)
+    assert st == sem.SEM_OK, res
+    for c in range(3):
+        x1 = torch.zeros_like(bs[c])
+        st1, r1 = sem.solve_batch([m], [bs[c]], [x1], [opts[c]])
+        assert st1 == sem.SEM_OK
+        assert torch.equal(xs[c], x1) and res[c]["iters"] == r1[0]["iters"]
+        bn = bs[c].cpu().numpy()
+        r = bn - P.A(xs[c].cpu().numpy())
+        assert np.sqrt(P.dot(r, r) / P.dot(bn, bn)) <= 1e-10
+    m.close()
+
+
 def test_batch_rejects_mixed_orders_and_even_N(problems):
     import torch
     import paper_2109_03592_gb300 as sem
