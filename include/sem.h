@@ -335,6 +335,23 @@ sem_status sem_server_destroy(sem_server* srv);
 sem_status sem_topology_numbering(int64_t E, int N, const int64_t* vert, int64_t* glo_host,
                                   int64_t* n_global);
 
+/* One rank's gather-scatter halo under an element partition (Sec. 3.1
+ * partitions elements across ranks, one per GPU; Sec. 2 sums shared face
+ * values across them).  This library runs one GPU per process, so it uses no
+ * halo itself; the split is defined here for a multi-rank QQ^T.  elem_rank
+ * [E] gives each element's rank (>= 0); a rank's local vector holds its
+ * elements in ascending element order, (N+1)^3 points each.  For every global
+ * node with copies on `rank` and on another rank, in ascending global id:
+ * node_gid[k], and its copies node_ptr[k] .. node_ptr[k+1]-1 as (copy_rank,
+ * copy_local = index in that rank's local vector) in ascending global local
+ * index.  Summing each node's copies in that order gives QQ^T bit for bit as
+ * on one rank; nodes with all copies on `rank` need no exchange.  Call with
+ * node_gid = NULL for *n_nodes and *n_copies, then with arrays of those
+ * sizes (node_ptr: n_nodes + 1).  Host memory only; no GPU needed. */
+sem_status sem_gs_halo(int64_t E, int N, const int64_t* vert, const int32_t* elem_rank, int rank,
+                       int64_t* n_nodes, int64_t* n_copies, int64_t* node_gid, int64_t* node_ptr,
+                       int32_t* copy_rank, int64_t* copy_local);
+
 /* Corner vertex ids [E][8] of the built-in box / pipe generators. */
 sem_status sem_mesh_vertices(const sem_mesh_desc* desc, int64_t* vert_host, int64_t* E_out);
 

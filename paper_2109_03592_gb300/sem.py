@@ -100,6 +100,8 @@ SIGNATURES = {
     "sem_server_stats_get": (C.c_int, [_P, C.POINTER(ServerStats)]),
     "sem_server_destroy": (C.c_int, [_P]),
     "sem_topology_numbering": (C.c_int, [C.c_int64, C.c_int, _P, _P, C.POINTER(C.c_int64)]),
+    "sem_gs_halo": (C.c_int, [C.c_int64, C.c_int, _P, _P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                              _P, _P, _P, _P]),
     "sem_mesh_vertices": (C.c_int, [C.POINTER(MeshDesc), _P, C.POINTER(C.c_int64)]),
     "sem_status_str": (C.c_char_p, [C.c_int]),
     "sem_last_error": (C.c_char_p, []),
@@ -364,6 +366,23 @@ def topology_numbering(E, N, vert):
     _check(lib().sem_topology_numbering(int(E), int(N), vert.ctypes.data, out.ctypes.data, C.byref(ng)),
            "sem_topology_numbering")
     return out, ng.value
+
+
+def gs_halo(E, N, vert, elem_rank, rank):
+    """Host-only (sem_gs_halo): the halo of `rank` under the element partition
+    elem_rank [E].  Returns (node_gid, node_ptr, copy_rank, copy_local)."""
+    vert = np.ascontiguousarray(vert, dtype=np.int64)
+    er = np.ascontiguousarray(elem_rank, dtype=np.int32)
+    nn, nc = C.c_int64(), C.c_int64()
+    _check(lib().sem_gs_halo(int(E), int(N), vert.ctypes.data, er.ctypes.data, int(rank), C.byref(nn), C.byref(nc),
+                             None, None, None, None), "sem_gs_halo")
+    gid = np.empty(nn.value, dtype=np.int64)
+    ptr = np.empty(nn.value + 1, dtype=np.int64)
+    crank = np.empty(nc.value, dtype=np.int32)
+    cloc = np.empty(nc.value, dtype=np.int64)
+    _check(lib().sem_gs_halo(int(E), int(N), vert.ctypes.data, er.ctypes.data, int(rank), C.byref(nn), C.byref(nc),
+                             gid.ctypes.data, ptr.ctypes.data, crank.ctypes.data, cloc.ctypes.data), "sem_gs_halo")
+    return gid, ptr, crank, cloc
 
 
 def mesh_vertices(desc):
