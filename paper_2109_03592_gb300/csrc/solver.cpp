@@ -99,7 +99,7 @@ cudaError_t ax64(const sem_mesh* m, const double* u, double* w, double h1, doubl
                  h2 != 0.0, m->E, z, p, st, part, m->eo64, m->eodf};
     return launch_ax_df(m->N, m->ax_var[2], fused, a, s, nullptr);
   }
-  AxParams<double> a{u, w, m->G64, m->B64, m->D64, h1, h2, h2 != 0.0, m->E, z, p, st, part};
+  AxParams<double> a{u, w, m->G64, m->B64, m->D64, h1, h2, h2 != 0.0, m->E, z, p, st, part, m->dev_err};
   return launch_ax_f64(m->N, m->ax_var[0], fused, a, s, nullptr);
 }
 
@@ -110,7 +110,8 @@ cudaError_t ax64(const sem_mesh* m, const double* u, double* w, double h1, doubl
 // than FP64's, would set the attainable residual (measured: the E = 262,144
 // pipe stalled above 1e-10 with a 2^-46 input split).
 cudaError_t ax64_exact(const sem_mesh* m, const double* u, double* w, double h1, double h2, cudaStream_t s) {
-  AxParams<double> a{u, w, m->G64, m->B64, m->D64, h1, h2, h2 != 0.0, m->E, nullptr, nullptr, nullptr, nullptr};
+  AxParams<double> a{u, w, m->G64, m->B64, m->D64, h1, h2, h2 != 0.0, m->E, nullptr, nullptr, nullptr, nullptr,
+                     m->dev_err};
   return launch_ax_f64(m->N, m->ax_var[0], false, a, s, nullptr);
 }
 
@@ -180,7 +181,8 @@ static sem_status autotune_measure(sem_mesh* m, cudaStream_t s) {
       for (int rep = 0; rep <= reps && err == cudaSuccess; ++rep) {
         cudaEventRecord(a, s);
         if (kind == 0) {
-          AxParams<double> pa{m->B64, w, m->G64, m->B64, m->D64, 1.0, 0.0, 0, m->E, nullptr, nullptr, nullptr, nullptr};
+          AxParams<double> pa{m->B64, w, m->G64, m->B64, m->D64, 1.0, 0.0, 0, m->E, nullptr, nullptr, nullptr, nullptr,
+                              m->dev_err};
           err = launch_ax_f64(m->N, v, false, pa, s, nullptr);
         } else if (kind == 1) {
           AxParams<float> pa{m->B32, (float*)w, m->G32, m->B32, m->D32, 1.f, 0.f, 0, m->E,
