@@ -176,7 +176,8 @@ typedef struct {
                        replacements; Sleijpen & van der Vorst 1996), 1 = restarted refinement
                        (defect correction: a fresh FP32 PCG on each FP64 residual) */
   double delta;     /* SEM_MIXED, refine = 0: replace the residual when the FP32 one has dropped by
-                       this factor since the last replacement; <= 0 means 0.1 */
+                       this factor since the last replacement; <= 0 means 0.3 (sem_pcg_solve) or
+                       0.1 (batched and served solves, where a replacement costs a host round trip) */
 } sem_solve_opts;
 
 typedef struct {

@@ -191,7 +191,7 @@ def pcg_mixed(prob, b, tol=1e-10, inner_tol=1e-5, max_outer=50, maxit=20000):
     return Result(x, total, rnorm / bnorm, st, hist, outer)
 
 
-def pcg_mixed_reliable(prob, b, tol=1e-10, delta=0.1, maxit=20000, gamma=0.2):
+def pcg_mixed_reliable(prob, b, tol=1e-10, delta=0.3, maxit=20000, gamma=0.2):
     """Mixed-precision PCG with reliable updates.
 
     The CG recurrences run in FP32 on the scaled system (b / ||b||): x32 holds

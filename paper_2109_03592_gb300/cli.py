@@ -2,9 +2,10 @@
 
     python -m paper_2109_03592_gb300.cli solve --workload pipe32768_n7 --prec fp64 [--repeat 2]
     python -m paper_2109_03592_gb300.cli ax --workload pipe262144_n7 --prec fp64 [--reps 10]
+    python -m paper_2109_03592_gb300.cli gs --workload pipe262144_n7 --prec fp32 [--reps 10]
 
-Prints one JSON line per solve (the sem_pcg_solve result) or per operator
-timing (CUDA events on the launching stream).
+Prints one JSON line per solve (the sem_pcg_solve result) or per operator /
+gather-scatter timing (CUDA events on the launching stream).
 """
 
 import argparse
@@ -29,7 +30,7 @@ def _mesh_and_rhs(workload):
 def main(argv=None):
     from . import sem
     ap = argparse.ArgumentParser(prog="python -m paper_2109_03592_gb300.cli")
-    ap.add_argument("what", choices=["solve", "ax"])
+    ap.add_argument("what", choices=["solve", "ax", "gs"])
     ap.add_argument("--workload", default="pipe32768_n7")
     ap.add_argument("--prec", default="mixed", choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--tol", type=float, default=1e-10)
@@ -45,6 +46,23 @@ def main(argv=None):
             x.zero_()
             r = m.solve(b, x, tol=args.tol, prec=prec)
             print(json.dumps({"workload": args.workload, "prec": args.prec, **r}), flush=True)
+    elif args.what == "gs":
+        dt = torch.float32 if prec == sem.FP32 else torch.float64
+        p = sem.FP32 if prec == sem.FP32 else sem.FP64
+        v = torch.randn(m.shape, dtype=dt, device="cuda")
+        for _ in range(3):
+            m.gs(v, apply_mask=True, prec=p)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(args.reps):
+            m.gs(v, apply_mask=True, prec=p)
+        e.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e) / args.reps
+        esz = 4 if p == sem.FP32 else 8
+        print(json.dumps({"workload": args.workload, "prec": args.prec, "ms": ms, "shared_points": m.n_seg_points,
+                          "alg_gbs": m.n_seg_points * (4 + 2 * esz) / ms / 1e6}), flush=True)
     else:
         dt = torch.float32 if prec == sem.FP32 else torch.float64
         u = torch.randn(m.shape, dtype=dt, device="cuda")

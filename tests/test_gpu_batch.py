@@ -61,7 +61,7 @@ def test_batch_equals_batch_of_one_and_meets_residual(problems):
         bn = b.cpu().numpy()
         r = bn - P.A(xs[i].cpu().numpy())
         assert np.sqrt(P.dot(r, r) / P.dot(bn, bn)) <= 1e-10
-        ref = solver.pcg_mixed_reliable(P, bn, tol=1e-10)
+        ref = solver.pcg_mixed_reliable(P, bn, tol=1e-10, delta=0.1)  # the batched solves' default
         assert abs(res[i]["iters"] - ref.iters) <= 0.1 * ref.iters + 3, (i, res[i], ref.iters)
 
 

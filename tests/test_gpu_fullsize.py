@@ -127,13 +127,14 @@ def test_gs_properties_full_size(big):
         assert np.all(after[copies] == expect)
 
 
-def test_mixed_solve_sampled_residual(big):
+@pytest.mark.parametrize("prec_name", ["MIXED", "FP64"])
+def test_solve_sampled_residual(big, prec_name):
+    """The bench's solve (mixed precision, reliable updates) and the plain
+    FP64 PCG, tol 1e-10: the residual at element-interior points of sampled
+    elements, recomputed by the oracle from x, is bounded by
+    ||r|| <= 1e-10 ||b|| (an interior point has one copy, so |r_l| <= ||r||)."""
     if big[1] != configs.mesh_desc(BENCH):
         pytest.skip("the solve is checked on the benchmark configuration")
-    """The bench's solve (mixed precision, reliable updates, tol 1e-10): the
-    residual at element-interior points of sampled elements, recomputed by the
-    oracle from x, is bounded by ||r|| <= 1e-10 ||b|| (an interior point has
-    one copy, so |r_l| <= ||r||)."""
     import torch
     import paper_2109_03592_gb300 as sem
     m, desc, els, om, G, B, D = big
@@ -147,7 +148,7 @@ def test_mixed_solve_sampled_residual(big):
     bnorm = float(torch.sqrt((b * b / mult).sum()))
     del mult, mask
     x = torch.zeros_like(b)
-    res = m.solve(b, x, tol=1e-10, prec=sem.MIXED)
+    res = m.solve(b, x, tol=1e-10, prec=getattr(sem, prec_name))
     assert res["status"] == 0 and res["rel_res"] <= 1e-10
     xs = _rows(x, els)
     fs = forcing.evaluate(om.xyz, modes)
