@@ -30,12 +30,19 @@ from .operator import ax_local, local_diagonal
 CONVERGED, NOT_CONVERGED, BREAKDOWN = 0, 4, 5
 
 
+def _coefficient(h):
+    """A scalar, or one value per local point [E, n, n, n] (Alg. 1 reads
+    h1(i,j,k,e); h2 per point likewise)."""
+    return float(h) if np.ndim(h) == 0 else np.asarray(h, dtype=np.float64)
+
+
 class Problem:
-    """Everything the solver needs for one mesh and one (h1, h2)."""
+    """Everything the solver needs for one mesh and one (h1, h2), each a
+    scalar or an array of per-local-point values."""
 
     def __init__(self, mesh, h1=1.0, h2=0.0):
         self.mesh = mesh
-        self.h1, self.h2 = float(h1), float(h2)
+        self.h1, self.h2 = _coefficient(h1), _coefficient(h2)
         self.D = gll.derivative_matrix(mesh.N)
         self.G, self.B, self.detJ = geometry.factors(mesh)
         self.glo, self.Pg = numbering.global_numbering(mesh)
@@ -127,7 +134,8 @@ class Problem32:
         self.D = prob.D.astype(np.float32)
         self.mask = prob.mask.astype(np.float32)
         self.Minv = prob.jacobi_inverse().astype(np.float32)
-        self.h1, self.h2 = np.float32(prob.h1), np.float32(prob.h2)
+        self.h1 = np.asarray(prob.h1, dtype=np.float32)
+        self.h2 = np.asarray(prob.h2, dtype=np.float32)
 
     def A(self, x):
         w = ax_local(x, self.G, self.B, self.D, self.h1, self.h2).astype(np.float32)
