@@ -142,8 +142,30 @@ sem_status sem_mesh_coords(const sem_mesh* mesh, double* xyz_dev, void* stream);
 sem_status sem_mesh_geometry(const sem_mesh* mesh, double* G_dev, double* B_dev, void* stream);
 sem_status sem_mesh_weights(const sem_mesh* mesh, double* mult_dev, double* mask_dev, void* stream);
 
-/* w = A_L u: Alg. 1 plus the Helmholtz term, element by element, with scalar
- * h1 (scaling the stiffness after the G contraction) and h2 (scaling B u).
+/* Per-point operator coefficients.  Alg. 1 scales the contracted gradient
+ * G (ur, us, ut) at every local point by that point's h1(i,j,k,e); the
+ * Helmholtz term of Sec. 2, Eq. 4 is read the same way with a per-point h2
+ * (variable viscosity and mass coefficient).
+ *   h1_dev, h2_dev: device FP64 arrays of n_local values in the local layout
+ *   [E][n^3], read during the call and not kept; NULL means 1 at every point.
+ * From then on every operator entry point on this mesh (sem_ax, sem_apply,
+ * sem_jacobi, the solvers, batches, projection spaces) applies
+ *   h1_eff(q) = h1 * h1_dev[q],  h2_eff(q) = h2 * h2_dev[q]
+ * with the scalar h1, h2 that the call passes.  Both NULL restores the
+ * constant-coefficient operator.  The factors are stored pre-multiplied
+ * (h1 G, h2 B in FP64, FP32 and the FP32 pair form: 128 B per local point
+ * with both), so the operator kernels read no more bytes than without.
+ * sem_mesh_geometry and sem_rhs keep using the plain G and B.
+ * A projection space on the mesh drops its basis at its next solve.
+ * Errors: SEM_ERR_INVALID (null mesh; an h1 value <= 0 or an h2 value < 0 or
+ * non-finite: the mesh keeps its previous coefficients), SEM_ERR_OOM.
+ * Runs on `stream` and returns after the device finished; not to be called
+ * while a solve, batch or server request on this mesh is in flight. */
+sem_status sem_mesh_set_coefficients(sem_mesh* mesh, const double* h1_dev, const double* h2_dev, void* stream);
+
+/* w = A_L u: Alg. 1 plus the Helmholtz term, element by element, with
+ * h1 (scaling the stiffness after the G contraction) and h2 (scaling B u):
+ * scalars, times the mesh's per-point coefficients if it has any.
  * No assembly and no mask.  u and w: local vectors of `prec` SEM_FP64 or
  * SEM_FP32 (SEM_FP32 uses the FP32 factors).  u and w must not overlap. */
 sem_status sem_ax(const sem_mesh* mesh, const void* u_dev, void* w_dev, double h1, double h2,
@@ -167,7 +189,7 @@ sem_status sem_jacobi(const sem_mesh* mesh, double h1, double h2, double* minv_d
 
 typedef struct {
   double tol;       /* stop when ||r|| <= tol ||b||, ||v||^2 = sum_l v_l^2 / mult_l; default 1e-10 */
-  double h1, h2;    /* operator coefficients (Poisson: 1, 0) */
+  double h1, h2;    /* operator coefficients (Poisson: 1, 0), times the mesh's per-point ones */
   double inner_tol; /* SEM_MIXED: relative tolerance of each FP32 inner solve; <= 0 picks the tuned value */
   int maxit;        /* iteration cap (per inner solve for SEM_MIXED); <= 0 means 20000 */
   int max_outer;    /* SEM_MIXED: refinement steps cap; <= 0 means 50 */

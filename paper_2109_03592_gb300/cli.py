@@ -3,6 +3,11 @@
     python -m paper_2109_03592_gb300.cli solve --workload pipe32768_n7 --prec fp64 [--repeat 2]
     python -m paper_2109_03592_gb300.cli ax --workload pipe262144_n7 --prec fp64 [--reps 10]
     python -m paper_2109_03592_gb300.cli gs --workload pipe262144_n7 --prec fp32 [--reps 10]
+    python -m paper_2109_03592_gb300.cli ax --workload pipe262144_n7 --prec fp32 --coef
+
+--coef gives the mesh seeded per-point coefficients h1(i,j,k,e), h2(i,j,k,e)
+(a variable viscosity and mass coefficient) before the timed calls, which then
+use h1 = h2 = 1.
 
 Prints one JSON line per solve (the sem_pcg_solve result) or per operator /
 gather-scatter timing (CUDA events on the launching stream).
@@ -27,6 +32,15 @@ def _mesh_and_rhs(workload):
     return m, b
 
 
+def _set_coefficients(m):
+    import torch
+    from sem_inputs import coefficients
+    xyz = m.coords().cpu().numpy()
+    h1 = torch.from_numpy(coefficients.viscosity(21, xyz)).cuda()
+    h2 = torch.from_numpy(coefficients.mass_coefficient(22, xyz)).cuda()
+    m.set_coefficients(h1, h2)
+
+
 def main(argv=None):
     from . import sem
     ap = argparse.ArgumentParser(prog="python -m paper_2109_03592_gb300.cli")
@@ -36,16 +50,22 @@ def main(argv=None):
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--coef", action="store_true", help="per-point h1, h2 on the mesh (h1 = h2 = 1 in the calls)")
+    ap.add_argument("--helmholtz", action="store_true", help="h2 = 1 (the mass term) with scalar coefficients")
     args = ap.parse_args(argv)
     import torch
     prec = {"fp64": sem.FP64, "fp32": sem.FP32, "mixed": sem.MIXED}[args.prec]
     m, b = _mesh_and_rhs(args.workload)
+    h1, h2 = 1.0, 1.0 if args.helmholtz else 0.0
+    if args.coef:
+        _set_coefficients(m)
+        h2 = 1.0
     if args.what == "solve":
         x = torch.zeros_like(b)
         for _ in range(args.repeat):
             x.zero_()
-            r = m.solve(b, x, tol=args.tol, prec=prec)
-            print(json.dumps({"workload": args.workload, "prec": args.prec, **r}), flush=True)
+            r = m.solve(b, x, tol=args.tol, prec=prec, h1=h1, h2=h2)
+            print(json.dumps({"workload": args.workload, "prec": args.prec, "coef": args.coef, **r}), flush=True)
     elif args.what == "gs":
         dt = torch.float32 if prec == sem.FP32 else torch.float64
         p = sem.FP32 if prec == sem.FP32 else sem.FP64
@@ -69,16 +89,16 @@ def main(argv=None):
         w = torch.empty_like(u)
         p = sem.FP32 if prec == sem.FP32 else sem.FP64
         for _ in range(3):
-            m.ax(u, w, prec=p)
+            m.ax(u, w, h1, h2, prec=p)
         a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record()
         for _ in range(args.reps):
-            m.ax(u, w, prec=p)
+            m.ax(u, w, h1, h2, prec=p)
         e.record()
         torch.cuda.synchronize()
         ms = a.elapsed_time(e) / args.reps
-        print(json.dumps({"workload": args.workload, "prec": args.prec, "ms": ms,
+        print(json.dumps({"workload": args.workload, "prec": args.prec, "coef": args.coef, "h2": h2, "ms": ms,
                           "gdofs": m.E * m.N ** 3 / ms / 1e6, "variant": m.ax_variant(p)}), flush=True)
     m.close()
     return 0

@@ -66,6 +66,14 @@ void free_mesh_arrays(sem_mesh* m) {
   dev_free(m->D32lo);
   dev_free(m->eo64);
   dev_free(m->eodf);
+  dev_free(m->cG64);
+  dev_free(m->cG32);
+  dev_free(m->cG32lo);
+  dev_free(m->cdK);
+  dev_free(m->cB64);
+  dev_free(m->cB32);
+  dev_free(m->cB32lo);
+  dev_free(m->cdB);
 }
 
 #define SEM_TRY(expr)                   \
@@ -73,6 +81,80 @@ void free_mesh_arrays(sem_mesh* m) {
     sem_status _s = (expr);             \
     if (_s != SEM_OK) return _s;        \
   } while (0)
+
+// The operator arrays for per-point coefficients, built aside and installed
+// only once the coefficients were found valid.
+struct CoefArrays {
+  double* G64 = nullptr;
+  float* G32 = nullptr;
+  float* G32lo = nullptr;
+  double* dK = nullptr;
+  double* B64 = nullptr;
+  float* B32 = nullptr;
+  float* B32lo = nullptr;
+  double* dB = nullptr;
+  size_t bytes = 0;
+  void release() {
+    dev_free(G64);
+    dev_free(G32);
+    dev_free(G32lo);
+    dev_free(dK);
+    dev_free(B64);
+    dev_free(B32);
+    dev_free(B32lo);
+    dev_free(dB);
+    bytes = 0;
+  }
+};
+
+size_t coef_bytes(const sem_mesh* m) {
+  const size_t P = (size_t)m->n_local;
+  return (m->cG64 ? P * (6 * 8 + 6 * 4 + 6 * 4 + 8) : 0) + (m->cB64 ? P * (8 + 4 + 4 + 8) : 0);
+}
+
+sem_status build_coef(const sem_mesh* m, const double* h1, const double* h2, CoefArrays& c, cudaStream_t s) {
+  const int64_t P = m->n_local;
+  const int n = m->n;
+  if (h1) {
+    SEM_TRY(dev_alloc(&c.G64, 6 * P, c.bytes));
+    SEM_TRY(dev_alloc(&c.G32, 6 * P, c.bytes));
+    SEM_TRY(dev_alloc(&c.G32lo, 6 * P, c.bytes));
+    SEM_TRY(dev_alloc(&c.dK, P, c.bytes));
+  }
+  if (h2) {
+    SEM_TRY(dev_alloc(&c.B64, P, c.bytes));
+    SEM_TRY(dev_alloc(&c.B32, P, c.bytes));
+    SEM_TRY(dev_alloc(&c.B32lo, P, c.bytes));
+    SEM_TRY(dev_alloc(&c.dB, P, c.bytes));
+  }
+  size_t tmp = 0;
+  int* bad_d = nullptr;
+  SEM_TRY(dev_alloc(&bad_d, 1, tmp));
+  std::unique_ptr<int, void (*)(int*)> bad_guard(bad_d, [](int* p) { cudaFree(p); });
+  SEM_CUDA(cudaMemsetAsync(bad_d, 0, sizeof(int), s));
+  launch_fold_coef(m->G64, m->B64, h1, h2, c.G64, c.B64, n, P, bad_d, s);
+  if (h1) {
+    launch_local_diag(c.G64, c.dK, m->D64, n, m->E, s);
+    SEM_CUDA(launch_gs<double>(c.dK, gs_dev(m), 0, nullptr, s));
+    launch_split_f64(c.G64, c.G32, c.G32lo, 6 * P, s);
+  }
+  if (h2) {
+    SEM_CUDA(cudaMemcpyAsync(c.dB, c.B64, P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    SEM_CUDA(launch_gs<double>(c.dB, gs_dev(m), 0, nullptr, s));
+    launch_split_f64(c.B64, c.B32, c.B32lo, P, s);
+  }
+  SEM_CUDA(cudaGetLastError());
+  count_launches(1 + (h1 ? 3 : 0) + (h2 ? 2 : 0));
+  int bad = 0;
+  SEM_CUDA(cudaMemcpyAsync(&bad, bad_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA(cudaStreamSynchronize(s));
+  if (bad) {
+    set_error((bad & 1) ? "sem_mesh_set_coefficients: need finite h1 > 0 at every point"
+                        : "sem_mesh_set_coefficients: need finite h2 >= 0 at every point");
+    return SEM_ERR_INVALID;
+  }
+  return SEM_OK;
+}
 
 sem_status build_mesh(const sem_mesh_desc& d, cudaStream_t s, sem_mesh* m) {
   std::vector<int64_t> vert;
@@ -309,10 +391,56 @@ sem_status sem_mesh_create(const sem_mesh_desc* desc, void* stream, sem_mesh** o
 
 sem_status sem_mesh_destroy(sem_mesh* m) {
   if (!m) return SEM_OK;
-  cudaDeviceSynchronize();
+  // No device-wide synchronisation here: another thread may be capturing a
+  // CUDA graph (the solvers and the batch engine do), and synchronising the
+  // device while any stream captures is invalid.  The workspace's stream is
+  // synchronised by release_workspace, and cudaFree waits for the work that
+  // still uses the memory it frees.
+  cudaSetDevice(m->device);
   release_workspace(m);
   free_mesh_arrays(m);
   delete m;
+  return SEM_OK;
+}
+
+sem_status sem_mesh_set_coefficients(sem_mesh* m, const double* h1_dev, const double* h2_dev, void* stream) {
+  if (!m) {
+    set_error("sem_mesh_set_coefficients: null mesh");
+    return SEM_ERR_INVALID;
+  }
+  SEM_CUDA(cudaSetDevice(m->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(m->ws_mutex);
+  CoefArrays c;
+  sem_status st = build_coef(m, h1_dev, h2_dev, c, s);
+  if (st != SEM_OK) {
+    cudaStreamSynchronize(s);
+    c.release();
+    return st;
+  }
+  // the old arrays are freed below: cudaFree waits for kernels still reading
+  // them (no device-wide synchronisation, see sem_mesh_destroy)
+  if (m->ws) SEM_CUDA(cudaStreamSynchronize(m->ws->s));
+  m->dev_bytes -= coef_bytes(m);
+  dev_free(m->cG64);
+  dev_free(m->cG32);
+  dev_free(m->cG32lo);
+  dev_free(m->cdK);
+  dev_free(m->cB64);
+  dev_free(m->cB32);
+  dev_free(m->cB32lo);
+  dev_free(m->cdB);
+  m->cG64 = c.G64;
+  m->cG32 = c.G32;
+  m->cG32lo = c.G32lo;
+  m->cdK = c.dK;
+  m->cB64 = c.B64;
+  m->cB32 = c.B32;
+  m->cB32lo = c.B32lo;
+  m->cdB = c.dB;
+  m->dev_bytes += coef_bytes(m);
+  m->coef_gen++;
+  if (m->ws) m->ws->minv_h1 = NAN;  // the cached Jacobi inverse belongs to the old operator
   return SEM_OK;
 }
 
@@ -437,7 +565,7 @@ sem_status sem_jacobi(const sem_mesh* m, double h1, double h2, double* minv_dev,
     set_error("sem_jacobi: null argument");
     return SEM_ERR_INVALID;
   }
-  launch_minv(minv_dev, nullptr, m->dK, m->dB, m->wm, h1, h2, m->n_local, (cudaStream_t)stream);
+  launch_minv(minv_dev, nullptr, m->opdK(), m->opdB(), m->wm, h1, h2, m->n_local, (cudaStream_t)stream);
   SEM_CUDA(cudaGetLastError());
   count_launches(1);
   return SEM_OK;

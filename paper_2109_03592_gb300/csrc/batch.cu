@@ -443,7 +443,8 @@ class EngineImpl {
     PcgState d;
     std::memset(&d, 0, sizeof(d));
     d.done = 1;
-    SEM_CUDA(cudaMemcpy(done_state_, &d, sizeof(d), cudaMemcpyHostToDevice));
+    SEM_CUDA(cudaMemcpyAsync(done_state_, &d, sizeof(d), cudaMemcpyHostToDevice, s_));
+    SEM_CUDA(cudaStreamSynchronize(s_));  // d is on this thread's stack
     std::memset(h_tab_, 0, sizeof(Table));
     return SEM_OK;
   }
@@ -488,7 +489,7 @@ class EngineImpl {
     SEM_CUDA(cudaMemcpyAsync(ws->b, q->b, bytes, cudaMemcpyDeviceToDevice, ws->s));
     SEM_CUDA(cudaMemcpyAsync(ws->x, q->x, bytes, cudaMemcpyDeviceToDevice, ws->s));
     launch_mask(ws->x, m->wm, ws->n, ws->s);
-    launch_minv(ws->minv, ws->minv32, m->dK, m->dB, m->wm, q->o.h1, q->o.h2, ws->n, ws->s);
+    launch_minv(ws->minv, ws->minv32, m->opdK(), m->opdB(), m->wm, q->o.h1, q->o.h2, ws->n, ws->s);
     ws->minv_h1 = q->o.h1;
     ws->minv_h2 = q->o.h2;
     SEM_CUDA(ax64_exact(m, ws->x, ws->w, q->o.h1, q->o.h2, ws->s));
@@ -543,7 +544,8 @@ class EngineImpl {
         SEM_CUDA(cudaMemcpyAsync(&h_st_[r], slots_[r]->ws->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s_));
     SEM_CUDA(cudaStreamSynchronize(s_));
     int err = 0;
-    SEM_CUDA(cudaMemcpy(&err, d_err_, sizeof(int), cudaMemcpyDeviceToHost));
+    SEM_CUDA(cudaMemcpyAsync(&err, d_err_, sizeof(int), cudaMemcpyDeviceToHost, s_));
+    SEM_CUDA(cudaStreamSynchronize(s_));
     for (int r = 0; r < kMaxSlots; ++r) {
       Req* q = slots_[r];
       if (!q || !h_st_[r].done) continue;
@@ -632,8 +634,8 @@ class EngineImpl {
       if (q) {
         sem_mesh* m = q->m;
         Workspace* ws = q->ws;
-        sl.G = m->G32;
-        sl.B = m->B32;
+        sl.G = m->opG32();
+        sl.B = m->opB32();
         sl.D = m->D32;
         if (!T.D) T.D = m->D32;
         sl.wm = m->wm;

@@ -159,6 +159,29 @@ __global__ void k_split_f64(const double* __restrict__ v, float* __restrict__ hi
   }
 }
 
+// Per-point coefficients folded into the stored factors: cG = h1[q] G (all six
+// factors of the point) and cB = h2[q] B.  Alg. 1 scales (G . grad u) at each
+// point by h1 of that point, which is h1 G at the point; the mass term scales
+// B u by h2.  Bit 0 / 1 of *bad flags an h1 <= 0 / h2 < 0 or a non-finite
+// value.
+__global__ void k_fold_coef(const double* __restrict__ G, const double* __restrict__ B, const double* __restrict__ h1,
+                            const double* __restrict__ h2, double* __restrict__ cG, double* __restrict__ cB, int n3,
+                            int64_t P, int* bad) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = q / n3, r = q - e * n3;
+    if (h1) {
+      const double c = h1[q];
+      if (!(c > 0.0) || !isfinite(c)) atomicOr(bad, 1);
+      for (int k = 0; k < 6; ++k) cG[(e * 6 + k) * n3 + r] = c * G[(e * 6 + k) * n3 + r];
+    }
+    if (h2) {
+      const double c = h2[q];
+      if (!(c >= 0.0) || !isfinite(c)) atomicOr(bad, 2);
+      cB[q] = c * B[q];
+    }
+  }
+}
+
 __global__ void k_weights(const uint8_t* __restrict__ wm, double* mult, double* mask, int64_t m) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m; q += (int64_t)gridDim.x * blockDim.x) {
     const uint8_t b = wm[q];
@@ -202,6 +225,11 @@ void launch_local_diag(const double* G, double* dK, const double* D, int n, int6
 
 void launch_split_f64(const double* v, float* hi, float* lo, int64_t m, cudaStream_t s) {
   k_split_f64<<<grid_for(m, 256), 256, 0, s>>>(v, hi, lo, m);
+}
+
+void launch_fold_coef(const double* G, const double* B, const double* h1, const double* h2, double* cG, double* cB,
+                      int n, int64_t P, int* bad, cudaStream_t s) {
+  k_fold_coef<<<grid_for(P, 256), 256, 0, s>>>(G, B, h1, h2, cG, cB, n * n * n, P, bad);
 }
 
 void launch_weights(const uint8_t* wm, double* mult, double* mask, int64_t m, cudaStream_t s) {

@@ -20,6 +20,8 @@ void launch_coords_pipe(double* xyz, const double* xi, const double* tlev, int n
 cudaError_t launch_geometry(const double* xyz, double* G, double* B, const double* D, const double* w, int n,
                             int64_t E, int* bad, cudaStream_t s);
 void launch_local_diag(const double* G, double* dK, const double* D, int n, int64_t E, cudaStream_t s);
+void launch_fold_coef(const double* G, const double* B, const double* h1, const double* h2, double* cG, double* cB,
+                      int n, int64_t P, int* bad, cudaStream_t s);
 void launch_split_f64(const double* v, float* hi, float* lo, int64_t m, cudaStream_t s);
 void launch_weights(const uint8_t* wm, double* mult, double* mask, int64_t m, cudaStream_t s);
 

@@ -114,7 +114,7 @@ extern "C" sem_status sem_pcg_solve_noalloc(const sem_mesh* m, const double* b_d
   h.maxit = maxit;
   SEM_CUDA(cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, s));
   launch_mask(x_dev, m->wm, n, s);
-  launch_minv(minv, nullptr, m->dK, m->dB, m->wm, h1, h2, n, s);
+  launch_minv(minv, nullptr, m->opdK(), m->opdB(), m->wm, h1, h2, n, s);
   count_launches(2);
   // r = b - A x0
   st = apply_local(m, x_dev, w, h1, h2, SEM_FP64, s);
@@ -127,11 +127,11 @@ extern "C" sem_status sem_pcg_solve_noalloc(const sem_mesh* m, const double* b_d
 
   auto fp64_ax = [&]() -> cudaError_t {
     if (m->fp64_df) {
-      AxDFParams a{nullptr, w, m->G32, m->G32lo, m->B32, m->B32lo, m->D32, m->D32lo, h1, h2, h2 != 0.0, m->E, z, p, dst,
+      AxDFParams a{nullptr, w, m->opG32(), m->opG32lo(), m->opB32(), m->opB32lo(), m->D32, m->D32lo, h1, h2, h2 != 0.0, m->E, z, p, dst,
                    part_ax, m->eo64, m->eodf};
       return launch_ax_df(m->N, m->ax_var[2], true, a, s, nullptr);
     }
-    AxParams<double> a{nullptr, w, m->G64, m->B64, m->D64, h1, h2, h2 != 0.0, m->E, z, p, dst, part_ax};
+    AxParams<double> a{nullptr, w, m->opG64(), m->opB64(), m->D64, h1, h2, h2 != 0.0, m->E, z, p, dst, part_ax};
     return launch_ax_f64(m->N, m->ax_var[0], true, a, s, nullptr);
   };
 

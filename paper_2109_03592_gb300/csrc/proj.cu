@@ -26,6 +26,7 @@ struct sem_proj {
   sem_mesh* m = nullptr;
   int L = 0, l = 0;
   double h1 = 1.0, h2 = 0.0;
+  uint64_t coef_gen = 0;   // the mesh's coefficient generation the basis belongs to
   int64_t n = 0;
   double* X = nullptr;     // [L][n]
   double* AX = nullptr;    // [L][n]
@@ -150,6 +151,7 @@ sem_status sem_proj_create(const sem_mesh* mesh, int max_vectors, double h1, dou
   p->L = max_vectors;
   p->h1 = h1;
   p->h2 = h2;
+  p->coef_gen = mesh->coef_gen;
   p->n = mesh->n_local;
   const size_t vb = (size_t)p->n * sizeof(double);
   cudaError_t e = cudaMalloc((void**)&p->X, vb * max_vectors);
@@ -175,8 +177,7 @@ sem_status sem_proj_create(const sem_mesh* mesh, int max_vectors, double h1, dou
 sem_status sem_proj_destroy(sem_proj* p) {
   if (!p) return SEM_OK;
   cudaSetDevice(p->m->device);
-  cudaDeviceSynchronize();
-  free_proj(p);
+  free_proj(p);  // cudaFree waits for work still using the space (no device-wide sync: see sem_mesh_destroy)
   return SEM_OK;
 }
 
@@ -210,6 +211,10 @@ sem_status sem_proj_solve(sem_proj* p, const double* b_dev, double* x_dev, const
   }
   cudaStream_t s = (cudaStream_t)stream;
   sem_mesh* m = p->m;
+  if (p->coef_gen != m->coef_gen) {  // new per-point coefficients: the basis is no longer A-orthonormal
+    p->l = 0;
+    p->coef_gen = m->coef_gen;
+  }
   const int64_t n = p->n;
   const size_t vb = (size_t)n * sizeof(double);
   SEM_CUDA(cudaEventRecord(p->e0, s));

@@ -112,6 +112,30 @@ struct sem_mesh {
   double* eo64 = nullptr;
   float* eodf = nullptr;
 
+  // per-point coefficients (sem_mesh_set_coefficients): cG = h1[q] G and
+  // cB = h2[q] B in the operator's precisions, with their assembled
+  // diagonals; null while the coefficient is constant.  coef_gen counts the
+  // changes, so cached data derived from the operator can tell it is stale.
+  double* cG64 = nullptr;
+  float* cG32 = nullptr;
+  float* cG32lo = nullptr;
+  double* cdK = nullptr;
+  double* cB64 = nullptr;
+  float* cB32 = nullptr;
+  float* cB32lo = nullptr;
+  double* cdB = nullptr;
+  uint64_t coef_gen = 0;
+
+  // the operator's arrays: the plain geometry, or its per-point copies
+  const double* opG64() const { return cG64 ? cG64 : G64; }
+  const float* opG32() const { return cG64 ? cG32 : G32; }
+  const float* opG32lo() const { return cG64 ? cG32lo : G32lo; }
+  const double* opdK() const { return cG64 ? cdK : dK; }
+  const double* opB64() const { return cB64 ? cB64 : B64; }
+  const float* opB32() const { return cB64 ? cB32 : B32; }
+  const float* opB32lo() const { return cB64 ? cB32lo : B32lo; }
+  const double* opdB() const { return cB64 ? cdB : dB; }
+
   // local-operator kernel choice, set by the autotuner at creation:
   // variant index per precision (0 FP64 native, 1 FP32, 2 FP64 double-float)
   // and whether FP64 requests run the double-float kernel.

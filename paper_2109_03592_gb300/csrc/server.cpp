@@ -165,7 +165,8 @@ void engine_main(sem_server* srv, EngineThread* et) {
         continue;
       }
       q->x.resize(q->n_local);
-      cudaMemcpy(q->x.data(), q->x_dev, (size_t)q->n_local * sizeof(double), cudaMemcpyDeviceToHost);
+      cudaMemcpyAsync(q->x.data(), q->x_dev, (size_t)q->n_local * sizeof(double), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
       free_request_device(*q);
       complete(srv, q, q->breq.status);
       et->active[k] = et->active.back();

@@ -95,11 +95,11 @@ sem_status alloc_ws(sem_mesh* m, Workspace** out) {
 cudaError_t ax64(const sem_mesh* m, const double* u, double* w, double h1, double h2, bool fused,
                         const double* z, double* p, PcgState* st, double* part, cudaStream_t s) {
   if (m->fp64_df) {
-    AxDFParams a{u,      w, m->G32, m->G32lo, m->B32, m->B32lo, m->D32, m->D32lo, h1,     h2,
+    AxDFParams a{u,      w, m->opG32(), m->opG32lo(), m->opB32(), m->opB32lo(), m->D32, m->D32lo, h1, h2,
                  h2 != 0.0, m->E, z, p, st, part, m->eo64, m->eodf};
     return launch_ax_df(m->N, m->ax_var[2], fused, a, s, nullptr);
   }
-  AxParams<double> a{u, w, m->G64, m->B64, m->D64, h1, h2, h2 != 0.0, m->E, z, p, st, part, m->dev_err};
+  AxParams<double> a{u, w, m->opG64(), m->opB64(), m->D64, h1, h2, h2 != 0.0, m->E, z, p, st, part, m->dev_err};
   return launch_ax_f64(m->N, m->ax_var[0], fused, a, s, nullptr);
 }
 
@@ -110,14 +110,15 @@ cudaError_t ax64(const sem_mesh* m, const double* u, double* w, double h1, doubl
 // than FP64's, would set the attainable residual (measured: the E = 262,144
 // pipe stalled above 1e-10 with a 2^-46 input split).
 cudaError_t ax64_exact(const sem_mesh* m, const double* u, double* w, double h1, double h2, cudaStream_t s) {
-  AxParams<double> a{u, w, m->G64, m->B64, m->D64, h1, h2, h2 != 0.0, m->E, nullptr, nullptr, nullptr, nullptr,
+  AxParams<double> a{u, w, m->opG64(), m->opB64(), m->D64, h1, h2, h2 != 0.0, m->E, nullptr, nullptr, nullptr, nullptr,
                      m->dev_err};
   return launch_ax_f64(m->N, m->ax_var[0], false, a, s, nullptr);
 }
 
 static cudaError_t ax32(const sem_mesh* m, const float* u, float* w, double h1, double h2, bool fused,
                         const float* z, float* p, PcgState* st, double* part, cudaStream_t s) {
-  AxParams<float> a{u, w, m->G32, m->B32, m->D32, (float)h1, (float)h2, h2 != 0.0, m->E, z, p, st, part, m->dev_err};
+  AxParams<float> a{u, w, m->opG32(), m->opB32(), m->D32, (float)h1, (float)h2, h2 != 0.0, m->E, z, p, st, part,
+                    m->dev_err};
   int var = m->ax_var[1];
   // the bulk-copy kernels read u with 16-byte aligned copies: a caller's
   // unaligned u takes the faster of the register kernels instead
@@ -312,7 +313,7 @@ static sem_status get_graph(sem_mesh* m, Workspace* ws, bool fp32, double h1, do
   GraphSlot& g = fp32 ? ws->g32 : ws->g64;
   const int var = fp32 ? m->ax_var[1] : (m->fp64_df ? m->ax_var[2] : m->ax_var[0]);
   const int df = fp32 ? 0 : m->fp64_df;
-  if (g.exec && g.h1 == h1 && g.h2 == h2 && g.var == var && g.df == df) return SEM_OK;
+  if (g.exec && g.h1 == h1 && g.h2 == h2 && g.var == var && g.df == df && g.coef_gen == m->coef_gen) return SEM_OK;
   if (g.exec) {
     cudaGraphExecDestroy(g.exec);
     g.exec = nullptr;
@@ -342,6 +343,7 @@ static sem_status get_graph(sem_mesh* m, Workspace* ws, bool fp32, double h1, do
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
   g.h1 = h1;
   g.h2 = h2;
+  g.coef_gen = m->coef_gen;
   g.var = var;
   g.df = df;
   return SEM_OK;
@@ -609,7 +611,7 @@ static sem_status solve_common(const sem_mesh* cm, const double* b, double* x, b
   launch_mask(ws->x, m->wm, ws->n, ws->s);
   count_launches(1);
   if (!(ws->minv_h1 == o.h1 && ws->minv_h2 == o.h2)) {
-    launch_minv(ws->minv, ws->minv32, m->dK, m->dB, m->wm, o.h1, o.h2, ws->n, ws->s);
+    launch_minv(ws->minv, ws->minv32, m->opdK(), m->opdB(), m->wm, o.h1, o.h2, ws->n, ws->s);
     count_launches(1);
     ws->minv_h1 = o.h1;
     ws->minv_h2 = o.h2;

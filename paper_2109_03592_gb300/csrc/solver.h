@@ -9,7 +9,8 @@ struct GraphSlot {
   cudaGraphExec_t exec = nullptr;
   double h1 = NAN, h2 = NAN;
   int var = -1, df = -1;
-  int nodes = 0;  // kernel launches per graph launch
+  uint64_t coef_gen = 0;  // the mesh's coefficient generation (the graph holds its array pointers)
+  int nodes = 0;          // kernel launches per graph launch
 };
 
 struct Workspace {

@@ -78,6 +78,7 @@ SIGNATURES = {
     "sem_mesh_global_ids": (C.c_int, [_P, _P]),
     "sem_mesh_coords": (C.c_int, [_P, _P, _P]),
     "sem_mesh_geometry": (C.c_int, [_P, _P, _P, _P]),
+    "sem_mesh_set_coefficients": (C.c_int, [_P, _P, _P, _P]),
     "sem_mesh_weights": (C.c_int, [_P, _P, _P, _P]),
     "sem_ax": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, C.c_int, _P]),
     "sem_gs": (C.c_int, [_P, _P, C.c_int, C.c_int, _P]),
@@ -256,6 +257,16 @@ class Mesh:
         B = torch.empty(self.shape, dtype=torch.float64, device="cuda")
         _check(lib().sem_mesh_geometry(self._h, _dptr(G), _dptr(B), _stream(stream)), "sem_mesh_geometry")
         return G, B
+
+    def set_coefficients(self, h1=None, h2=None, stream=None):
+        """sem_mesh_set_coefficients: per-point h1, h2 (device FP64 tensors of
+        n_local values, local layout) multiplying the scalar h1, h2 of every
+        later operator call; None means 1 everywhere (both None: constant
+        coefficients again)."""
+        import torch
+        p1 = _dptr(h1, torch.float64, self.n_local) if h1 is not None else None
+        p2 = _dptr(h2, torch.float64, self.n_local) if h2 is not None else None
+        _check(lib().sem_mesh_set_coefficients(self._h, p1, p2, _stream(stream)), "sem_mesh_set_coefficients")
 
     def weights(self, stream=None):
         import torch
