@@ -99,6 +99,11 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_ax(const AxParams<T> 
 
   T pw = T(0);  // this thread's part of <p, A_L p> (n terms, accumulated in T)
   if (act) {
+    // the n values of B first, all in flight together: loaded next to the
+    // stores of w, each load waited in turn (w and B may alias for the compiler)
+    T rb[n];
+#pragma unroll
+    for (int k = 0; k < n; ++k) rb[k] = P.helm ? __ldg(P.B + base + k * n2) : T(0);
 #pragma unroll
     for (int k = 0; k < n; ++k) {
       T acc = rw[k];
@@ -106,7 +111,7 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_ax(const AxParams<T> 
       for (int l = 0; l < n; ++l)
         acc += sD[l * RP + i] * swre[k * PL + j * RP + l] + sD[l * RP + j] * swse[k * PL + l * RP + i];
       T out = P.h1 * acc;
-      if (P.helm) out += P.h2 * P.B[base + k * n2] * ru[k];
+      if (P.helm) out += P.h2 * rb[k] * ru[k];
       P.w[base + k * n2] = out;
       if (FUSED) pw += ru[k] * out;
     }

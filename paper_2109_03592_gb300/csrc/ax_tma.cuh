@@ -99,6 +99,14 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_ax_tma(const AxParams
     const bool act = e < P.E;
     const int64_t base = e * n3 + ij;
 
+    // h2 B u: B does not go through the copy ring (the Poisson operator
+    // needs no room for it).  Its n values are loaded here, before any store
+    // of this tile, so that their latency overlaps the contractions; loaded
+    // next to the stores of w, each load waited in turn (3x the time).
+    float rb[n];
+#pragma unroll
+    for (int k = 0; k < n; ++k) rb[k] = (act && P.helm) ? __ldg(P.B + base + k * n2) : 0.f;
+
     float ru[n];
     if (act) {
 #pragma unroll
@@ -155,7 +163,7 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_ax_tma(const AxParams
         for (int l = 0; l < n; ++l)
           acc += sD[l * n + i] * swr[le * n3 + k * n2 + j * n + l] + sD[l * n + j] * sws[le * n3 + k * n2 + l * n + i];
         float out = P.h1 * acc;
-        if (P.helm) out += P.h2 * P.B[base + k * n2] * ru[k];
+        if (P.helm) out += P.h2 * rb[k] * ru[k];
         P.w[base + k * n2] = out;
         if (FUSED) pw += ru[k] * out;
       }

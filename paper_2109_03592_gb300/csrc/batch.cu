@@ -161,6 +161,10 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_bax(const Table* __re
     const bool act = e < sl.E;
     const int64_t base = e * n3 + ij;
     const float beta = (float)sl.st->beta;
+    // B loaded ahead of the stores of this tile (see the single-mesh kernel)
+    float rb[n];
+#pragma unroll
+    for (int k = 0; k < n; ++k) rb[k] = (act && sl.helm) ? __ldg(sl.B + base + k * n2) : 0.f;
 
     float ru[n];
     if (act) {
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_bax(const Table* __re
         for (int l = 0; l < n; ++l)
           acc += sD[l * n + i] * swr[le * n3 + k * n2 + j * n + l] + sD[l * n + j] * sws[le * n3 + k * n2 + l * n + i];
         float out = sl.h1 * acc;
-        if (sl.helm) out += sl.h2 * sl.B[base + k * n2] * ru[k];
+        if (sl.helm) out += sl.h2 * rb[k] * ru[k];
         sl.w[base + k * n2] = out;
         pw += ru[k] * out;
       }
