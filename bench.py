@@ -198,15 +198,15 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- serving leg
 
-def serving_stream(count, rate, seed=4):
+def serving_stream(count, rate, seed=4, log2_e=(9.0, 15.0)):
     """Request stream through the batching server: Poisson arrivals at `rate`
-    per second; box or pipe meshes with E log-uniform in [512, 4096]; N in
+    per second; box or pipe meshes with E log-uniform in [512, 32768]; N in
     {5, 7, 9}; Poisson or Helmholtz (h2 log-uniform in [1e-2, 1e2]); mixed
     precision to 1e-10.  Latency = submit -> result visible to poll."""
     import numpy as np
     import paper_2109_03592_gb300 as sem
     from sem_inputs import serving
-    stream = serving.request_stream(seed=seed, count=count, rate=rate, log2_e=(9.0, 12.0))
+    stream = serving.request_stream(seed=seed, count=count, rate=rate, log2_e=log2_e)
     srv = sem.Server(max_slots=8)
     pending = {}
     t0 = time.perf_counter()
@@ -233,7 +233,8 @@ def serving_stream(count, rate, seed=4):
     return {"requests": count, "arrival_rate_per_s": rate, "throughput_solves_per_s": count / wall,
             "latency_ms": {"p50": pct(lat_ms, 50), "p99": pct(lat_ms, 99), "max": lat_ms[-1]},
             "max_rel_res": worst, "mode": "batched per order (one CUDA graph per order per step)",
-            "mix": "box/pipe, E log-uniform in [512, 4096], N in {5,7,9}, Poisson/Helmholtz, tol 1e-10"}
+            "mix": (f"box/pipe, E log-uniform in [{2 ** log2_e[0]:.0f}, {2 ** log2_e[1]:.0f}], N in {{5,7,9}}, "
+                    "Poisson/Helmholtz, tol 1e-10")}
 
 
 # ---------------------------------------------------------------- projection leg
@@ -276,6 +277,66 @@ def projection_leg(count=6, max_vectors=8, workload="pipe32768_n7"):
     return {"workload": f"{workload}: E={desc_elements(desc)} N={desc['N']}", "solves": count,
             "max_vectors": max_vectors, **out, "time_ratio": tw / to if to > 0 else None,
             "note": "first solve has an empty space; ms includes projection and basis update"}
+
+
+def velocity_helmholtz_leg(workload="pipe32768_n7", re=1.0e4, dt=2.0e-4):
+    """The velocity step of Sec. 2, Eq. 4: (b0/dt) u - div(nu grad u) / Re = rhs for the three
+    velocity components on one mesh.  Per-point viscosity nu(x) (sem_mesh_set_coefficients,
+    seeded smooth field times per-element jumps), h1 = 1/Re with Re = 1e4, h2 = b0/dt with BDF2's
+    b0 = 3/2 and dt = 2e-4; mixed precision to 1e-10; the three solves as one batch
+    (sem_pcg_solve_batch) and one at a time."""
+    import torch
+    import paper_2109_03592_gb300 as sem
+    from sem_inputs import coefficients, configs, forcing
+    desc = configs.mesh_desc(workload)
+    m = sem.Mesh(desc)
+    xyz = m.coords()
+    m.set_coefficients(torch.from_numpy(coefficients.viscosity(31, xyz.cpu().numpy())).cuda(), None)
+    h1, h2 = 1.0 / re, 1.5 / dt
+    bs = []
+    for c in range(3):
+        b = torch.empty(m.shape, dtype=torch.float64, device="cuda")
+        m.rhs(forcing.evaluate_torch(xyz, forcing.random_modes(40 + c, L=desc.get("L", 8.0))), b)
+        bs.append(b)
+    del xyz
+    opts = dict(tol=1e-10, h1=h1, h2=h2, prec=sem.MIXED)
+    xs = [torch.zeros_like(b) for b in bs]
+
+    def one_at_a_time():
+        res = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for b, x in zip(bs, xs):
+            x.zero_()
+            res.append(m.solve(b, x, **opts))
+        torch.cuda.synchronize()
+        return res, time.perf_counter() - t0
+
+    def batched():
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, res = sem.solve_batch([m] * 3, bs, xs, [dict(tol=1e-10, h1=h1, h2=h2)] * 3)
+        torch.cuda.synchronize()
+        if st != sem.SEM_OK:
+            raise RuntimeError(f"velocity batch failed: {st} {res}")
+        return res, time.perf_counter() - t0
+
+    one_at_a_time()  # warm-up (graphs, workspace)
+    batched()
+    seq, t_seq = one_at_a_time()
+    bat, t_bat = batched()
+    m.close()
+    for r in seq + bat:
+        if r["status"] != 0:
+            raise RuntimeError(f"velocity solve failed: {r}")
+    return {"workload": f"{workload}: E={desc_elements(desc)} N={desc['N']}", "components": 3,
+            "coefficients": "h1 = nu(x)/Re per point, Re = 1e4; h2 = b0/dt = 7500", "tol": 1e-10,
+            "iters": [r["iters"] for r in bat], "iters_one_at_a_time": [r["iters"] for r in seq],
+            "max_rel_res": max(r["rel_res"] for r in seq + bat),
+            "batched_ms": t_bat * 1e3, "one_at_a_time_ms": t_seq * 1e3,
+            "note": "wall time of the three solves (host-synchronous calls, device-resident data)"}
 
 
 def desc_elements(d):
@@ -416,6 +477,9 @@ def run_gpu(args):
     proj = None
     if not args.no_projection:
         proj = projection_leg()
+    velocity = None
+    if not args.no_velocity:
+        velocity = velocity_helmholtz_leg()
 
     line = None
     if rank == 0:
@@ -444,6 +508,7 @@ def run_gpu(args):
             "fp64_pcg": fp64,
             "serving": serving,
             "projection": proj,
+            "velocity_helmholtz": velocity,
             "roofline": {"bound": "hbm", "kernel": fp32_kernel_name(m.N, m.ax_variant(sem.FP32)),
                          "timed": "sem_ax FP32 launches on the bench mesh, CUDA events on the launching stream, "
                                   "after the timed solves (the inner CG runs the fused form of the same kernel)",
@@ -474,8 +539,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-projection", action="store_true", help="skip the projection leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream leg")
+    ap.add_argument("--no-velocity", action="store_true", help="skip the three-component velocity Helmholtz leg")
     ap.add_argument("--serving-requests", type=int, default=64)
-    ap.add_argument("--serving-rate", type=float, default=20.0)
+    ap.add_argument("--serving-rate", type=float, default=4.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

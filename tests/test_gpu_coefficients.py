@@ -261,6 +261,32 @@ def test_batch_with_per_point_coefficients():
         assert _residual(probs[i], bs[i].cpu().numpy(), xs[i].cpu().numpy()) <= 1e-10
 
 
+def test_three_velocity_components_with_per_point_viscosity():
+    """One velocity step of Sec. 2, Eq. 4 with a variable viscosity: the three
+    components on one mesh in one batch, each equal to its batch of one and
+    within the oracle's residual bound for the per-point operator."""
+    import torch
+    import paper_2109_03592_gb300 as sem
+    d = dict(kind="pipe", nc=4, nr=2, nzp=3, N=7, L=2.0)
+    m = sem.Mesh(d)
+    om = _om(d)
+    nu, _ = _fields(om, 91)
+    m.set_coefficients(to_gpu(nu), None)
+    h1, h2 = 0.05, 30.0  # 1/Re, b0/dt
+    P = solver.Problem(om, h1 * nu, h2)
+    bs = [to_gpu(P.rhs(forcing.evaluate(om.xyz, forcing.random_modes(410 + c, L=2.0)))) for c in range(3)]
+    opts = [dict(tol=1e-10, h1=h1, h2=h2)] * 3
+    xs = [torch.zeros_like(b) for b in bs]
+    st, res = sem.solve_batch([m, m, m], bs, xs, opts)
+    assert st == sem.SEM_OK, res
+    for c in range(3):
+        x1 = torch.zeros_like(bs[c])
+        st1, r1 = sem.solve_batch([m], [bs[c]], [x1], [opts[c]])
+        assert st1 == sem.SEM_OK
+        assert torch.equal(xs[c], x1) and res[c]["iters"] == r1[0]["iters"]
+        assert _residual(P, bs[c].cpu().numpy(), xs[c].cpu().numpy()) <= 1e-10
+
+
 def test_projection_space_follows_the_coefficients():
     import torch
     import paper_2109_03592_gb300 as sem
