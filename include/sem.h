@@ -234,8 +234,11 @@ sem_status sem_pcg_solve_host(const sem_mesh* mesh, const double* b_host, double
  * data, so its result equals that of a batch of one.  Synchronous.  A mesh
  * may appear several times (several right-hand sides on one mesh, e.g. the
  * three velocity components of a Helmholtz step); each repeat gets its own
- * work vectors, allocated for the call.  Returns SEM_OK, or the first
- * request's failing status (results[k].status has each). */
+ * work vectors (~80 B per local point), which the mesh keeps for its later
+ * batches and frees with sem_mesh_destroy.  The engine of an order (its
+ * buffers and captured graph) is kept for later calls of the same order.
+ * Returns SEM_OK, or the first request's failing status (results[k].status
+ * has each). */
 sem_status sem_pcg_solve_batch(const sem_mesh* const* meshes, const double* const* b_dev, double* const* x_dev,
                                const sem_solve_opts* opts, sem_solve_result* results, int count, void* stream);
 

@@ -21,6 +21,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
+#include <mutex>
 #include <vector>
 
 #include "ax_impl.cuh"
@@ -433,11 +435,19 @@ class EngineImpl {
   ~EngineImpl() { release(); }
   int order() const { return N_; }
 
+  // Order the engine's stream after the caller's (at init, and each time a
+  // cached engine serves another call).
+  sem_status attach(cudaStream_t user) {
+    SEM_CUDA(cudaEventRecord(eu_, user));
+    SEM_CUDA(cudaStreamWaitEvent(s_, eu_, 0));
+    return SEM_OK;
+  }
+
   sem_status init(cudaStream_t user) {
     SEM_CUDA(cudaStreamCreateWithFlags(&s_, cudaStreamNonBlocking));
     SEM_CUDA(cudaEventCreateWithFlags(&eu_, cudaEventDisableTiming));
-    SEM_CUDA(cudaEventRecord(eu_, user));
-    SEM_CUDA(cudaStreamWaitEvent(s_, eu_, 0));
+    sem_status st = attach(user);
+    if (st != SEM_OK) return st;
     SEM_CUDA(cudaMallocHost((void**)&h_tab_, sizeof(Table)));
     SEM_CUDA(cudaMalloc((void**)&d_tab_, sizeof(Table)));
     SEM_CUDA(cudaMallocHost((void**)&h_st_, kMaxSlots * sizeof(PcgState)));
@@ -474,8 +484,13 @@ class EngineImpl {
       if (o && o->ws == m->ws) taken = true;
     if (taken) {
       Workspace* own = nullptr;
-      sem_status st = alloc_ws(m, &own);
-      if (st != SEM_OK) return st;
+      if (!m->spare_ws.empty()) {  // one kept from an earlier batch on this mesh
+        own = m->spare_ws.back();
+        m->spare_ws.pop_back();
+      } else {
+        sem_status st = alloc_ws(m, &own);
+        if (st != SEM_OK) return st;
+      }
       q->ws = own;
       q->own_ws = true;
     } else {
@@ -596,8 +611,8 @@ class EngineImpl {
     Workspace* ws = q->ws;
     SEM_CUDA(cudaMemcpyAsync(q->x, ws->x, (size_t)ws->n * sizeof(double), cudaMemcpyDeviceToDevice, ws->s));
     SEM_CUDA(cudaStreamSynchronize(ws->s));
-    if (q->own_ws) {
-      free_ws(ws);
+    if (q->own_ws) {  // kept on the mesh for its next batch
+      q->m->spare_ws.push_back(ws);
       q->ws = nullptr;
       q->own_ws = false;
     }
@@ -768,6 +783,7 @@ class EngineImpl {
 Engine::Engine(int N) : impl_(new EngineImpl(N)) {}
 Engine::~Engine() { delete impl_; }
 sem_status Engine::init(cudaStream_t user) { return impl_->init(user); }
+sem_status Engine::attach(cudaStream_t user) { return impl_->attach(user); }
 sem_status Engine::add(Req* q) { return impl_->add(q); }
 sem_status Engine::step() { return impl_->step(); }
 bool Engine::idle() const { return impl_->idle(); }
@@ -777,6 +793,31 @@ int Engine::order() const { return impl_->order(); }
 }  // namespace sem
 
 using namespace sem;
+
+namespace {
+// Idle engines of sem_pcg_solve_batch by (device, order): a later call reuses
+// one with its buffers and captured graph instead of building and capturing
+// anew.  Never destroyed: freeing CUDA resources during static destruction at
+// exit is not safe, and the driver reclaims them with the process.
+std::mutex g_engine_mutex;
+auto* g_idle_engines = new std::vector<std::pair<std::pair<int, int>, batch::Engine*>>();
+
+batch::Engine* take_idle_engine(int dev, int N) {
+  std::lock_guard<std::mutex> lk(g_engine_mutex);
+  for (size_t k = 0; k < g_idle_engines->size(); ++k)
+    if ((*g_idle_engines)[k].first == std::make_pair(dev, N)) {
+      batch::Engine* e = (*g_idle_engines)[k].second;
+      g_idle_engines->erase(g_idle_engines->begin() + k);
+      return e;
+    }
+  return nullptr;
+}
+
+void put_idle_engine(int dev, int N, batch::Engine* e) {
+  std::lock_guard<std::mutex> lk(g_engine_mutex);
+  g_idle_engines->push_back({{dev, N}, e});
+}
+}  // namespace
 
 extern "C" sem_status sem_pcg_solve_batch(const sem_mesh* const* meshes, const double* const* b_dev,
                                           double* const* x_dev, const sem_solve_opts* opts,
@@ -824,9 +865,18 @@ extern "C" sem_status sem_pcg_solve_batch(const sem_mesh* const* meshes, const d
   distinct.erase(std::unique(distinct.begin(), distinct.end()), distinct.end());
   std::vector<std::unique_lock<std::mutex>> locks;
   for (sem_mesh* m : distinct) locks.emplace_back(m->ws_mutex);
-  batch::Engine eng(N);
-  sem_status st = eng.init((cudaStream_t)stream);
+  int dev = 0;
+  SEM_CUDA(cudaGetDevice(&dev));
+  std::unique_ptr<batch::Engine> held(take_idle_engine(dev, N));
+  sem_status st;
+  if (held) {
+    st = held->attach((cudaStream_t)stream);
+  } else {
+    held.reset(new batch::Engine(N));
+    st = held->init((cudaStream_t)stream);
+  }
   if (st != SEM_OK) return st;
+  batch::Engine& eng = *held;
   size_t next = 0;
   const int max_steps = 1 << 20;
   for (int step = 0; step < max_steps; ++step) {
@@ -841,6 +891,7 @@ extern "C" sem_status sem_pcg_solve_batch(const sem_mesh* const* meshes, const d
     st = eng.step();
     if (st != SEM_OK) return st;
   }
+  if (eng.idle()) put_idle_engine(dev, N, held.release());  // kept with its captured graph
   sem_status first_bad = SEM_OK;
   for (auto& q : reqs)
     if (q.status != SEM_OK && first_bad == SEM_OK) first_bad = q.status;

@@ -32,6 +32,8 @@ class Engine {
   explicit Engine(int N);
   ~Engine();
   sem_status init(cudaStream_t user);
+  // Order the engine after `user` (a cached engine serving another call).
+  sem_status attach(cudaStream_t user);
   // FP64 set-up of a request and its activation in a free slot; SEM_ERR_BUSY
   // when every slot is taken.  The request may finish inside add() (b = 0 or
   // x already converged).

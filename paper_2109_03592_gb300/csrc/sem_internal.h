@@ -145,6 +145,9 @@ struct sem_mesh {
 
   std::mutex ws_mutex;
   sem::Workspace* ws = nullptr;  // cached solver workspace
+  // workspaces of further right-hand sides on this mesh in one batch, kept
+  // for the next batch (guarded by ws_mutex; freed with the mesh)
+  std::vector<sem::Workspace*> spare_ws;
 };
 
 namespace sem {

@@ -53,6 +53,8 @@ void release_workspace(sem_mesh* m) {
   std::lock_guard<std::mutex> lk(m->ws_mutex);
   destroy_ws(m->ws);
   m->ws = nullptr;
+  for (Workspace* w : m->spare_ws) destroy_ws(w);
+  m->spare_ws.clear();
 }
 
 static int max_ax_grid(const sem_mesh* m) {
