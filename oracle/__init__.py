@@ -20,10 +20,14 @@ The oracle restates, slowly and directly, what the method of Vincent et al.,
 * Jacobi-preconditioned CG and FP32-inner / FP64-outer iterative
   refinement (Sec. 2: "iterative solvers with proper preconditioners") --
   ``solver``.
+* Projection onto previous solutions (Sec. 2, Fischer 1998) -- ``projection``.
+* The staggered P_N - P_{N-2} pressure space (GL points), the weak divergence
+  and gradient, and the consistent Poisson operator E = D B^{-1} D^T of
+  Sec. 2, Eq. 5 -- ``pressure``.
 
 Each function cites the passage it follows.  No code here is shared with the
 CUDA path; the two meet only through ``sem_inputs`` (seeded random draws and
 mesh descriptors, which contain none of the method's arithmetic).
 """
 
-from . import gll, mesh, geometry, operator, numbering, solver  # noqa: F401
+from . import gll, mesh, geometry, operator, numbering, solver, pressure  # noqa: F401

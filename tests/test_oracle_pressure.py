@@ -1,0 +1,161 @@
+"""Pins for the oracle's P_N - P_{N-2} pressure operators (Sec. 2: GL pressure
+points; Sec. 2, Eq. 5: the consistent Poisson operator E = D B^{-1} D^T)."""
+
+import numpy as np
+import pytest
+
+from oracle import gll, mesh, pressure, solver
+from sem_inputs import vectors
+
+
+@pytest.mark.parametrize("m,nodes,weights", [
+    (1, [0.0], [2.0]),
+    (2, [-1 / np.sqrt(3), 1 / np.sqrt(3)], [1.0, 1.0]),
+    (3, [-np.sqrt(0.6), 0.0, np.sqrt(0.6)], [5 / 9, 8 / 9, 5 / 9]),
+])
+def test_gl_closed_forms(m, nodes, weights):
+    z, r = pressure.gl_nodes_weights(m)
+    np.testing.assert_allclose(z, nodes, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(r, weights, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("m", [1, 4, 10])
+def test_gl_quadrature_exact_to_degree_2m_minus_1(m):
+    z, r = pressure.gl_nodes_weights(m)
+    for d in range(2 * m):
+        exact = 0.0 if d % 2 else 2.0 / (d + 1)
+        assert abs(np.sum(r * z ** d) - exact) < 1e-14
+
+
+@pytest.mark.parametrize("N", [2, 3, 6, 11])
+def test_interpolation_and_derivative_at_gl_points(N):
+    xi, _ = gll.nodes_weights(N)
+    zeta, _ = pressure.gl_nodes_weights(N - 1)
+    I, Dg, _ = pressure.interpolation_matrices(N)
+    for d in range(N + 1):
+        np.testing.assert_allclose(I @ xi ** d, zeta ** d, rtol=0, atol=1e-13)
+        deriv = d * zeta ** (d - 1) if d else np.zeros_like(zeta)
+        np.testing.assert_allclose(Dg @ xi ** d, deriv, rtol=0, atol=1e-11 * max(1, d))
+
+
+def _gl_coords(m_, N):
+    I, _, _ = pressure.interpolation_matrices(N)
+    return np.stack([pressure._contract(I, I, I, m_.xyz[:, c]) for c in range(3)])  # [3, E, m, m, m]
+
+
+def _monomial_integral(p, L):
+    return L ** (p + 1) / (p + 1)
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_weak_divergence_is_exact_quadrature_on_affine_box(N):
+    """For u_a of degree <= N-1 and psi of degree <= N-2 in each coordinate, GL
+    quadrature is exact on axis-aligned affine elements: sum_q psi(x_q) (D_a u_a)_q
+    = int psi d(u_a)/dx_a dx, taken here in closed form from the monomials."""
+    lx, ly, lz = 1.0, 2.0, 3.5
+    m_ = mesh.box(2, 3, 1, N, lx, ly, lz)
+    F, _ = pressure.div_factors(m_)
+    X = m_.xyz
+    Xg = _gl_coords(m_, N)
+    rng = np.random.default_rng(7)
+    for a in range(3):
+        for _ in range(3):
+            e_u = rng.integers(0, N, size=3)       # degree <= N-1 per coordinate
+            e_p = rng.integers(0, N - 1, size=3)   # degree <= N-2
+            e_u[a] = max(e_u[a], 1)
+            u = np.zeros((3, m_.E) + (N + 1,) * 3)
+            u[a] = X[:, 0] ** e_u[0] * X[:, 1] ** e_u[1] * X[:, 2] ** e_u[2]
+            psi = Xg[0] ** e_p[0] * Xg[1] ** e_p[1] * Xg[2] ** e_p[2]
+            got = np.sum(psi * pressure.div_local(N, F, u))
+            L = (lx, ly, lz)
+            exact = float(e_u[a])
+            for c in range(3):
+                pw = e_p[c] + e_u[c] - (1 if c == a else 0)
+                exact *= _monomial_integral(pw, L[c])
+            assert abs(got - exact) <= 1e-12 * max(1.0, abs(exact)), (a, e_u, e_p, got, exact)
+
+
+def test_divergence_of_coordinates_is_gl_volume_on_curved_pipe():
+    """The coordinates are in the isoparametric space, so div(x, 0, 0) at a GL
+    point is rho^3 sum_b adj(J)_{b0} J_{0b} = rho^3 det(J), and div(y, 0, 0) is 0
+    (adj(J) J = det(J) I).  A transposed adjugate fails this on curved elements."""
+    N = 5
+    m_ = mesh.pipe(2, 2, 2, N, L=2.0)
+    F, det = pressure.div_factors(m_)
+    _, _, rho = pressure.interpolation_matrices(N)
+    rho3 = rho[:, None, None] * rho[None, :, None] * rho[None, None, :]
+    vol = rho3 * det
+    for a in range(3):
+        for c in range(3):
+            u = np.zeros((3, m_.E) + (N + 1,) * 3)
+            u[a] = m_.xyz[:, c]
+            d = pressure.div_local(N, F, u)
+            if a == c:
+                np.testing.assert_allclose(d, vol, rtol=1e-13, atol=0)
+            else:
+                assert np.abs(d).max() < 1e-13 * vol.max()
+    # the GL quadrature of the volume converges to pi R^2 L
+    assert abs(vol.sum() - np.pi * 2.0) < 1e-2
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_affine_element_matches_kronecker_divergence(N):
+    """On one axis-aligned element of size hx x hy x hz: F[b, a] = 0 for b != a and
+    D_0 = (hy hz / 4) diag(rho (x) rho (x) rho) (I (x) I (x) Dg) (k factor leftmost)."""
+    hx, hy, hz = 0.5, 2.0 / 3.0, 3.5
+    m_ = mesh.box(1, 1, 1, N, hx, hy, hz)
+    F, _ = pressure.div_factors(m_)
+    I, Dg, rho = pressure.interpolation_matrices(N)
+    R3 = np.diag(np.kron(rho, np.kron(rho, rho)))
+    kron3 = lambda a, b, c: np.kron(a, np.kron(b, c))  # noqa: E731
+    K = [(hy * hz / 4) * R3 @ kron3(I, I, Dg),
+         (hx * hz / 4) * R3 @ kron3(I, Dg, I),
+         (hx * hy / 4) * R3 @ kron3(Dg, I, I)]
+    n3 = (N + 1) ** 3
+    for a in range(3):
+        cols = []
+        for q in range(n3):
+            u = np.zeros((3, 1) + (N + 1,) * 3)
+            u[a].reshape(-1)[q] = 1.0
+            cols.append(pressure.div_local(N, F, u).reshape(-1))
+        A = np.array(cols).T
+        assert np.abs(A - K[a]).max() <= 1e-14 * np.abs(K[a]).max()
+
+
+def test_gradient_is_the_transpose_of_divergence():
+    N = 5
+    m_ = mesh.pipe(2, 1, 2, N, L=1.5)
+    F, _ = pressure.div_factors(m_)
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal((3, m_.E) + (N + 1,) * 3)
+    p = rng.standard_normal((m_.E,) + (N - 1,) * 3)
+    lhs = np.sum(p * pressure.div_local(N, F, u))
+    rhs = np.sum(pressure.grad_local(N, F, p) * u)
+    assert abs(lhs - rhs) < 1e-13 * abs(lhs) * 10
+
+
+def test_consistent_poisson_operator_has_only_the_constant_null_mode():
+    """Box with Dirichlet velocity on every face, N = 4: E is symmetric positive
+    semi-definite; constants span its null space (GL quadrature is exact for the
+    weak gradient of a constant on affine elements when N >= 3), and there is no
+    other (spurious) zero mode -- the point of the staggered pair."""
+    m_ = mesh.box(2, 2, 2, 4)
+    P = pressure.Pressure(solver.Problem(m_))
+    A = P.dense()
+    assert np.abs(A - A.T).max() < 1e-13 * np.abs(A).max()
+    ones = np.ones(P.shape)
+    assert np.abs(P.E(ones)).max() < 1e-13 * np.abs(A).max()
+    ev = np.linalg.eigvalsh(0.5 * (A + A.T))
+    assert ev[0] > -1e-13 * ev[-1]
+    assert abs(ev[0]) < 1e-13 * ev[-1]
+    assert ev[1] > 1e-4 * ev[-1]
+
+
+def test_operator_symmetry_on_curved_pipe():
+    m_ = mesh.pipe(2, 1, 2, 4, L=1.0)
+    P = pressure.Pressure(solver.Problem(m_))
+    p = vectors.local_field(11, m_.E, 3)
+    q = vectors.local_field(12, m_.E, 3)
+    a, b = np.sum(q * P.E(p)), np.sum(p * P.E(q))
+    assert abs(a - b) < 1e-13 * abs(a) * 10
+    assert np.sum(p * P.E(p)) > 0
