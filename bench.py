@@ -344,6 +344,43 @@ def velocity_helmholtz_leg(workload, re=1.0e4, dt=2.0e-4, reps=5):
             "note": "median wall time of the three solves (host-synchronous calls, device-resident data)"}
 
 
+def pressure_leg(m, stream, reps):
+    """The consistent Poisson operator E = D B^-1 D^T of the P_N - P_{N-2}
+    pressure space (Sec. 2, Eq. 5) on the bench mesh: sem_pressure_apply
+    (weak gradient, three QQ^T with mask, inverse mass and weak divergence),
+    timed with CUDA events on the launching stream after a first call that
+    builds the GL-point factors.  Algorithmic work per element, m = N - 1 GL
+    and n = N + 1 GLL points per direction: bytes = m^3 (p 8 + F 72 read twice
+    + q 8) + n^3 (velocity 24 written and read, inverse mass 8) plus three
+    FP64 QQ^T passes (20 B per shared point); FP64 multiply-adds = 9 (m (m^2 n
+    + m n^2 + n^3)) for D^T and 9 (n (n^2 m + n m^2 + m^3)) for D."""
+    import torch
+    mm, n = m.N - 1, m.N + 1
+    m3, n3 = mm ** 3, n ** 3
+    p = torch.randn(m.pressure_shape, dtype=torch.float64, device="cuda")
+    q = torch.empty_like(p)
+    work = torch.empty(3 * m.n_local, dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    m.pressure_apply(p, q, work)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    apply_ms = time_kernel(lambda: m.pressure_apply(p, q, work), reps, stream)
+    u = work.view((3,) + m.shape)
+    grad_ms = time_kernel(lambda: m.pressure_grad(p, u), reps, stream)
+    div_ms = time_kernel(lambda: m.pressure_div(u, q), reps, stream)
+    shared = 1.0 - (max(m.N - 1, 0) ** 3) / n3
+    bytes_el = m3 * (8 + 2 * 72 + 8) + n3 * (2 * 24 + 8) + 3 * 20 * shared * n3
+    fma_el = 9 * (mm * (mm * mm * n + mm * n * n + n3)) + 9 * (n * (n * n * mm + n * mm * mm + m3))
+    dofs = m.E * m3
+    del p, q, work, u
+    return {"workload": f"E={m.E} N={m.N}: {dofs} pressure values on the GL points",
+            "apply_ms": apply_ms, "grad_ms": grad_ms, "div_ms": div_ms, "first_call_ms": setup_ms,
+            "gdofs": dofs / (apply_ms * 1e6),
+            "algorithmic_gbs": bytes_el * m.E / (apply_ms * 1e6),
+            "fp64_tflops": 2 * fma_el * m.E / (apply_ms * 1e9),
+            "bound": "fp64 pipe (native FP64 contractions)"}
+
+
 def desc_elements(d):
     return d["nx"] * d["ny"] * d["nz"] if d["kind"] == "box" else d["nc"] * (d["nc"] + 4 * d["nr"]) * d["nzp"]
 
@@ -455,6 +492,7 @@ def run_gpu(args):
     gs64_ms = time_kernel(lambda: m.gs(w64, apply_mask=True), reps, stream)
     gs32_ms = time_kernel(lambda: m.gs(w32, apply_mask=True, prec=sem.FP32), reps, stream)
     del u64, w64, u32, w32
+    pressure = None if args.no_pressure else pressure_leg(m, stream, reps)
     ax32_gbs = AX_BYTES["fp32"] * P / (ax32_ms * 1e6)
     ax64_gbs = AX_BYTES["fp64"] * P / (ax64_ms * 1e6)
 
@@ -514,6 +552,7 @@ def run_gpu(args):
             "serving": serving,
             "projection": proj,
             "velocity_helmholtz": velocity,
+            "pressure_operator": pressure,
             "roofline": {"bound": "hbm", "kernel": fp32_kernel_name(m.N, m.ax_variant(sem.FP32)),
                          "timed": "sem_ax FP32 launches on the bench mesh, CUDA events on the launching stream, "
                                   "after the timed solves (the inner CG runs the fused form of the same kernel)",
@@ -543,6 +582,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the FP64 PCG comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-projection", action="store_true", help="skip the projection leg")
+    ap.add_argument("--no-pressure", action="store_true", help="skip the P_N - P_{N-2} pressure-operator leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream leg")
     ap.add_argument("--no-velocity", action="store_true", help="skip the three-component velocity Helmholtz leg")
     ap.add_argument("--serving-requests", type=int, default=64)

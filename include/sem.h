@@ -305,6 +305,57 @@ sem_status sem_proj_size(const sem_proj* proj, int* nvec);
 /* Empties the space (after the operator or the mesh changed). */
 sem_status sem_proj_reset(sem_proj* proj);
 
+/* ---- staggered P_N - P_{N-2} pressure space ------------------------------ */
+
+/* Sec. 2 discretises velocity with Lagrange interpolants of order N on the
+ * GLL points and pressure with interpolants of order N - 2 on the
+ * Gauss-Legendre (GL) points, and solves the consistent Poisson equation for
+ * the pressure update (Sec. 2, Eq. 5).  With m = N - 1 GL points per
+ * direction, a pressure field is element-local (discontinuous): [E][m^3]
+ * doubles, i fastest, n_pressure = E m^3 values.  A velocity is three local
+ * vectors, component-major: [3][n_local] doubles (component a of local point
+ * l at a * n_local + l).
+ *
+ * Definitions (the paper does not write them out; textbook staggered SEM):
+ * at every GL point q of an element, J = dx/dr of the isoparametric map
+ * evaluated there, rho_q = rho_i rho_j rho_k (GL weights) and
+ *   F[b][a](q) = rho_q adj(J)_{ba} = rho_q det(J) (dr_b/dx_a);
+ * the weak divergence  (D u)_q = sum_{a,b} F[b][a](q) (d u_a / d r_b)(q)
+ * (the GL quadrature of the divergence against the GL Lagrange basis), the
+ * weak gradient D^T (its transpose), and
+ *   E p = sum_a D_a M^{-1} D_a^T p,   M^{-1} v = mask QQ^T(v) / QQ^T(B),
+ * the inverse of the assembled GLL mass on the velocity nodes that are not
+ * Dirichlet.  E is symmetric positive semi-definite; with Dirichlet velocity
+ * on the whole boundary of an affine mesh (N >= 3) the constants span its
+ * null space.
+ *
+ * All calls: FP64, asynchronous on `stream`, except that the first pressure
+ * call on a mesh builds its GL-point data (9 m^3 doubles per element) on
+ * `stream` and synchronises `stream` (so it must not be made while `stream`
+ * is being captured).  Errors: SEM_ERR_INVALID (null argument, N < 2,
+ * overlapping buffers), SEM_ERR_OOM, SEM_ERR_BAD_MESH (det J <= 0 at a GL
+ * point), SEM_ERR_CUDA. */
+
+/* Number of pressure values of the mesh: E (N-1)^3. */
+sem_status sem_pressure_info(const sem_mesh* mesh, int64_t* n_pressure);
+
+/* Copy of the GL-point factors F [E][9][m^3] (entry 3 b + a is F[b][a]). */
+sem_status sem_pressure_factors(const sem_mesh* mesh, double* F_dev, void* stream);
+
+/* u_a = (D_a^T p) element by element: p [E][m^3] -> u [3][n_local]; no
+ * assembly, no mask.  p and u must not overlap. */
+sem_status sem_pressure_grad(const sem_mesh* mesh, const double* p_dev, double* u_dev, void* stream);
+
+/* q = sum_a D_a u_a element by element: u [3][n_local] -> q [E][m^3]. u and
+ * q must not overlap. */
+sem_status sem_pressure_div(const sem_mesh* mesh, const double* u_dev, double* q_dev, void* stream);
+
+/* q = E p (Sec. 2, Eq. 5).  work_dev: caller-owned scratch of 3 n_local
+ * doubles (the three velocity components), overwritten; it must not overlap
+ * p or q.  q may equal p (p is read in full before q is written). */
+sem_status sem_pressure_apply(const sem_mesh* mesh, const double* p_dev, double* q_dev, double* work_dev,
+                              void* stream);
+
 /* ---- serving ------------------------------------------------------------ */
 
 typedef struct {

@@ -74,6 +74,9 @@ void free_mesh_arrays(sem_mesh* m) {
   dev_free(m->cB32);
   dev_free(m->cB32lo);
   dev_free(m->cdB);
+  dev_free(m->Fgl);
+  dev_free(m->Igl);
+  dev_free(m->DIgl);
 }
 
 #define SEM_TRY(expr)                   \

@@ -131,4 +131,15 @@ void launch_zero_f32(float* a, int64_t n, cudaStream_t s);
 // pAp and alpha from the per-block partials of a fused local operator
 cudaError_t launch_pap_finish(const double* partial, int count, PcgState* st, cudaStream_t s);
 
+// ---- P_N - P_{N-2} pressure space (pressure.cu) ----
+// m = N - 1 GL points, n = N + 1 GLL points per direction; Ig, DIg [m][n];
+// F [E][9][m^3] (index 3 b + a); u [3][n_local]; pressures [E][m^3].
+size_t gl_factors_smem(int n, int m);
+cudaError_t launch_gl_factors(const double* xyz, const double* Ig, const double* DIg, const double* rho, int n, int m,
+                              int64_t E, double* F, int* bad, cudaStream_t s);
+cudaError_t launch_pgrad(const double* p, const double* F, const double* Ig, const double* DIg, int n, int m,
+                         int64_t E, double* u, int64_t n_local, cudaStream_t s);
+cudaError_t launch_pdiv(const double* u, const double* dB, const double* F, const double* Ig, const double* DIg, int n,
+                        int m, int64_t E, double* out, int64_t n_local, cudaStream_t s);
+
 }  // namespace sem

@@ -1,0 +1,249 @@
+// Kernels of the staggered P_N - P_{N-2} pressure space (Sec. 2: velocity on
+// the GLL points of order N, pressure on the Gauss-Legendre (GL) points of
+// order N-2; Sec. 2, Eq. 5: the consistent Poisson equation for the pressure).
+//
+// With m = N - 1 GL points and n = N + 1 GLL points per direction, Ig[i][l] =
+// l_l(zeta_i) (the GLL basis at the GL points) and DIg[i][l] = l_l'(zeta_i):
+//   * factors F[b][a](q) = rho_i rho_j rho_k adj(J)_{ba} at every GL point q,
+//     J = dx/dr of the isoparametric map (rho: GL weights, adj(J) = det(J) J^-1);
+//   * weak divergence  (D u)_q = sum_{a,b} F[b][a](q) (C_b u_a)(q), where C_b
+//     differentiates along direction b and interpolates along the other two
+//     (DIg along b, Ig elsewhere);
+//   * weak gradient    u_a = sum_b C_b^T (F[b][a] p), the transpose of D.
+// Every kernel runs one CTA per element and applies each C_b as three 1D
+// contractions through shared memory (sum factorisation), in FP64.
+#include "kernels.h"
+
+namespace sem {
+
+// GL-point factors.  Dynamic shared memory: X [3][n^3] (coordinates relative
+// to the element's first node; D annihilates constants), Y and Yd [3][m][n][n]
+// (the coordinates interpolated, resp. differentiated, along k).
+__global__ void k_gl_factors(const double* __restrict__ xyz, const double* __restrict__ Ig,
+                             const double* __restrict__ DIg, const double* __restrict__ rho, int n, int m, int64_t E,
+                             double* __restrict__ F, int* bad) {
+  extern __shared__ double sm[];
+  const int n2 = n * n, n3 = n2 * n, m3 = m * m * m, mnn = m * n2;
+  double* X = sm;
+  double* Y = X + 3 * n3;
+  double* Yd = Y + 3 * mnn;
+  const int64_t e = blockIdx.x;
+  if (e >= E) return;
+  const double* xe = xyz + e * 3 * n3;
+  for (int q = threadIdx.x; q < 3 * n3; q += blockDim.x) X[q] = xe[q] - xe[(q / n3) * n3];
+  __syncthreads();
+  // Y[c][kk][p][l] = sum_s Ig[kk][s] X[c][s][p][l], Yd likewise with DIg
+  for (int q = threadIdx.x; q < 3 * mnn; q += blockDim.x) {
+    const int c = q / mnn, r = q - c * mnn, kk = r / n2, pl = r - kk * n2;
+    const double* Xc = X + c * n3 + pl;
+    double a = 0.0, b = 0.0;
+    for (int s = 0; s < n; ++s) {
+      const double x = Xc[s * n2];
+      a += Ig[kk * n + s] * x;
+      b += DIg[kk * n + s] * x;
+    }
+    Y[q] = a;
+    Yd[q] = b;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < m3; q += blockDim.x) {
+    const int i = q % m, j = (q / m) % m, k = q / (m * m);
+    double J[3][3];
+    for (int c = 0; c < 3; ++c) {
+      const double* Yc = Y + c * mnn + k * n2;
+      const double* Ydc = Yd + c * mnn + k * n2;
+      double dr = 0.0, ds = 0.0, dt = 0.0;
+      for (int p = 0; p < n; ++p) {
+        double ar = 0.0, as = 0.0, at = 0.0;
+        for (int l = 0; l < n; ++l) {
+          const double y = Yc[p * n + l], yd = Ydc[p * n + l];
+          ar += DIg[i * n + l] * y;
+          as += Ig[i * n + l] * y;
+          at += Ig[i * n + l] * yd;
+        }
+        dr += Ig[j * n + p] * ar;
+        ds += DIg[j * n + p] * as;
+        dt += Ig[j * n + p] * at;
+      }
+      J[c][0] = dr;  // d x_c / d r
+      J[c][1] = ds;  // d x_c / d s
+      J[c][2] = dt;  // d x_c / d t
+    }
+    // cofactors C[a][b]; adj(J)[b][a] = C[a][b]
+    double C[3][3];
+    C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+    C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+    C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+    C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+    if (!(det > 0.0)) atomicExch(bad, 1);
+    const double w = rho[i] * rho[j] * rho[k];
+    double* Fe = F + e * 9 * m3 + q;
+    for (int b = 0; b < 3; ++b)
+      for (int a = 0; a < 3; ++a) Fe[(3 * b + a) * m3] = w * C[a][b];
+  }
+}
+
+// u_a = sum_b C_b^T (F[b][a] p) for a = 0, 1, 2 (local, unassembled).
+// Shared memory: the two 1D matrices [m][n], tb [m^3], T1 [m][m][n],
+// T2 [m][n][n], acc [n^3].  Each thread owns the acc entries q = tid + t blockDim.
+__global__ void k_pgrad(const double* __restrict__ p, const double* __restrict__ F, const double* __restrict__ Ig,
+                        const double* __restrict__ DIg, int n, int m, int64_t E, double* __restrict__ u,
+                        int64_t n_local) {
+  extern __shared__ double sm[];
+  const int n2 = n * n, n3 = n2 * n, m2 = m * m, m3 = m2 * m;
+  double* sI = sm;
+  double* sD = sI + m * n;
+  double* tb = sD + m * n;
+  double* T1 = tb + m3;
+  double* T2 = T1 + m2 * n;
+  double* acc = T2 + m * n2;
+  const int64_t e = blockIdx.x;
+  if (e >= E) return;
+  for (int q = threadIdx.x; q < m * n; q += blockDim.x) {
+    sI[q] = Ig[q];
+    sD[q] = DIg[q];
+  }
+  const double* pe = p + e * m3;
+  for (int a = 0; a < 3; ++a) {
+    for (int q = threadIdx.x; q < n3; q += blockDim.x) acc[q] = 0.0;
+    for (int b = 0; b < 3; ++b) {
+      const double* Mi = b == 0 ? sD : sI;
+      const double* Mj = b == 1 ? sD : sI;
+      const double* Mk = b == 2 ? sD : sI;
+      const double* Fba = F + (e * 9 + 3 * b + a) * m3;
+      for (int q = threadIdx.x; q < m3; q += blockDim.x) tb[q] = Fba[q] * pe[q];
+      __syncthreads();
+      // T1[k][j][l] = sum_i Mi[i][l] tb[k][j][i]
+      for (int q = threadIdx.x; q < m2 * n; q += blockDim.x) {
+        const int l = q % n, kj = q / n;
+        double s = 0.0;
+        for (int i = 0; i < m; ++i) s += Mi[i * n + l] * tb[kj * m + i];
+        T1[q] = s;
+      }
+      __syncthreads();
+      // T2[k][pp][l] = sum_j Mj[j][pp] T1[k][j][l]
+      for (int q = threadIdx.x; q < m * n2; q += blockDim.x) {
+        const int l = q % n, pp = (q / n) % n, k = q / n2;
+        double s = 0.0;
+        for (int j = 0; j < m; ++j) s += Mj[j * n + pp] * T1[(k * m + j) * n + l];
+        T2[q] = s;
+      }
+      __syncthreads();
+      // acc[s][pp][l] += sum_k Mk[k][s] T2[k][pp][l]
+      for (int q = threadIdx.x; q < n3; q += blockDim.x) {
+        const int pl = q % n2, s_ = q / n2;
+        double s = 0.0;
+        for (int k = 0; k < m; ++k) s += Mk[k * n + s_] * T2[k * n2 + pl];
+        acc[q] += s;
+      }
+    }
+    double* ua = u + a * n_local + e * n3;
+    for (int q = threadIdx.x; q < n3; q += blockDim.x) ua[q] = acc[q];
+  }
+}
+
+// out_q = sum_a sum_b F[b][a](q) (C_b v_a)(q), v_a = u_a / dB when dB is given
+// (the inverse assembled mass), u_a itself otherwise.  Shared memory: the two
+// 1D matrices, V [n^3], S1 [n][n][m], S2 [n][m][m], oacc [m^3].
+__global__ void k_pdiv(const double* __restrict__ u, const double* __restrict__ dB, const double* __restrict__ F,
+                       const double* __restrict__ Ig, const double* __restrict__ DIg, int n, int m, int64_t E,
+                       double* __restrict__ out, int64_t n_local) {
+  extern __shared__ double sm[];
+  const int n2 = n * n, n3 = n2 * n, m2 = m * m, m3 = m2 * m;
+  double* sI = sm;
+  double* sD = sI + m * n;
+  double* V = sD + m * n;
+  double* S1 = V + n3;
+  double* S2 = S1 + n2 * m;
+  double* oacc = S2 + n * m2;
+  const int64_t e = blockIdx.x;
+  if (e >= E) return;
+  for (int q = threadIdx.x; q < m * n; q += blockDim.x) {
+    sI[q] = Ig[q];
+    sD[q] = DIg[q];
+  }
+  for (int q = threadIdx.x; q < m3; q += blockDim.x) oacc[q] = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double* ua = u + a * n_local + e * n3;
+    for (int q = threadIdx.x; q < n3; q += blockDim.x) V[q] = dB ? ua[q] / dB[e * n3 + q] : ua[q];
+    __syncthreads();
+    for (int b = 0; b < 3; ++b) {
+      const double* Mi = b == 0 ? sD : sI;
+      const double* Mj = b == 1 ? sD : sI;
+      const double* Mk = b == 2 ? sD : sI;
+      // S1[s][pp][i] = sum_l Mi[i][l] V[s][pp][l]
+      for (int q = threadIdx.x; q < n2 * m; q += blockDim.x) {
+        const int i = q % m, spp = q / m;
+        double s = 0.0;
+        for (int l = 0; l < n; ++l) s += Mi[i * n + l] * V[spp * n + l];
+        S1[q] = s;
+      }
+      __syncthreads();
+      // S2[s][j][i] = sum_pp Mj[j][pp] S1[s][pp][i]
+      for (int q = threadIdx.x; q < n * m2; q += blockDim.x) {
+        const int i = q % m, j = (q / m) % m, s_ = q / m2;
+        double s = 0.0;
+        for (int pp = 0; pp < n; ++pp) s += Mj[j * n + pp] * S1[(s_ * n + pp) * m + i];
+        S2[q] = s;
+      }
+      __syncthreads();
+      // oacc[k][j][i] += F[b][a] sum_s Mk[k][s] S2[s][j][i]
+      const double* Fba = F + (e * 9 + 3 * b + a) * m3;
+      for (int q = threadIdx.x; q < m3; q += blockDim.x) {
+        const int ji = q % m2, k = q / m2;
+        double s = 0.0;
+        for (int s_ = 0; s_ < n; ++s_) s += Mk[k * n + s_] * S2[s_ * m2 + ji];
+        oacc[q] += Fba[q] * s;
+      }
+    }
+  }
+  double* oe = out + e * m3;
+  for (int q = threadIdx.x; q < m3; q += blockDim.x) oe[q] = oacc[q];
+}
+
+// ---- launchers ---------------------------------------------------------------
+
+static constexpr int kPressureThreads = 256;
+
+size_t gl_factors_smem(int n, int m) { return sizeof(double) * (3 * n * n * n + 6 * m * n * n); }
+static size_t pgrad_smem(int n, int m) {
+  return sizeof(double) * (2 * m * n + m * m * m + m * m * n + m * n * n + n * n * n);
+}
+static size_t pdiv_smem(int n, int m) {
+  return sizeof(double) * (2 * m * n + n * n * n + n * n * m + n * m * m + m * m * m);
+}
+
+cudaError_t launch_gl_factors(const double* xyz, const double* Ig, const double* DIg, const double* rho, int n, int m,
+                              int64_t E, double* F, int* bad, cudaStream_t s) {
+  const size_t smem = gl_factors_smem(n, m);
+  cudaError_t err = cudaFuncSetAttribute(k_gl_factors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_gl_factors<<<(unsigned)E, kPressureThreads, smem, s>>>(xyz, Ig, DIg, rho, n, m, E, F, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pgrad(const double* p, const double* F, const double* Ig, const double* DIg, int n, int m,
+                         int64_t E, double* u, int64_t n_local, cudaStream_t s) {
+  const size_t smem = pgrad_smem(n, m);
+  cudaError_t err = cudaFuncSetAttribute(k_pgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_pgrad<<<(unsigned)E, kPressureThreads, smem, s>>>(p, F, Ig, DIg, n, m, E, u, n_local);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pdiv(const double* u, const double* dB, const double* F, const double* Ig, const double* DIg, int n,
+                        int m, int64_t E, double* out, int64_t n_local, cudaStream_t s) {
+  const size_t smem = pdiv_smem(n, m);
+  cudaError_t err = cudaFuncSetAttribute(k_pdiv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_pdiv<<<(unsigned)E, kPressureThreads, smem, s>>>(u, dB, F, Ig, DIg, n, m, E, out, n_local);
+  return cudaGetLastError();
+}
+
+}  // namespace sem

@@ -1,0 +1,269 @@
+// C ABI of the staggered P_N - P_{N-2} pressure space: the weak divergence D,
+// the weak gradient D^T and the consistent Poisson operator E = D B^{-1} D^T
+// of Sec. 2, Eq. 5 (pressure on the Gauss-Legendre points of order N-2,
+// velocity on the GLL points of order N, Sec. 2).
+//
+// The GL-point data of a mesh (factors F = rho^3 adj(J) [E][9][m^3], and the
+// GLL basis values and derivatives at the GL points) are built on the first
+// pressure call on that mesh, on the caller's stream, which that call then
+// synchronises.
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "kernels.h"
+#include "sem_internal.h"
+
+namespace sem {
+namespace {
+
+// Legendre P_m(x) and P_{m-1}(x) by the three-term recurrence.
+void legendre2(int m, double x, double& pm, double& pm1) {
+  double p0 = 1.0, p1 = x;
+  if (m == 0) {
+    pm = 1.0;
+    pm1 = 0.0;
+    return;
+  }
+  for (int k = 1; k < m; ++k) {
+    const double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  pm = p1;
+  pm1 = p0;
+}
+
+// Gauss-Legendre nodes (roots of P_m, ascending) and weights
+// rho = 2 / ((1 - x^2) P_m'(x)^2), by Newton from x = cos(pi (i + 3/4) / (m + 1/2)),
+// with (1 - x^2) P_m' = m (P_{m-1} - x P_m).
+void gauss_legendre(int m, std::vector<double>& z, std::vector<double>& rho) {
+  z.assign(m, 0.0);
+  rho.assign(m, 0.0);
+  for (int i = 0; i < m; ++i) {
+    double x = std::cos(M_PI * (i + 0.75) / (m + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double pm, pm1;
+      legendre2(m, x, pm, pm1);
+      dp = m * (pm1 - x * pm) / (1.0 - x * x);
+      const double dx = pm / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    double pm, pm1;
+    legendre2(m, x, pm, pm1);
+    dp = m * (pm1 - x * pm) / (1.0 - x * x);
+    z[i] = x;
+    rho[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+  std::vector<int> ord(m);
+  for (int i = 0; i < m; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return z[a] < z[b]; });
+  std::vector<double> zs(m), rs(m);
+  for (int i = 0; i < m; ++i) {
+    zs[i] = z[ord[i]];
+    rs[i] = rho[ord[i]];
+  }
+  z.swap(zs);
+  rho.swap(rs);
+}
+
+// Ig[i][l] = l_l(z_i) by the barycentric formula on the GLL nodes xi (exactly
+// 1 / 0 where z_i is a GLL node), and DIg = Ig D: l_l' has degree N - 1, so it
+// equals its own GLL interpolant, l_l'(z) = sum_q l_q(z) D[q][l].
+void gl_matrices(int N, std::vector<double>& Ig, std::vector<double>& DIg, std::vector<double>& rho) {
+  const int n = N + 1, m = N - 1;
+  std::vector<double> xi, w, D, z;
+  gll(N, xi, w, D);
+  gauss_legendre(m, z, rho);
+  std::vector<double> lam(n, 1.0);
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k)
+      if (k != j) lam[j] /= (xi[j] - xi[k]);
+  Ig.assign(m * n, 0.0);
+  for (int i = 0; i < m; ++i) {
+    int hit = -1;
+    for (int l = 0; l < n; ++l)
+      if (z[i] == xi[l]) hit = l;
+    if (hit >= 0) {
+      Ig[i * n + hit] = 1.0;
+      continue;
+    }
+    double den = 0.0;
+    for (int l = 0; l < n; ++l) den += lam[l] / (z[i] - xi[l]);
+    for (int l = 0; l < n; ++l) Ig[i * n + l] = (lam[l] / (z[i] - xi[l])) / den;
+  }
+  DIg.assign(m * n, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int l = 0; l < n; ++l) {
+      double s = 0.0;
+      for (int q = 0; q < n; ++q) s += Ig[i * n + q] * D[q * n + l];
+      DIg[i * n + l] = s;
+    }
+}
+
+sem_status check_mesh(const sem_mesh* m, const char* who) {
+  if (!m) {
+    set_error(std::string(who) + ": null mesh");
+    return SEM_ERR_INVALID;
+  }
+  if (m->N < 2) {
+    set_error(std::string(who) + ": the P_N - P_{N-2} pressure space needs N >= 2");
+    return SEM_ERR_INVALID;
+  }
+  return SEM_OK;
+}
+
+// Build the mesh's GL-point data once (under its p_mutex).
+sem_status ensure_pressure(const sem_mesh* m, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(m->p_mutex);
+  if (m->Fgl) return SEM_OK;
+  SEM_CUDA(cudaSetDevice(m->device));
+  const int N = m->N, n = N + 1, mm = N - 1;
+  const int64_t m3 = (int64_t)mm * mm * mm;
+  std::vector<double> Ig, DIg, rho;
+  gl_matrices(N, Ig, DIg, rho);
+  double *F = nullptr, *I_d = nullptr, *DI_d = nullptr, *rho_d = nullptr;
+  int* bad_d = nullptr;
+  auto release = [&]() {
+    if (F) cudaFree(F);
+    if (I_d) cudaFree(I_d);
+    if (DI_d) cudaFree(DI_d);
+    if (rho_d) cudaFree(rho_d);
+    if (bad_d) cudaFree(bad_d);
+  };
+  auto fail = [&](cudaError_t e, const char* what) {
+    cudaStreamSynchronize(s);
+    release();
+    return cuda_fail(e, what);
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc((void**)&F, sizeof(double) * 9 * m3 * m->E)) != cudaSuccess) return fail(e, "cudaMalloc");
+  if ((e = cudaMalloc((void**)&I_d, sizeof(double) * mm * n)) != cudaSuccess) return fail(e, "cudaMalloc");
+  if ((e = cudaMalloc((void**)&DI_d, sizeof(double) * mm * n)) != cudaSuccess) return fail(e, "cudaMalloc");
+  if ((e = cudaMalloc((void**)&rho_d, sizeof(double) * mm)) != cudaSuccess) return fail(e, "cudaMalloc");
+  if ((e = cudaMalloc((void**)&bad_d, sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc");
+  if ((e = cudaMemcpyAsync(I_d, Ig.data(), sizeof(double) * mm * n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return fail(e, "cudaMemcpyAsync");
+  if ((e = cudaMemcpyAsync(DI_d, DIg.data(), sizeof(double) * mm * n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return fail(e, "cudaMemcpyAsync");
+  if ((e = cudaMemcpyAsync(rho_d, rho.data(), sizeof(double) * mm, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return fail(e, "cudaMemcpyAsync");
+  if ((e = cudaMemsetAsync(bad_d, 0, sizeof(int), s)) != cudaSuccess) return fail(e, "cudaMemsetAsync");
+  if ((e = launch_gl_factors(m->xyz, I_d, DI_d, rho_d, n, mm, m->E, F, bad_d, s)) != cudaSuccess)
+    return fail(e, "k_gl_factors");
+  count_launches(1);
+  int bad = 0;
+  if ((e = cudaMemcpyAsync(&bad, bad_d, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return fail(e, "cudaMemcpyAsync");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e, "cudaStreamSynchronize");
+  cudaFree(rho_d);
+  rho_d = nullptr;
+  cudaFree(bad_d);
+  bad_d = nullptr;
+  if (bad) {
+    release();
+    set_error("mesh has an element with det(J) <= 0 at a GL point");
+    return SEM_ERR_BAD_MESH;
+  }
+  sem_mesh* mut = const_cast<sem_mesh*>(m);
+  mut->dev_bytes += sizeof(double) * (9 * m3 * m->E + 2 * mm * n);
+  m->Igl = I_d;
+  m->DIgl = DI_d;
+  m->Fgl = F;
+  return SEM_OK;
+}
+
+}  // namespace
+}  // namespace sem
+
+using namespace sem;
+
+extern "C" {
+
+sem_status sem_pressure_info(const sem_mesh* m, int64_t* n_pressure) {
+  sem_status st = check_mesh(m, "sem_pressure_info");
+  if (st != SEM_OK) return st;
+  if (!n_pressure) {
+    set_error("sem_pressure_info: null argument");
+    return SEM_ERR_INVALID;
+  }
+  const int64_t mm = m->N - 1;
+  *n_pressure = m->E * mm * mm * mm;
+  return SEM_OK;
+}
+
+sem_status sem_pressure_factors(const sem_mesh* m, double* F_dev, void* stream) {
+  sem_status st = check_mesh(m, "sem_pressure_factors");
+  if (st != SEM_OK) return st;
+  if (!F_dev) {
+    set_error("sem_pressure_factors: null argument");
+    return SEM_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_pressure(m, s);
+  if (st != SEM_OK) return st;
+  const int64_t mm = m->N - 1;
+  SEM_CUDA(cudaMemcpyAsync(F_dev, m->Fgl, sizeof(double) * 9 * mm * mm * mm * m->E, cudaMemcpyDeviceToDevice, s));
+  return SEM_OK;
+}
+
+sem_status sem_pressure_grad(const sem_mesh* m, const double* p_dev, double* u_dev, void* stream) {
+  sem_status st = check_mesh(m, "sem_pressure_grad");
+  if (st != SEM_OK) return st;
+  if (!p_dev || !u_dev) {
+    set_error("sem_pressure_grad: null argument");
+    return SEM_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_pressure(m, s);
+  if (st != SEM_OK) return st;
+  SEM_CUDA(launch_pgrad(p_dev, m->Fgl, m->Igl, m->DIgl, m->n, m->N - 1, m->E, u_dev, m->n_local, s));
+  count_launches(1);
+  return SEM_OK;
+}
+
+sem_status sem_pressure_div(const sem_mesh* m, const double* u_dev, double* q_dev, void* stream) {
+  sem_status st = check_mesh(m, "sem_pressure_div");
+  if (st != SEM_OK) return st;
+  if (!u_dev || !q_dev) {
+    set_error("sem_pressure_div: null argument");
+    return SEM_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_pressure(m, s);
+  if (st != SEM_OK) return st;
+  SEM_CUDA(launch_pdiv(u_dev, nullptr, m->Fgl, m->Igl, m->DIgl, m->n, m->N - 1, m->E, q_dev, m->n_local, s));
+  count_launches(1);
+  return SEM_OK;
+}
+
+sem_status sem_pressure_apply(const sem_mesh* m, const double* p_dev, double* q_dev, double* work_dev, void* stream) {
+  sem_status st = check_mesh(m, "sem_pressure_apply");
+  if (st != SEM_OK) return st;
+  if (!p_dev || !q_dev || !work_dev) {
+    set_error("sem_pressure_apply: null argument");
+    return SEM_ERR_INVALID;
+  }
+  const int64_t mm = m->N - 1, np = m->E * mm * mm * mm;
+  const double* w0 = work_dev;
+  const double* w1 = work_dev + 3 * m->n_local;
+  auto overlaps = [&](const double* a) { return a + np > w0 && a < w1; };
+  if (overlaps(p_dev) || overlaps(q_dev)) {
+    set_error("sem_pressure_apply: work must not overlap p or q");
+    return SEM_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_pressure(m, s);
+  if (st != SEM_OK) return st;
+  const GsDev g = gs_dev(m);
+  SEM_CUDA(launch_pgrad(p_dev, m->Fgl, m->Igl, m->DIgl, m->n, m->N - 1, m->E, work_dev, m->n_local, s));
+  for (int a = 0; a < 3; ++a) SEM_CUDA(launch_gs<double>(work_dev + a * m->n_local, g, 1, nullptr, s));
+  SEM_CUDA(launch_pdiv(work_dev, m->dB, m->Fgl, m->Igl, m->DIgl, m->n, m->N - 1, m->E, q_dev, m->n_local, s));
+  count_launches(5);
+  return SEM_OK;
+}
+
+}  // extern "C"

@@ -143,6 +143,14 @@ struct sem_mesh {
   int fp64_df = 0;
   float ax_ms[3][4] = {{0}};
 
+  // P_N - P_{N-2} pressure operators (pressure_api.cpp), built on first use
+  // under p_mutex: GL-point factors F [E][9][m^3] (rho^3 adj(J)_{ba}, index
+  // 3 b + a) and the GLL basis values / derivatives at the GL points [m][n]
+  mutable std::mutex p_mutex;
+  mutable double* Fgl = nullptr;
+  mutable double* Igl = nullptr;
+  mutable double* DIgl = nullptr;
+
   std::mutex ws_mutex;
   sem::Workspace* ws = nullptr;  // cached solver workspace
   // workspaces of further right-hand sides on this mesh in one batch, kept

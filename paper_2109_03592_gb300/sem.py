@@ -111,6 +111,11 @@ SIGNATURES = {
     "sem_mesh_fp64_kernel": (C.c_int, [_P]),
     "sem_mesh_check": (C.c_int, [_P, _P]),
     "sem_mesh_ax_variant": (C.c_int, [_P, C.c_int]),
+    "sem_pressure_info": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+    "sem_pressure_factors": (C.c_int, [_P, _P, _P]),
+    "sem_pressure_grad": (C.c_int, [_P, _P, _P, _P]),
+    "sem_pressure_div": (C.c_int, [_P, _P, _P, _P]),
+    "sem_pressure_apply": (C.c_int, [_P, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -306,6 +311,52 @@ class Mesh:
         _check(lib().sem_jacobi(self._h, float(h1), float(h2), _dptr(out, torch.float64, self.n_local),
                                 _stream(stream)), "sem_jacobi")
         return out
+
+    # -- staggered P_N - P_{N-2} pressure space (Sec. 2, Eq. 5) -------------
+    @property
+    def pressure_shape(self):
+        """Shape of a pressure field: (E, m, m, m), m = N - 1."""
+        return (self.E,) + (self.N - 1,) * 3
+
+    def pressure_size(self):
+        v = C.c_int64()
+        _check(lib().sem_pressure_info(self._h, C.byref(v)), "sem_pressure_info")
+        return v.value
+
+    def pressure_factors(self, stream=None):
+        """GL-point factors F [E, 9, m, m, m] (entry 3 b + a = rho^3 adj(J)_{ba})."""
+        import torch
+        m = self.N - 1
+        F = torch.empty((self.E, 9, m, m, m), dtype=torch.float64, device="cuda")
+        _check(lib().sem_pressure_factors(self._h, _dptr(F), _stream(stream)), "sem_pressure_factors")
+        return F
+
+    def pressure_grad(self, p, u, stream=None):
+        """u = D^T p: p [E, m, m, m] -> u [3, E, n, n, n] (local, unassembled)."""
+        import torch
+        _check(lib().sem_pressure_grad(self._h, _dptr(p, torch.float64, self.pressure_size()),
+                                       _dptr(u, torch.float64, 3 * self.n_local), _stream(stream)),
+               "sem_pressure_grad")
+        return u
+
+    def pressure_div(self, u, q, stream=None):
+        """q = D u: u [3, E, n, n, n] -> q [E, m, m, m] (element by element)."""
+        import torch
+        _check(lib().sem_pressure_div(self._h, _dptr(u, torch.float64, 3 * self.n_local),
+                                      _dptr(q, torch.float64, self.pressure_size()), _stream(stream)),
+               "sem_pressure_div")
+        return q
+
+    def pressure_apply(self, p, q, work=None, stream=None):
+        """q = E p = D B^{-1} D^T p; work: 3 n_local doubles of scratch (allocated if None)."""
+        import torch
+        if work is None:
+            work = torch.empty(3 * self.n_local, dtype=torch.float64, device="cuda")
+        np_ = self.pressure_size()
+        _check(lib().sem_pressure_apply(self._h, _dptr(p, torch.float64, np_), _dptr(q, torch.float64, np_),
+                                        _dptr(work, torch.float64, 3 * self.n_local), _stream(stream)),
+               "sem_pressure_apply")
+        return q
 
     def solve(self, b, x, stream=None, check=False, **opts):
         """sem_pcg_solve on device tensors; returns the result record (a dict).
