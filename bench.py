@@ -381,6 +381,28 @@ def pressure_leg(m, stream, reps):
             "bound": "fp64 pipe (native FP64 contractions)"}
 
 
+def pressure_solve_leg(workload="pipe4096_n7", tol=1e-10):
+    """One solve of the pressure equation E p = g (Sec. 2, Eq. 5) on the
+    mean-free space (sem_pressure_solve, CG) on the E = 4096 pipe, the paper's
+    per-GPU regime, g a seeded standard-normal pressure field.  The first
+    operator call (which builds the GL-point factors) is made before timing."""
+    import torch
+    import paper_2109_03592_gb300 as sem
+    from sem_inputs import configs
+    m = sem.Mesh(configs.mesh_desc(workload))
+    g = torch.randn(m.pressure_shape, dtype=torch.float64, device="cuda",
+                    generator=torch.Generator(device="cuda").manual_seed(4))
+    x = torch.empty_like(g)
+    m.pressure_apply(g, x)
+    torch.cuda.synchronize()
+    r = m.pressure_solve(g, x, tol=tol)
+    out = {"workload": f"{workload}: E={m.E} N={m.N}, {m.pressure_size()} pressure values", "tol": tol,
+           "iters": r["iters"], "ms": r["ms"], "ms_per_iter": r["ms"] / max(1, r["iters"]),
+           "rel_res": r["rel_res"], "status": r["status"]}
+    m.close()
+    return out
+
+
 def desc_elements(d):
     return d["nx"] * d["ny"] * d["nz"] if d["kind"] == "box" else d["nc"] * (d["nc"] + 4 * d["nr"]) * d["nzp"]
 
@@ -520,6 +542,8 @@ def run_gpu(args):
     proj = None
     if not args.no_projection:
         proj = projection_leg()
+    if pressure is not None:
+        pressure["solve"] = pressure_solve_leg()
     velocity = None
     if not args.no_velocity:
         velocity = [velocity_helmholtz_leg(w) for w in ("pipe4096_n7", "pipe32768_n7")]

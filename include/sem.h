@@ -356,6 +356,26 @@ sem_status sem_pressure_div(const sem_mesh* mesh, const double* u_dev, double* q
 sem_status sem_pressure_apply(const sem_mesh* mesh, const double* p_dev, double* q_dev, double* work_dev,
                               void* stream);
 
+/* Pressure solve for Sec. 2, Eq. 5: E p = g on the mean-free pressure space.
+ * The constants are E's null space when the velocity is Dirichlet on the
+ * whole boundary (exactly on affine meshes; on curved elements GL quadrature
+ * leaves them a near-null mode), so the pressure is fixed up to a constant.
+ * Solved: Pm E Pm p = Pm g with Pm = I - 1 1^T / n_pressure, by plain
+ * (unpreconditioned) CG from p = 0 in the Euclidean inner product over the
+ * pressure values, stopped when ||r|| <= opts->tol ||Pm g|| for the recurrence
+ * residual and then for the true residual Pm (g - E p) (CG restarts from p,
+ * at most 5 times, when the recurrence drifted); tol <= 0 means 1e-10,
+ * maxit <= 0 means 20000, the other fields of opts are ignored.
+ * result->rel_res is the true residual once converged.
+ * g_dev, p_dev: [E][m^3] FP64; p_dev is output only (mean zero).  Every
+ * reduction is deterministic.  Synchronous: the host reads three sums per
+ * iteration.  Allocates 3 n_pressure + 3 n_local doubles of scratch for the
+ * call.  Returns the solve's status (also in result->status): SEM_OK,
+ * SEM_ERR_NOT_CONVERGED or SEM_ERR_BREAKDOWN (<p, E p> <= 0), with result
+ * filled in; result->outer_iters is 0 and result->ms the device time. */
+sem_status sem_pressure_solve(const sem_mesh* mesh, const double* g_dev, double* p_dev, const sem_solve_opts* opts,
+                              sem_solve_result* result, void* stream);
+
 /* ---- serving ------------------------------------------------------------ */
 
 typedef struct {

@@ -168,3 +168,54 @@ class Pressure:
             p[c] = 1.0
             A[:, c] = self.E(p.reshape(self.shape)).reshape(-1)
         return A
+
+
+def cg(P, g, tol=1e-10, maxit=20000, max_restarts=5):
+    """CG for the pressure equation E p = g (Sec. 2, Eq. 5) on the mean-free
+    subspace.  With Dirichlet velocity on the whole boundary the constants
+    are the null space of E (exactly so on affine meshes; on curved elements
+    GL quadrature leaves them a near-null mode), and the pressure is defined
+    up to a constant.  The reading taken here solves
+        Pm E Pm p = Pm g,   Pm = I - 1 1^T / n_p   (mean over the GL values),
+    plain (unpreconditioned) CG from p = 0 in the Euclidean inner product.
+    When the recurrence residual reaches tol ||Pm g||, the true residual
+    Pm (g - E p) is formed; the solve stops if it meets the tolerance too,
+    and otherwise CG restarts from p with that residual (at most
+    ``max_restarts`` times; the paper fixes no stopping rule, and this one
+    makes the returned residual the true one).  Returns (p, iterations,
+    ||Pm (g - E p)|| / ||Pm g|| -- the recurrence value if not converged --,
+    status) with status as in ``solver``."""
+    from .solver import BREAKDOWN, CONVERGED, NOT_CONVERGED
+    gm = g - g.mean()
+    gnorm = np.sqrt(np.sum(gm * gm))
+    x = np.zeros(P.shape)
+    if gnorm == 0.0:
+        return x, 0, 0.0, CONVERGED
+    r = gm.copy()
+    p = r.copy()
+    rho = np.sum(r * r)
+    restarts = 0
+    for k in range(1, maxit + 1):
+        w = P.E(p)
+        w = w - w.mean()
+        sigma = np.sum(p * w)
+        if not sigma > 0.0:
+            return x, k, np.sqrt(rho) / gnorm, BREAKDOWN
+        alpha = rho / sigma
+        x = x + alpha * p
+        r = r - alpha * w
+        rho_new = np.sum(r * r)
+        if np.sqrt(rho_new) <= tol * gnorm:
+            w = P.E(x)
+            r = gm - (w - w.mean())
+            rho = np.sum(r * r)
+            if np.sqrt(rho) <= tol * gnorm:
+                return x, k, np.sqrt(rho) / gnorm, CONVERGED
+            if restarts == max_restarts:
+                return x, k, np.sqrt(rho) / gnorm, NOT_CONVERGED
+            restarts += 1
+            p = r.copy()
+            continue
+        p = r + (rho_new / rho) * p
+        rho = rho_new
+    return x, maxit, np.sqrt(rho) / gnorm, NOT_CONVERGED

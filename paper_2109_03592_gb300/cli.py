@@ -4,6 +4,13 @@
     python -m paper_2109_03592_gb300.cli ax --workload pipe262144_n7 --prec fp64 [--reps 10]
     python -m paper_2109_03592_gb300.cli gs --workload pipe262144_n7 --prec fp32 [--reps 10]
     python -m paper_2109_03592_gb300.cli ax --workload pipe262144_n7 --prec fp32 --coef
+    python -m paper_2109_03592_gb300.cli pressure --workload pipe32768_n7 [--reps 10]
+    python -m paper_2109_03592_gb300.cli psolve --workload pipe4096_n7 [--tol 1e-10]
+
+pressure times the consistent Poisson operator E = D B^-1 D^T of the
+P_N - P_{N-2} pressure space (sem_pressure_apply); psolve solves E p = g on
+the mean-free pressure space (sem_pressure_solve) for a seeded
+standard-normal g.
 
 --coef gives the mesh seeded per-point coefficients h1(i,j,k,e), h2(i,j,k,e)
 (a variable viscosity and mass coefficient) before the timed calls, which then
@@ -41,10 +48,41 @@ def _set_coefficients(m):
     m.set_coefficients(h1, h2)
 
 
+def _pressure(args):
+    import torch
+    from sem_inputs import configs
+    from . import sem
+    m = sem.Mesh(configs.mesh_desc(args.workload))
+    g = torch.randn(m.pressure_shape, dtype=torch.float64, device="cuda",
+                    generator=torch.Generator(device="cuda").manual_seed(4))
+    q = torch.empty_like(g)
+    work = torch.empty(3 * m.n_local, dtype=torch.float64, device="cuda")
+    if args.what == "psolve":
+        m.pressure_apply(g, q, work)  # builds the GL-point factors
+        for _ in range(args.repeat):
+            r = m.pressure_solve(g, q, tol=args.tol)
+            print(json.dumps({"workload": args.workload, "pressure_values": m.pressure_size(), **r}), flush=True)
+    else:
+        for _ in range(3):
+            m.pressure_apply(g, q, work)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(args.reps):
+            m.pressure_apply(g, q, work)
+        e.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e) / args.reps
+        print(json.dumps({"workload": args.workload, "ms": ms, "pressure_values": m.pressure_size(),
+                          "gdofs": m.pressure_size() / ms / 1e6}), flush=True)
+    m.close()
+    return 0
+
+
 def main(argv=None):
     from . import sem
     ap = argparse.ArgumentParser(prog="python -m paper_2109_03592_gb300.cli")
-    ap.add_argument("what", choices=["solve", "ax", "gs"])
+    ap.add_argument("what", choices=["solve", "ax", "gs", "pressure", "psolve"])
     ap.add_argument("--workload", default="pipe32768_n7")
     ap.add_argument("--prec", default="mixed", choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--tol", type=float, default=1e-10)
@@ -55,6 +93,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     import torch
     prec = {"fp64": sem.FP64, "fp32": sem.FP32, "mixed": sem.MIXED}[args.prec]
+    if args.what in ("pressure", "psolve"):
+        return _pressure(args)
     m, b = _mesh_and_rhs(args.workload)
     h1, h2 = 1.0, 1.0 if args.helmholtz else 0.0
     if args.coef:

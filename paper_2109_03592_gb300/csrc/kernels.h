@@ -141,5 +141,18 @@ cudaError_t launch_pgrad(const double* p, const double* F, const double* Ig, con
                          int64_t E, double* u, int64_t n_local, cudaStream_t s);
 cudaError_t launch_pdiv(const double* u, const double* dB, const double* F, const double* Ig, const double* DIg, int n,
                         int m, int64_t E, double* out, int64_t n_local, cudaStream_t s);
+// Pressure-CG vector kernels; each reduction writes its (deterministic) sum to
+// out[0] on the device, using partial[pressure_red_blocks()] as scratch.
+int pressure_red_blocks();
+cudaError_t launch_pdot(const double* a, const double* b, int64_t n, double* partial, double* out, cudaStream_t s);
+cudaError_t launch_pshift_dot(double* w, const double* p, double c, int64_t n, double* partial, double* out,
+                              cudaStream_t s);
+cudaError_t launch_pupdate(double* x, double* r, const double* p, const double* w, double alpha, int64_t n,
+                           double* partial, double* out, cudaStream_t s);
+cudaError_t launch_pdir(double* y, const double* a, double beta, int64_t n, cudaStream_t s);
+cudaError_t launch_pstart(const double* g, double c, double* r, double* p, double* x, int64_t n, double* partial,
+                          double* out, cudaStream_t s);
+cudaError_t launch_presidual(const double* g, double cg, const double* w, double cw, double* r, double* q, int64_t n,
+                             double* partial, double* out, cudaStream_t s);
 
 }  // namespace sem

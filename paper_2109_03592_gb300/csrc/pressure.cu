@@ -207,9 +207,113 @@ __global__ void k_pdiv(const double* __restrict__ u, const double* __restrict__ 
   for (int q = threadIdx.x; q < m3; q += blockDim.x) oe[q] = oacc[q];
 }
 
+// ---- vector kernels of the pressure CG (pressure values, Euclidean products) ----
+// Reductions are deterministic: block b sums its grid-stride slice in a fixed
+// order and then a fixed shared-memory tree; k_psum_finish adds the block
+// partials in index order.
+
+static constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* s) {
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int h = kRedThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+    __syncthreads();
+  }
+  return s[0];
+}
+
+// partial[block] = sum a_i b_i over the block's slice (b null: sum a_i)
+__global__ void k_pdot(const double* __restrict__ a, const double* __restrict__ b, int64_t n, double* partial) {
+  __shared__ double s[kRedThreads];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads)
+    acc += b ? a[i] * b[i] : a[i];
+  const double t = block_sum(acc, s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// w_i -= c; partial sums of p_i w_i
+__global__ void k_pshift_dot(double* __restrict__ w, const double* __restrict__ p, double c, int64_t n,
+                             double* partial) {
+  __shared__ double s[kRedThreads];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
+    const double v = w[i] - c;
+    w[i] = v;
+    acc += p[i] * v;
+  }
+  const double t = block_sum(acc, s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// x += alpha p; r -= alpha w; partial sums of r_i r_i
+__global__ void k_pupdate(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                          const double* __restrict__ w, double alpha, int64_t n, double* partial) {
+  __shared__ double s[kRedThreads];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
+    x[i] += alpha * p[i];
+    const double v = r[i] - alpha * w[i];
+    r[i] = v;
+    acc += v * v;
+  }
+  const double t = block_sum(acc, s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// y = a + beta y (the CG direction p = r + beta p)
+__global__ void k_pdir(double* __restrict__ y, const double* __restrict__ a, double beta, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a[i] + beta * y[i];
+}
+
+// r = g - c, p = r, x = 0; partial sums of r_i r_i
+__global__ void k_pstart(const double* __restrict__ g, double c, double* __restrict__ r, double* __restrict__ p,
+                         double* __restrict__ x, int64_t n, double* partial) {
+  __shared__ double s[kRedThreads];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
+    const double v = g[i] - c;
+    r[i] = v;
+    p[i] = v;
+    x[i] = 0.0;
+    acc += v * v;
+  }
+  const double t = block_sum(acc, s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// r = (g - cg) - (w - cw), q = r; partial sums of r_i r_i (the true residual
+// Pm (g - E x) when w = E x and cg, cw are the means of g and w)
+__global__ void k_presidual(const double* __restrict__ g, double cg, const double* __restrict__ w, double cw,
+                            double* __restrict__ r, double* __restrict__ q, int64_t n, double* partial) {
+  __shared__ double s[kRedThreads];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
+    const double v = (g[i] - cg) - (w[i] - cw);
+    r[i] = v;
+    q[i] = v;
+    acc += v * v;
+  }
+  const double t = block_sum(acc, s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// out[0] = sum of partial[0..cnt) (one CTA)
+__global__ void k_psum_finish(const double* __restrict__ partial, int cnt, double* out) {
+  __shared__ double s[kRedThreads];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < cnt; i += kRedThreads) acc += partial[i];
+  const double t = block_sum(acc, s);
+  if (threadIdx.x == 0) out[0] = t;
+}
+
 // ---- launchers ---------------------------------------------------------------
 
 static constexpr int kPressureThreads = 256;
+static constexpr int kPressureRedBlocks = 2 * 152;  // reduction grid: two CTAs per SM
 
 size_t gl_factors_smem(int n, int m) { return sizeof(double) * (3 * n * n * n + 6 * m * n * n); }
 static size_t pgrad_smem(int n, int m) {
@@ -246,4 +350,46 @@ cudaError_t launch_pdiv(const double* u, const double* dB, const double* F, cons
   return cudaGetLastError();
 }
 
+int pressure_red_blocks() { return kPressureRedBlocks; }
+
+cudaError_t launch_pdot(const double* a, const double* b, int64_t n, double* partial, double* out, cudaStream_t s) {
+  k_pdot<<<kPressureRedBlocks, kRedThreads, 0, s>>>(a, b, n, partial);
+  k_psum_finish<<<1, kRedThreads, 0, s>>>(partial, kPressureRedBlocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pshift_dot(double* w, const double* p, double c, int64_t n, double* partial, double* out,
+                              cudaStream_t s) {
+  k_pshift_dot<<<kPressureRedBlocks, kRedThreads, 0, s>>>(w, p, c, n, partial);
+  k_psum_finish<<<1, kRedThreads, 0, s>>>(partial, kPressureRedBlocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pupdate(double* x, double* r, const double* p, const double* w, double alpha, int64_t n,
+                           double* partial, double* out, cudaStream_t s) {
+  k_pupdate<<<kPressureRedBlocks, kRedThreads, 0, s>>>(x, r, p, w, alpha, n, partial);
+  k_psum_finish<<<1, kRedThreads, 0, s>>>(partial, kPressureRedBlocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pdir(double* y, const double* a, double beta, int64_t n, cudaStream_t s) {
+  k_pdir<<<kPressureRedBlocks, kRedThreads, 0, s>>>(y, a, beta, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pstart(const double* g, double c, double* r, double* p, double* x, int64_t n, double* partial,
+                          double* out, cudaStream_t s) {
+  k_pstart<<<kPressureRedBlocks, kRedThreads, 0, s>>>(g, c, r, p, x, n, partial);
+  k_psum_finish<<<1, kRedThreads, 0, s>>>(partial, kPressureRedBlocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_presidual(const double* g, double cg, const double* w, double cw, double* r, double* q, int64_t n,
+                             double* partial, double* out, cudaStream_t s) {
+  k_presidual<<<kPressureRedBlocks, kRedThreads, 0, s>>>(g, cg, w, cw, r, q, n, partial);
+  k_psum_finish<<<1, kRedThreads, 0, s>>>(partial, kPressureRedBlocks, out);
+  return cudaGetLastError();
+}
+
 }  // namespace sem
+

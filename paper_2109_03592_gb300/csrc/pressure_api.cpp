@@ -104,6 +104,12 @@ void gl_matrices(int N, std::vector<double>& Ig, std::vector<double>& DIg, std::
     }
 }
 
+#define SEM_TRY_STATUS(expr)          \
+  do {                                \
+    sem_status _s = (expr);           \
+    if (_s != SEM_OK) return _s;      \
+  } while (0)
+
 sem_status check_mesh(const sem_mesh* m, const char* who) {
   if (!m) {
     set_error(std::string(who) + ": null mesh");
@@ -180,6 +186,8 @@ sem_status ensure_pressure(const sem_mesh* m, cudaStream_t s) {
 }  // namespace sem
 
 using namespace sem;
+
+constexpr int kPressureMaxRestarts = 5;
 
 extern "C" {
 
@@ -266,4 +274,137 @@ sem_status sem_pressure_apply(const sem_mesh* m, const double* p_dev, double* q_
   return SEM_OK;
 }
 
+// CG on the mean-free pressure space: Pm E Pm p = Pm g, Pm = I - 1 1^T / n_p.
+// When the recurrence residual meets the tolerance, the true residual
+// Pm (g - E p) is formed; CG restarts from p with it (at most
+// kPressureMaxRestarts times) unless it meets the tolerance as well.
+// Host-driven: each iteration applies E (five launches), then three
+// deterministic reductions whose sums the host reads back to form the mean of
+// E p, alpha and beta.
+sem_status sem_pressure_solve(const sem_mesh* m, const double* g_dev, double* p_dev, const sem_solve_opts* opts,
+                              sem_solve_result* result, void* stream) {
+  sem_status st = check_mesh(m, "sem_pressure_solve");
+  if (st != SEM_OK) return st;
+  if (!g_dev || !p_dev || !opts || !result || g_dev == p_dev) {
+    set_error("sem_pressure_solve: null or overlapping argument");
+    return SEM_ERR_INVALID;
+  }
+  const double tol = opts->tol > 0 ? opts->tol : 1e-10;
+  const int maxit = opts->maxit > 0 ? opts->maxit : 20000;
+  *result = sem_solve_result{0, 0, 0.0, 0.0, SEM_OK};
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_pressure(m, s);
+  if (st != SEM_OK) return st;
+  const int64_t mm = m->N - 1, np = m->E * mm * mm * mm;
+  const int nb = pressure_red_blocks();
+  // scratch: r, q (direction), w [np]; velocity work [3 n_local]; partials; one sum
+  double* buf = nullptr;
+  const size_t count = 3 * (size_t)np + 3 * (size_t)m->n_local + nb + 1;
+  SEM_CUDA(cudaMalloc((void**)&buf, count * sizeof(double)));
+  struct Free {
+    double* b;
+    ~Free() { cudaFree(b); }
+  } guard{buf};
+  double* r = buf;
+  double* q = r + np;
+  double* w = q + np;
+  double* work = w + np;
+  double* partial = work + 3 * m->n_local;
+  double* sum_d = partial + nb;
+  const GsDev g = gs_dev(m);
+  auto read = [&](double& v) -> sem_status {
+    SEM_CUDA(cudaMemcpyAsync(&v, sum_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    return SEM_OK;
+  };
+  cudaEvent_t e0, e1;
+  SEM_CUDA(cudaEventCreate(&e0));
+  SEM_CUDA(cudaEventCreate(&e1));
+  struct Ev {
+    cudaEvent_t a, b;
+    ~Ev() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } evguard{e0, e1};
+  SEM_CUDA(cudaEventRecord(e0, s));
+  uint64_t launches = 0;
+  // mean of g, then r = q = g - mean, x = 0, rho = <r, r>
+  double gsum = 0.0, rho = 0.0;
+  SEM_CUDA(launch_pdot(g_dev, nullptr, np, partial, sum_d, s));
+  launches += 2;
+  SEM_TRY_STATUS(read(gsum));
+  SEM_CUDA(launch_pstart(g_dev, gsum / (double)np, r, q, p_dev, np, partial, sum_d, s));
+  launches += 2;
+  SEM_TRY_STATUS(read(rho));
+  const double gnorm = std::sqrt(rho);
+  // out = E v (weak gradient, QQ^T with mask on each component, inverse mass, weak divergence)
+  auto apply_E = [&](const double* v, double* out) -> sem_status {
+    SEM_CUDA(launch_pgrad(v, m->Fgl, m->Igl, m->DIgl, m->n, (int)mm, m->E, work, m->n_local, s));
+    for (int a = 0; a < 3; ++a) SEM_CUDA(launch_gs<double>(work + a * m->n_local, g, 1, nullptr, s));
+    SEM_CUDA(launch_pdiv(work, m->dB, m->Fgl, m->Igl, m->DIgl, m->n, (int)mm, m->E, out, m->n_local, s));
+    launches += 5;
+    return SEM_OK;
+  };
+  int it = 0, restarts = 0;
+  int status = SEM_OK;
+  double rel = 0.0;
+  if (gnorm > 0.0) {
+    status = SEM_ERR_NOT_CONVERGED;
+    rel = 1.0;
+    for (it = 1; it <= maxit; ++it) {
+      // w = E q, then w -= mean(w) and sigma = <q, w>
+      SEM_TRY_STATUS(apply_E(q, w));
+      double wsum = 0.0, sigma = 0.0, rho_new = 0.0;
+      SEM_CUDA(launch_pdot(w, nullptr, np, partial, sum_d, s));
+      SEM_TRY_STATUS(read(wsum));
+      SEM_CUDA(launch_pshift_dot(w, q, wsum / (double)np, np, partial, sum_d, s));
+      SEM_TRY_STATUS(read(sigma));
+      launches += 4;
+      if (!(sigma > 0.0)) {
+        status = SEM_ERR_BREAKDOWN;
+        break;
+      }
+      const double alpha = rho / sigma;
+      SEM_CUDA(launch_pupdate(p_dev, r, q, w, alpha, np, partial, sum_d, s));
+      launches += 2;
+      SEM_TRY_STATUS(read(rho_new));
+      rel = std::sqrt(rho_new) / gnorm;
+      if (std::sqrt(rho_new) <= tol * gnorm) {
+        // the true residual Pm (g - E x); restart from x if the recurrence drifted
+        SEM_TRY_STATUS(apply_E(p_dev, w));
+        double xs = 0.0;
+        SEM_CUDA(launch_pdot(w, nullptr, np, partial, sum_d, s));
+        SEM_TRY_STATUS(read(xs));
+        SEM_CUDA(launch_presidual(g_dev, gsum / (double)np, w, xs / (double)np, r, q, np, partial, sum_d, s));
+        launches += 4;
+        SEM_TRY_STATUS(read(rho));
+        rel = std::sqrt(rho) / gnorm;
+        if (std::sqrt(rho) <= tol * gnorm) {
+          status = SEM_OK;
+          break;
+        }
+        if (restarts == kPressureMaxRestarts) break;
+        ++restarts;
+        continue;  // q = r: a steepest-descent restart
+      }
+      SEM_CUDA(launch_pdir(q, r, rho_new / rho, np, s));
+      launches += 1;
+      rho = rho_new;
+    }
+    if (it > maxit) it = maxit;
+  }
+  SEM_CUDA(cudaEventRecord(e1, s));
+  SEM_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  SEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  count_launches(launches);
+  result->iters = it;
+  result->rel_res = rel;
+  result->ms = ms;
+  result->status = status;
+  return (sem_status)status;
+}
+
 }  // extern "C"
+

@@ -116,6 +116,7 @@ SIGNATURES = {
     "sem_pressure_grad": (C.c_int, [_P, _P, _P, _P]),
     "sem_pressure_div": (C.c_int, [_P, _P, _P, _P]),
     "sem_pressure_apply": (C.c_int, [_P, _P, _P, _P, _P]),
+    "sem_pressure_solve": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
 }
 
 _lib = None
@@ -357,6 +358,20 @@ class Mesh:
                                         _dptr(work, torch.float64, 3 * self.n_local), _stream(stream)),
                "sem_pressure_apply")
         return q
+
+    def pressure_solve(self, g, p, tol=1e-10, maxit=0, stream=None, check=False):
+        """sem_pressure_solve: E p = g on the mean-free pressure space (CG);
+        returns the result record (a dict), raising on errors other than
+        not-converged / breakdown unless check=True."""
+        import torch
+        o = _opts(tol=tol, maxit=maxit)
+        r = SolveResult()
+        np_ = self.pressure_size()
+        st = lib().sem_pressure_solve(self._h, _dptr(g, torch.float64, np_), _dptr(p, torch.float64, np_),
+                                      C.byref(o), C.byref(r), _stream(stream))
+        if st not in (SEM_OK, SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN) or (check and st != SEM_OK):
+            _check(st, "sem_pressure_solve")
+        return r.as_dict()
 
     def solve(self, b, x, stream=None, check=False, **opts):
         """sem_pcg_solve on device tensors; returns the result record (a dict).

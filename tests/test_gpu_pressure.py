@@ -163,3 +163,76 @@ def test_full_size_pipe_sampled_elements_and_symmetry():
     assert abs(a - b) <= 1e-13 * scale
     assert torch.dot(p.view(-1), Ep.view(-1)).item() > 0
     m.close()
+
+
+SOLVE_CASES = {
+    "box_n4": CASES["box_n4"],                                    # exact constant null space
+    "pipe_n3": dict(kind="pipe", nc=2, nr=1, nzp=3, N=3, L=1.5),  # curved: near-null constant mode
+    "pipe_n4": dict(kind="pipe", nc=1, nr=1, nzp=3, N=4, L=1.5),
+}
+
+
+@pytest.mark.parametrize("name", list(SOLVE_CASES))
+def test_pressure_solve_matches_oracle(name):
+    """CG on the mean-free space: iteration count within 2 of the oracle's, the
+    GPU solution's residual Pm (g - E x) recomputed with the oracle's E within
+    the tolerance, mean zero, and close to the oracle's solution."""
+    import torch
+    import paper_2109_03592_gb300 as sem
+    desc = SOLVE_CASES[name]
+    m = sem.Mesh(desc)
+    P = pressure.Pressure(solver.Problem(_oracle_mesh(desc)))
+    g = np.random.default_rng(12).standard_normal(P.shape)
+    x = torch.full(P.shape, float("nan"), dtype=torch.float64, device="cuda")
+    r = m.pressure_solve(to_gpu(g), x, tol=1e-10)
+    assert r["status"] == 0, r
+    xo, it, rel, st = pressure.cg(P, g, tol=1e-10)
+    assert st == solver.CONVERGED
+    assert abs(r["iters"] - it) <= 2, (r["iters"], it)
+    assert r["rel_res"] <= 1e-10
+    xg = x.cpu().numpy()
+    gm = g - g.mean()
+    res = g - P.E(xg)
+    res = res - res.mean()
+    assert np.linalg.norm(res) <= 1.5e-10 * np.linalg.norm(gm)
+    assert abs(xg.sum()) <= 1e-10 * np.abs(xg).sum()
+    assert relerr(xg, xo) <= 1e-6
+    m.close()
+
+
+def test_pressure_solve_degenerate_right_hand_sides_and_iteration_cap():
+    import torch
+    import paper_2109_03592_gb300 as sem
+    m, P = setup("box_n4")
+    for val in (0.0, 3.0):  # zero and constant g: Pm g = 0
+        x = torch.full(P.shape, float("nan"), dtype=torch.float64, device="cuda")
+        r = m.pressure_solve(torch.full(P.shape, val, dtype=torch.float64, device="cuda"), x)
+        assert r["status"] == 0 and r["iters"] == 0 and x.abs().max().item() == 0.0
+    g = to_gpu(np.random.default_rng(13).standard_normal(P.shape))
+    x = torch.empty_like(g)
+    r = m.pressure_solve(g, x, maxit=3)
+    assert r["status"] == sem.SEM_ERR_NOT_CONVERGED and r["iters"] == 3
+    with pytest.raises(sem.SemError) as ei:
+        m.pressure_solve(g, g)
+    assert ei.value.status == sem.SEM_ERR_INVALID
+
+
+def test_pressure_solve_on_the_4096_element_pipe():
+    """The paper's per-GPU regime (E = 4096, N = 7): the true residual,
+    recomputed with the parity-tested operator, meets the tolerance."""
+    import torch
+    import paper_2109_03592_gb300 as sem
+    m = sem.Mesh(configs.mesh_desc("pipe4096_n7"))
+    g = torch.randn(m.pressure_shape, dtype=torch.float64, device="cuda",
+                    generator=torch.Generator(device="cuda").manual_seed(4))
+    x = torch.empty_like(g)
+    r = m.pressure_solve(g, x, tol=1e-10)
+    assert r["status"] == 0, r
+    Ex = torch.empty_like(g)
+    m.pressure_apply(x, Ex)
+    res = g - Ex
+    res -= res.mean()
+    gm = g - g.mean()
+    assert (res.norm() / gm.norm()).item() <= 2e-10
+    assert abs(x.sum().item()) <= 1e-10 * x.abs().sum().item()
+    m.close()

@@ -159,3 +159,33 @@ def test_operator_symmetry_on_curved_pipe():
     a, b = np.sum(q * P.E(p)), np.sum(p * P.E(q))
     assert abs(a - b) < 1e-13 * abs(a) * 10
     assert np.sum(p * P.E(p)) > 0
+
+
+@pytest.mark.parametrize("maker", [lambda: mesh.box(2, 2, 2, 4), lambda: mesh.pipe(2, 1, 3, 3, L=1.5)])
+def test_pressure_cg_matches_dense_solve_on_the_mean_free_space(maker):
+    """CG on Pm E Pm against the dense minimum-norm solution (eigendecomposition
+    of the projected matrix, its one zero mode dropped)."""
+    P = pressure.Pressure(solver.Problem(maker()))
+    g = vectors.local_field(21, P.shape[0], P.shape[1])
+    x, it, rel, st = pressure.cg(P, g, tol=1e-12)
+    assert st == solver.CONVERGED and rel <= 1e-12
+    A = P.dense()
+    n = A.shape[0]
+    Pm = np.eye(n) - np.ones((n, n)) / n
+    S = Pm @ A @ Pm
+    ev, V = np.linalg.eigh(0.5 * (S + S.T))
+    assert abs(ev[0]) < 1e-12 * ev[-1] and ev[1] > 1e-6 * ev[-1]  # one zero mode: the constant
+    gv = Pm @ g.reshape(-1)
+    xd = V[:, 1:] @ ((V[:, 1:].T @ gv) / ev[1:])
+    assert np.linalg.norm(x.reshape(-1) - xd) <= 1e-9 * np.linalg.norm(xd)
+    assert abs(x.sum()) <= 1e-10 * np.abs(x).sum()
+    # Pm (g - E x) = 0: the residual of the unprojected equation is a constant
+    res = g - P.E(x)
+    assert np.abs(res - res.mean()).max() <= 1e-9 * np.abs(g).max()
+
+
+def test_pressure_cg_zero_rhs_and_constant_rhs():
+    P = pressure.Pressure(solver.Problem(mesh.box(2, 1, 1, 3)))
+    for g in (np.zeros(P.shape), np.full(P.shape, 2.5)):
+        x, it, rel, st = pressure.cg(P, g)
+        assert st == solver.CONVERGED and it == 0 and not x.any()
