@@ -336,6 +336,12 @@ sem_status sem_proj_reset(sem_proj* proj);
  * overlapping buffers), SEM_ERR_OOM, SEM_ERR_BAD_MESH (det J <= 0 at a GL
  * point), SEM_ERR_CUDA. */
 
+/* Host only (no device use): the 1D data of the pressure space for order N
+ * (2..11), m = N - 1: GL nodes zeta [m] (roots of P_m, ascending) and weights
+ * rho [m]; Ig [m][n] = l_l(zeta_i) and DIg [m][n] = l_l'(zeta_i) for the GLL
+ * Lagrange basis l_l of order N (n = N + 1).  Any output may be NULL. */
+sem_status sem_pressure_basis(int N, double* zeta_host, double* rho_host, double* Ig_host, double* DIg_host);
+
 /* Number of pressure values of the mesh: E (N-1)^3. */
 sem_status sem_pressure_info(const sem_mesh* mesh, int64_t* n_pressure);
 

@@ -191,6 +191,21 @@ constexpr int kPressureMaxRestarts = 5;
 
 extern "C" {
 
+sem_status sem_pressure_basis(int N, double* zeta_host, double* rho_host, double* Ig_host, double* DIg_host) {
+  if (N < 2 || N > kMaxN) {
+    set_error("sem_pressure_basis: N must be in [2, 11]");
+    return SEM_ERR_INVALID;
+  }
+  std::vector<double> Ig, DIg, rho, z, r2;
+  gl_matrices(N, Ig, DIg, rho);
+  gauss_legendre(N - 1, z, r2);
+  if (zeta_host) std::copy(z.begin(), z.end(), zeta_host);
+  if (rho_host) std::copy(rho.begin(), rho.end(), rho_host);
+  if (Ig_host) std::copy(Ig.begin(), Ig.end(), Ig_host);
+  if (DIg_host) std::copy(DIg.begin(), DIg.end(), DIg_host);
+  return SEM_OK;
+}
+
 sem_status sem_pressure_info(const sem_mesh* m, int64_t* n_pressure) {
   sem_status st = check_mesh(m, "sem_pressure_info");
   if (st != SEM_OK) return st;

@@ -111,6 +111,7 @@ SIGNATURES = {
     "sem_mesh_fp64_kernel": (C.c_int, [_P]),
     "sem_mesh_check": (C.c_int, [_P, _P]),
     "sem_mesh_ax_variant": (C.c_int, [_P, C.c_int]),
+    "sem_pressure_basis": (C.c_int, [C.c_int, _P, _P, _P, _P]),
     "sem_pressure_info": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "sem_pressure_factors": (C.c_int, [_P, _P, _P]),
     "sem_pressure_grad": (C.c_int, [_P, _P, _P, _P]),
@@ -563,3 +564,17 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def pressure_basis(N):
+    """sem_pressure_basis (host only): (zeta [m], rho [m], Ig [m, n], DIg [m, n])
+    of the P_N - P_{N-2} pressure space, m = N - 1, n = N + 1."""
+    m, n = N - 1, N + 1
+    if m < 1:
+        _check(lib().sem_pressure_basis(int(N), None, None, None, None), "sem_pressure_basis")
+    z, r = np.empty(m), np.empty(m)
+    Ig, DIg = np.empty((m, n)), np.empty((m, n))
+    _check(lib().sem_pressure_basis(int(N), z.ctypes.data, r.ctypes.data, Ig.ctypes.data, DIg.ctypes.data),
+           "sem_pressure_basis")
+    return z, r, Ig, DIg
+
