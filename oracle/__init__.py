@@ -24,10 +24,12 @@ The oracle restates, slowly and directly, what the method of Vincent et al.,
 * The staggered P_N - P_{N-2} pressure space (GL points), the weak divergence
   and gradient, and the consistent Poisson operator E = D B^{-1} D^T of
   Sec. 2, Eq. 5 -- ``pressure``.
+* The overlapping Schwarz preconditioner with a coarse grid of Sec. 2,
+  Eq. 6 (fast-diagonalisation local solves) -- ``schwarz``.
 
 Each function cites the passage it follows.  No code here is shared with the
 CUDA path; the two meet only through ``sem_inputs`` (seeded random draws and
 mesh descriptors, which contain none of the method's arithmetic).
 """
 
-from . import gll, mesh, geometry, operator, numbering, solver, pressure  # noqa: F401
+from . import gll, mesh, geometry, operator, numbering, solver, pressure, schwarz  # noqa: F401
