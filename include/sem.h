@@ -382,6 +382,41 @@ sem_status sem_pressure_apply(const sem_mesh* mesh, const double* p_dev, double*
 sem_status sem_pressure_solve(const sem_mesh* mesh, const double* g_dev, double* p_dev, const sem_solve_opts* opts,
                               sem_solve_result* result, void* stream);
 
+/* ---- overlapping Schwarz preconditioner: host set-up ---------------------- */
+
+/* Sec. 2, Eq. 6 preconditions with local solves on overlapping subdomains.
+ * Here a subdomain is one element with all its GLL nodes (the overlap is the
+ * nodes shared with neighbours), and its local problem is replaced by the
+ * separable fast-diagonalisation form built from 1D operators per reference
+ * direction: with the element's mean length l along it, K = (2/l) D^T W D and
+ * B = (l/2) W on the n GLL points; at an end shared with a neighbour of mean
+ * length l' normal to the shared face, K[end][end] += (2/l') (D^T W D)[N][N]
+ * and B[end][end] += (l'/2) w_N; an end on a Dirichlet face is decoupled (its
+ * off-diagonal entries of K removed).  These calls solve K S = B S diag(lam)
+ * with S^T B S = I (lam ascending); the local inverse is then
+ * (S_t (x) S_s (x) S_r) (h1 (lam_t + lam_s + lam_r) + h2)^{-1} (S_t (x) S_s (x) S_r)^T.
+ * Host only: no device use.  The device apply of this preconditioner is not
+ * part of the library. */
+
+/* One 1D problem.  l_lo, l_hi <= 0: no neighbour at that end; dir_lo, dir_hi:
+ * that end is on a Dirichlet face.  S_host [n][n] row-major (column c is the
+ * c-th eigenvector), lam_host [n].  SEM_ERR_INVALID for N outside [1, 11] or
+ * l <= 0. */
+sem_status sem_schwarz_fdm_1d(int N, double l, double l_lo, double l_hi, int dir_lo, int dir_hi, double* S_host,
+                              double* lam_host);
+
+/* Every element of a mesh given on the host: glo [E][n^3] global ids (as
+ * sem_mesh_global_ids), xyz [E][3][n^3] GLL coordinates, dirichlet_face [E][6]
+ * (faces 0: i = 0, 1: i = N, 2: j = 0, 3: j = N, 4: k = 0, 5: k = N).  Mean
+ * lengths are the mean over the n^2 GLL lines of the distance between their
+ * ends; two element faces are neighbours when their centre nodes share a
+ * global id (so N >= 2).  Outputs S_host [E][3][n][n] and lam_host [E][3][n]
+ * (direction r, s, t); each distinct 1D problem is solved once, and
+ * *n_distinct (nullable) receives their number. */
+sem_status sem_schwarz_setup_host(int64_t E, int N, const int64_t* glo, const double* xyz,
+                                  const uint8_t* dirichlet_face, double* S_host, double* lam_host,
+                                  int64_t* n_distinct);
+
 /* ---- serving ------------------------------------------------------------ */
 
 typedef struct {

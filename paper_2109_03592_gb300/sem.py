@@ -112,6 +112,8 @@ SIGNATURES = {
     "sem_mesh_check": (C.c_int, [_P, _P]),
     "sem_mesh_ax_variant": (C.c_int, [_P, C.c_int]),
     "sem_pressure_basis": (C.c_int, [C.c_int, _P, _P, _P, _P]),
+    "sem_schwarz_fdm_1d": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, _P, _P]),
+    "sem_schwarz_setup_host": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, C.POINTER(C.c_int64)]),
     "sem_pressure_info": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "sem_pressure_factors": (C.c_int, [_P, _P, _P]),
     "sem_pressure_grad": (C.c_int, [_P, _P, _P, _P]),
@@ -577,4 +579,27 @@ def pressure_basis(N):
     _check(lib().sem_pressure_basis(int(N), z.ctypes.data, r.ctypes.data, Ig.ctypes.data, DIg.ctypes.data),
            "sem_pressure_basis")
     return z, r, Ig, DIg
+
+
+def schwarz_fdm_1d(N, l, l_lo=None, l_hi=None, dir_lo=False, dir_hi=False):
+    """sem_schwarz_fdm_1d (host only): (S [n, n], lam [n]) of one 1D problem."""
+    n = N + 1
+    S, lam = np.empty((n, n)), np.empty(n)
+    _check(lib().sem_schwarz_fdm_1d(int(N), float(l), float(l_lo or 0.0), float(l_hi or 0.0), int(bool(dir_lo)),
+                                    int(bool(dir_hi)), S.ctypes.data, lam.ctypes.data), "sem_schwarz_fdm_1d")
+    return S, lam
+
+
+def schwarz_setup_host(N, glo, xyz, dirichlet_face):
+    """sem_schwarz_setup_host: (S [E, 3, n, n], lam [E, 3, n], distinct count)
+    from host arrays glo [E*n^3] int64, xyz [E, 3, n, n, n], dirichlet_face [E, 6]."""
+    glo = np.ascontiguousarray(glo, dtype=np.int64)
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    df = np.ascontiguousarray(dirichlet_face, dtype=np.uint8)
+    E, n = xyz.shape[0], N + 1
+    S, lam = np.empty((E, 3, n, n)), np.empty((E, 3, n))
+    k = C.c_int64()
+    _check(lib().sem_schwarz_setup_host(int(E), int(N), glo.ctypes.data, xyz.ctypes.data, df.ctypes.data,
+                                        S.ctypes.data, lam.ctypes.data, C.byref(k)), "sem_schwarz_setup_host")
+    return S, lam, k.value
 
