@@ -264,7 +264,12 @@ sem_status sem_pcg_solve_batch(const sem_mesh* const* meshes, const double* cons
  * overlaps on the GPU (different streams or threads) race and must not be
  * issued.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Runs on `stream` and returns when x is written; result->ms is 0. */
+ * Same solve rule as sem_pcg_solve with SEM_FP64: CG on the tuned operator,
+ * then the true residual ||b - A x|| / ||b|| with the native FP64 operator,
+ * and restarts from x (at most 3, within maxit) while it misses opts->tol;
+ * result->rel_res is that true residual and result->outer_iters the number
+ * of restarts.  Runs on `stream` (on the mesh's device, which it makes
+ * current) and returns when x is written; result->ms is 0. */
 sem_status sem_pcg_solve_noalloc(const sem_mesh* mesh, const double* b_dev, double* x_dev,
                                  const sem_solve_opts* opts, sem_solve_result* result, void* stream);
 

@@ -232,13 +232,11 @@ template <int N, int EPB, bool FUSED>
 cudaError_t launch_df_t(const AxDFParams& p, cudaStream_t s, int* grid_out) {
   constexpr int n = N + 1;
   const size_t smem = sizeof(float2) * ((size_t)n * (n + 1) + 3ull * EPB * n * n * (n + 1));
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t err =
-        cudaFuncSetAttribute(k_ax_df<N, EPB, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    attr_set = true;
-  }
+  static DeviceOnce once;
+  cudaError_t aerr = once.get([&](int, int*) {
+    return cudaFuncSetAttribute(k_ax_df<N, EPB, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (aerr != cudaSuccess) return aerr;
   const int64_t grid = (p.E + EPB - 1) / EPB;
   if (grid_out) *grid_out = (int)grid;
   if (p.E == 0) return cudaSuccess;

@@ -400,13 +400,11 @@ template <int N, int EPB, bool FUSED>
 cudaError_t launch_eo_t(const AxDFParams& p, cudaStream_t s, int* grid_out) {
   constexpr int n = N + 1, h = n / 2;
   const size_t smem = sizeof(float4) * 2 * h * h + sizeof(float2) * 3ull * EPB * EoLayout<n>::size;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t err =
-        cudaFuncSetAttribute(k_ax_eo<N, EPB, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    attr_set = true;
-  }
+  static DeviceOnce once;
+  cudaError_t aerr = once.get([&](int, int*) {
+    return cudaFuncSetAttribute(k_ax_eo<N, EPB, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (aerr != cudaSuccess) return aerr;
   if (!p.eo64 || !p.eodf) return cudaErrorInvalidValue;
   const int64_t grid = (p.E + EPB - 1) / EPB;
   if (grid_out) *grid_out = (int)grid;

@@ -133,13 +133,11 @@ template <int N, typename T, int EPB, bool FUSED>
 cudaError_t launch_ax_t(const AxParams<T>& p, cudaStream_t s, int* grid_out) {
   constexpr int n = N + 1;
   const size_t smem = ax_smem_bytes<N, T, EPB>();
-  static bool attr_set = false;  // set once per instantiation (idempotent, racing threads write the same value)
-  if (!attr_set) {
-    cudaError_t err =
-        cudaFuncSetAttribute(k_ax<N, T, EPB, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    attr_set = true;
-  }
+  static DeviceOnce once;
+  cudaError_t aerr = once.get([&](int, int*) {
+    return cudaFuncSetAttribute(k_ax<N, T, EPB, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (aerr != cudaSuccess) return aerr;
   const int64_t grid = (p.E + EPB - 1) / EPB;
   if (grid_out) *grid_out = (int)grid;
   if (p.E == 0) return cudaSuccess;

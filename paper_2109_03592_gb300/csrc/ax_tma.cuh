@@ -220,19 +220,25 @@ template <int N, int EPB, int STAGES, bool FUSED>
 cudaError_t launch_ax_tma_t(const AxParams<float>& p, int* err, cudaStream_t s, int* grid_out) {
   constexpr int n = N + 1;
   const size_t smem = tma_smem_bytes<N, EPB, STAGES, FUSED>();
-  static int grid_cap = 0;  // CTAs per device, computed once per instantiation
-  if (!grid_cap) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_ax_tma<N, EPB, STAGES, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0, dev = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax_tma<N, EPB, STAGES, FUSED>, EPB * n * n, smem);
-    if (e != cudaSuccess) return e;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    grid_cap = per_sm * sms;
-  }
+  static DeviceOnce once;  // CTAs per device, computed once per device
+  int grid_cap = 0;
+  cudaError_t oerr = once.get(
+      [&](int dev, int* cap) {
+        cudaError_t e = cudaFuncSetAttribute(k_ax_tma<N, EPB, STAGES, FUSED>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax_tma<N, EPB, STAGES, FUSED>, EPB * n * n,
+                                                          smem);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        *cap = per_sm * sms;
+        return cudaSuccess;
+      },
+      &grid_cap);
+  if (oerr != cudaSuccess) return oerr;
   const int64_t ntiles = (p.E + EPB - 1) / EPB;
   const int grid = (int)std::min<int64_t>(ntiles, grid_cap);
   if (grid_out) *grid_out = grid;

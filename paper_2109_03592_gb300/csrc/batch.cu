@@ -397,18 +397,24 @@ cudaError_t launch_bax(const Table* T, double* part, int* err, int variant, cuda
   constexpr int EPB = epb_for(N, 1), STAGES = 3;
   (void)variant;
   const size_t smem = tma::tma_smem_bytes<N, EPB, STAGES, true>();
-  static int cap = 0;
-  if (!cap) {
-    cudaError_t e = cudaFuncSetAttribute(k_bax<N, EPB, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0, dev = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bax<N, EPB, STAGES>, EPB * n * n, smem);
-    if (e != cudaSuccess) return e;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    cap = per_sm * sms;
-  }
+  static DeviceOnce once;  // CTAs per device, computed once per device
+  int cap = 0;
+  cudaError_t oerr = once.get(
+      [&](int dev, int* c) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_bax<N, EPB, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bax<N, EPB, STAGES>, EPB * n * n, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        *c = per_sm * sms;
+        return cudaSuccess;
+      },
+      &cap);
+  if (oerr != cudaSuccess) return oerr;
   if (grid_cap) *grid_cap = EPB;
   k_bax<N, EPB, STAGES><<<cap, EPB * n * n, smem, s>>>(T, part, err);
   return cudaGetLastError();

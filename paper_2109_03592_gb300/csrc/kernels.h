@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "device_util.cuh"
+#include "launch_once.h"
 
 namespace sem {
 

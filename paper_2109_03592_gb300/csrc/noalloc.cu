@@ -1,5 +1,8 @@
 // sem_pcg_solve_noalloc: the FP64 Jacobi-PCG solve of sem_pcg_solve for callers
-// that cannot allocate device memory.
+// that cannot allocate device memory.  It follows sem_pcg_solve's FP64 rule:
+// CG on the tuned operator, then the true residual with the native FP64
+// operator and restarts from x while that residual misses the tolerance;
+// result->rel_res is that true residual.
 //
 // Some callers cannot call cudaMalloc: code running under a memory manager
 // that owns every byte of the device (a fixed pool handed out up front),
@@ -93,6 +96,18 @@ extern "C" sem_status sem_pcg_solve_noalloc(const sem_mesh* m, const double* b_d
   const int maxit = opts->maxit > 0 ? opts->maxit : 20000;
   cudaStream_t s = (cudaStream_t)stream;
 
+  // the mesh's device (each device has its own copy of the array), and the
+  // kernel choice, which the autotuner writes under the mesh's lock
+  SEM_CUDA(cudaSetDevice(m->device));
+  sem_mesh* mm = const_cast<sem_mesh*>(m);
+  int var_native = 0, var_df = 0, use_df = 0;
+  {
+    std::lock_guard<std::mutex> lk(mm->ws_mutex);
+    var_native = m->ax_var[0];
+    var_df = m->ax_var[2];
+    use_df = m->fp64_df;
+  }
+
   double* base = nullptr;
   sem_status st = scratch_address(&base);
   if (st != SEM_OK) return st;
@@ -106,64 +121,93 @@ extern "C" sem_status sem_pcg_solve_noalloc(const sem_mesh* m, const double* b_d
   double* part_vec = part_ax + kMaxAxPartials;
   PcgState* dst = reinterpret_cast<PcgState*>(part_vec + 3 * 1024);
 
-  // The array keeps the previous call's contents: the state (reduction
-  // counters included) is written in full before any kernel reads it.
-  PcgState h;
-  std::memset(&h, 0, sizeof(h));
-  h.tol2 = tol * tol;
-  h.maxit = maxit;
-  SEM_CUDA(cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, s));
   launch_mask(x_dev, m->wm, n, s);
   launch_minv(minv, nullptr, m->opdK(), m->opdB(), m->wm, h1, h2, n, s);
   count_launches(2);
-  // r = b - A x0
-  st = apply_local(m, x_dev, w, h1, h2, SEM_FP64, s);
-  if (st != SEM_OK) return st;
-  SEM_CUDA(launch_gs<double>(w, gs_dev(m), 1, nullptr, s));
-  SEM_CUDA(launch_residual(r, b_dev, w, m->wm, n, dst, part_vec, 1, s));
   VecParams<double> v{x_dev, r, z, p, w, minv, b_dev, m->wm, n, dst, part_vec};
-  SEM_CUDA(launch_pcg_init<double>(v, s));
-  count_launches(3);
 
-  auto fp64_ax = [&]() -> cudaError_t {
-    if (m->fp64_df) {
-      AxDFParams a{nullptr, w, m->opG32(), m->opG32lo(), m->opB32(), m->opB32lo(), m->D32, m->D32lo, h1, h2, h2 != 0.0, m->E, z, p, dst,
-                   part_ax, m->eo64, m->eodf};
-      return launch_ax_df(m->N, m->ax_var[2], true, a, s, nullptr);
+  // the fused CG operator: the tuned kernel (double-float or native FP64)
+  auto fused_ax = [&]() -> cudaError_t {
+    if (use_df) {
+      AxDFParams a{nullptr, w, m->opG32(), m->opG32lo(), m->opB32(), m->opB32lo(), m->D32, m->D32lo, h1, h2,
+                   h2 != 0.0, m->E, z, p, dst, part_ax, m->eo64, m->eodf};
+      return launch_ax_df(m->N, var_df, true, a, s, nullptr);
     }
-    AxParams<double> a{nullptr, w, m->opG64(), m->opB64(), m->D64, h1, h2, h2 != 0.0, m->E, z, p, dst, part_ax};
-    return launch_ax_f64(m->N, m->ax_var[0], true, a, s, nullptr);
+    AxParams<double> a{nullptr, w, m->opG64(), m->opB64(), m->D64, h1, h2, h2 != 0.0, m->E, z, p, dst, part_ax,
+                       m->dev_err};
+    return launch_ax_f64(m->N, var_native, true, a, s, nullptr);
   };
 
-  PcgState cur;
-  SEM_CUDA(cudaMemcpyAsync(&cur, dst, sizeof(cur), cudaMemcpyDeviceToHost, s));
-  SEM_CUDA(cudaStreamSynchronize(s));
-  if (cur.bb == 0.0) {
-    SEM_CUDA(cudaMemsetAsync(x_dev, 0, n * sizeof(double), s));
-    SEM_CUDA(cudaStreamSynchronize(s));
-  }
+  // The same rule as sem_pcg_solve's FP64 solve: CG runs on its recurrences;
+  // once they meet the tolerance, the true residual b - A x is formed with
+  // the native FP64 operator (exact FP64 arithmetic), and CG restarts from x
+  // if that residual misses (at most kMaxRestarts times within maxit).
+  constexpr int kMaxRestarts = 3;
   constexpr int kChunk = 8;
-  const int max_chunks = maxit / kChunk + 2;
-  for (int c = 0; c < max_chunks && !cur.done; ++c) {
-    for (int k = 0; k < kChunk; ++k) {
-      SEM_CUDA(fp64_ax());
-      SEM_CUDA(launch_gs<double>(w, gs_dev(m), 1, dst, s));
-      SEM_CUDA(launch_pcg_update<double>(v, s));
-    }
-    count_launches(3 * kChunk);
+  int iters = 0, passes = 0;
+  double rel = 0.0;
+  sem_status status = SEM_OK;
+  for (int pass = 0;; ++pass) {
+    // The array keeps the previous call's contents: the state (reduction
+    // counters included) is written in full before any kernel reads it.
+    PcgState h;
+    std::memset(&h, 0, sizeof(h));
+    h.tol2 = tol * tol;
+    h.maxit = maxit - iters;
+    SEM_CUDA(cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    SEM_CUDA(ax64_exact(m, x_dev, w, h1, h2, s));
+    SEM_CUDA(launch_gs<double>(w, gs_dev(m), 1, nullptr, s));
+    SEM_CUDA(launch_residual(r, b_dev, w, m->wm, n, dst, part_vec, 1, s));
+    SEM_CUDA(launch_pcg_init<double>(v, s));
+    count_launches(4);
+    PcgState cur;
     SEM_CUDA(cudaMemcpyAsync(&cur, dst, sizeof(cur), cudaMemcpyDeviceToHost, s));
     SEM_CUDA(cudaStreamSynchronize(s));
-  }
-  if (!cur.done) {
-    set_error("sem_pcg_solve_noalloc: CG did not report completion within maxit iterations");
-    return SEM_ERR_DEVICE_TIMEOUT;
+    if (cur.bb == 0.0) {  // b = 0: x = 0
+      SEM_CUDA(cudaMemsetAsync(x_dev, 0, n * sizeof(double), s));
+      SEM_CUDA(cudaStreamSynchronize(s));
+      rel = 0.0;
+      status = SEM_OK;
+      break;
+    }
+    rel = std::sqrt(cur.aux / cur.bb);  // true residual of the current x
+    passes = pass;
+    if (rel <= tol) {
+      status = SEM_OK;
+      break;
+    }
+    if (pass > kMaxRestarts || iters >= maxit) {
+      status = SEM_ERR_NOT_CONVERGED;
+      break;
+    }
+    const int max_chunks = (maxit - iters) / kChunk + 2;
+    for (int c = 0; c < max_chunks && !cur.done; ++c) {
+      for (int k = 0; k < kChunk; ++k) {
+        SEM_CUDA(fused_ax());
+        SEM_CUDA(launch_gs<double>(w, gs_dev(m), 1, dst, s));
+        SEM_CUDA(launch_pcg_update<double>(v, s));
+      }
+      count_launches(3 * kChunk);
+      SEM_CUDA(cudaMemcpyAsync(&cur, dst, sizeof(cur), cudaMemcpyDeviceToHost, s));
+      SEM_CUDA(cudaStreamSynchronize(s));
+    }
+    if (!cur.done) {
+      set_error("sem_pcg_solve_noalloc: CG did not report completion within maxit iterations");
+      return SEM_ERR_DEVICE_TIMEOUT;
+    }
+    iters += cur.iter;
+    if (cur.status != SEM_OK) {  // breakdown, or maxit without meeting the tolerance
+      rel = std::sqrt(cur.rr / cur.bb);
+      status = (sem_status)cur.status;
+      break;
+    }
   }
   if (result) {
-    result->iters = cur.iter;
-    result->outer_iters = 0;
-    result->rel_res = cur.bb > 0.0 ? std::sqrt(cur.rr / cur.bb) : 0.0;
+    result->iters = iters;
+    result->outer_iters = passes;
+    result->rel_res = rel;
     result->ms = 0.0;
-    result->status = cur.status;
+    result->status = status;
   }
-  return (sem_status)cur.status;
+  return status;
 }

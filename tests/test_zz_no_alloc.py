@@ -50,6 +50,32 @@ def test_noalloc_solve_matches_pcg_solve_twice():
         assert np.sqrt(P.dot(r, r) / P.dot(bn, bn)) <= 1.1e-10
 
 
+@pytest.mark.parametrize("kernel", ["df", "native"])
+def test_noalloc_reports_the_true_residual(monkeypatch, kernel):
+    """The reported rel_res is the true residual ||b - A x|| / ||b||, formed
+    after the CG recurrences stop; the oracle's FP64 operator recomputes it.
+    With the double-float CG operator forced, the recurrence alone would not
+    show whether the true residual meets the tolerance."""
+    import paper_2109_03592_gb300 as sem
+    monkeypatch.setenv("SEM_FP64_KERNEL", kernel)
+    m, P, b = _case()
+    assert m.fp64_double_float() == (kernel == "df")
+    import torch
+    bn = b.cpu().numpy()
+    for call in range(2):
+        x = torch.zeros_like(b)
+        res = m.solve_noalloc(b, x, tol=SOLVE_TOL, h1=1.0, h2=0.5)
+        assert res["status"] == 0, (call, res)
+        r = bn - P.A(x.cpu().numpy())
+        true_rel = np.sqrt(P.dot(r, r) / P.dot(bn, bn))
+        assert true_rel <= 1.05e-10, (call, true_rel)
+        assert abs(res["rel_res"] - true_rel) <= 1e-3 * true_rel + 1e-15, (call, res, true_rel)
+    # a starting guess that already meets the tolerance: no iteration, the same residual
+    res2 = m.solve_noalloc(b, x, tol=SOLVE_TOL, h1=1.0, h2=0.5)
+    assert res2["status"] == 0 and res2["iters"] == 0, res2
+    assert abs(res2["rel_res"] - res["rel_res"]) <= 1e-3 * res["rel_res"], (res2, res)
+
+
 def test_noalloc_rejects_large_mesh_and_other_precisions():
     import torch
     import paper_2109_03592_gb300 as sem
