@@ -134,13 +134,14 @@ def aggregate(local_seconds, steps, world, dist=None):
 
 # ---------------------------------------------------------------- oracle arm
 
-def oracle_sample(budget_s=20.0, iters=None):
-    """Time the CPU oracle's FP64 PCG iteration (A = mask QQ^T A_L, Jacobi,
-    weighted dots) on a slab of the benchmark pipe: same cross-section
-    (nc = 16, nr = 4, N = 7), 3 axial layers (E = 1536).  Returns seconds per
-    local point per iteration and a description."""
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+def _oracle_slab_worker(budget_s):
+    """One host core: the oracle's FP64 Jacobi-PCG iteration (A = mask QQ^T
+    A_L, Jacobi, weighted dots; oracle/solver.py restated as a loop) on a
+    3-layer slab of the bench pipe (nc = 16, nr = 4, N = 7, E = 1536) for
+    budget_s seconds.  Returns (local points x iterations per second,
+    iterations, seconds)."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
     import numpy as np
     from oracle import mesh as omesh, solver as osolver
     from sem_inputs import forcing
@@ -167,12 +168,55 @@ def oracle_sample(budget_s=20.0, iters=None):
         rho = rho_new
         k += 1
         el = time.perf_counter() - t0
-        if (iters and k >= iters) or (not iters and el >= budget_s):
+        if el >= budget_s:
             break
-    per_pt_iter = el / (k * m.E * 512)
-    desc = (f"oracle FP64 PCG iterations on a 3-layer slab of the pipe (nc=16, nr=4, N=7, E=1536, "
-            f"{k} iterations, {el:.1f} s), scaled per local point to E=262144 and the GPU solve's iteration count")
-    return per_pt_iter, k, el, desc
+    return k * m.E * 512 / el, k, el
+
+
+def host_cpu():
+    """(logical cores, CPU model) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return os.cpu_count() or 1, model
+
+
+def oracle_sample(budget_s=20.0, cores=None):
+    """The oracle's FP64 PCG iteration timed on every host core at once: one
+    spawned process per core, each iterating on its own copy of the 3-layer
+    slab (independent problems, as the GPU replicas).  Returns (seconds per
+    local point per iteration for the whole host, cores, description)."""
+    import multiprocessing as mp
+    ncores, model = host_cpu()
+    cores = cores or ncores
+    ctx = mp.get_context("spawn")  # no fork after CUDA initialisation
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_slab_worker, [budget_s] * cores)
+    rate = sum(r[0] for r in res)
+    its = sum(r[1] for r in res)
+    desc = (f"oracle FP64 Jacobi-PCG iterations on a 3-layer slab of the pipe (nc=16, nr=4, N=7, E=1536), one "
+            f"process per core on {cores} cores ({model}), {budget_s:.0f} s each, {its} iterations in total; the "
+            f"host's points x iterations per second scaled to the solve")
+    return 1.0 / rate, cores, model, desc
+
+
+# FP64 Jacobi-PCG iterations of the bench system (E = 262,144 pipe, seed-2
+# right-hand side, tol 1e-10), measured by the FP64 solve of this build on
+# GB300 (its iteration counts are held to within 2 of the oracle's by the
+# parity tests on smaller meshes).  The oracle cannot run a solve of this size
+# on the host; the reference arm multiplies its measured per-iteration rate by
+# this count.  The GPU arm uses the count its own FP64 solve measures in the
+# same run.
+FP64_ITERS_BENCH = 5564
 
 
 def run_reference(args):
@@ -180,17 +224,15 @@ def run_reference(args):
     if rank != 0:
         return 0
     E, n3 = 262144, 512
-    per_pt, k, el, desc = oracle_sample(budget_s=max(10.0, 20.0 / max(1, args.steps)))
-    # the FP64 oracle iteration count of the full solve is not affordable on the
-    # CPU; use the GPU FP64 PCG iteration count of this workload (5561)
-    iters_full = 5561
-    sec_per_solve = per_pt * E * n3 * iters_full
+    sec_pt, cores, model, desc = oracle_sample(budget_s=max(10.0, 20.0 / max(1, args.steps)))
+    sec_per_solve = sec_pt * E * n3 * FP64_ITERS_BENCH
     value = 1.0 / sec_per_solve
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_solve * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": f"{WORKLOAD}: O-grid pipe E=262144 N=7, FP64 Jacobi-PCG to 1e-10"},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "cpu": model, "kind": "oracle",
+                             "sample": desc + f" and {FP64_ITERS_BENCH} iterations (the system's FP64 PCG count)"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -403,6 +445,105 @@ def pressure_solve_leg(workload="pipe4096_n7", tol=1e-10):
     return out
 
 
+def _sig(obj, digits=4):
+    """Floats rounded to `digits` significant digits (auxiliary legs only)."""
+    if isinstance(obj, float):
+        return float(f"{obj:.{digits}g}") if math.isfinite(obj) else obj
+    if isinstance(obj, dict):
+        return {k: _sig(v, digits) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [_sig(v, digits) for v in obj]
+    return obj
+
+
+def compact_projection(p):
+    if not p:
+        return p
+    return _sig({"workload": p["workload"], "solves": p["solves"], "iters_with": p["with"]["iters"],
+                 "iters_without": p["without"]["iters"], "ms_with": sum(p["with"]["ms"]),
+                 "ms_without": sum(p["without"]["ms"]), "time_ratio": p["time_ratio"]})
+
+
+def compact_velocity(v):
+    if not v:
+        return v
+    return [_sig({"workload": r["workload"], "iters": r["iters"], "batched_ms": r["batched_ms"],
+                  "one_at_a_time_ms": r["one_at_a_time_ms"], "max_rel_res": r["max_rel_res"]}) for r in v]
+
+
+def compact_pressure(p):
+    if not p or "error" in p:
+        return p
+    out = {k: p[k] for k in ("apply_ms", "grad_ms", "div_ms", "gdofs", "fp64_tflops", "algorithmic_gbs") if k in p}
+    if "solve" in p:
+        sv = p["solve"]
+        out["solve"] = sv if "error" in sv else {k: sv[k] for k in ("iters", "ms", "rel_res", "status")}
+    return _sig(out)
+
+
+def schwarz_leg(m, b, stream, precs=("MIXED",)):
+    """The overlapping Schwarz preconditioner (Sec. 2, Eq. 6; sem_schwarz_*)
+    on the bench system: set-up, one application (FP32 and FP64, CUDA events
+    on the launching stream) and solves to 1e-10 beside the Jacobi ones."""
+    import torch
+    import paper_2109_03592_gb300 as sem
+    t0 = time.perf_counter()
+    sw = sem.Schwarz(m, coarse=True)
+    setup_s = time.perf_counter() - t0
+    info = sw.info()
+    out = {"setup_s": setup_s, "coarse": info["coarse"], "n_coarse": info["n_coarse"],
+           "n_distinct_1d": info["n_distinct"]}
+    r32 = torch.randn(m.shape, dtype=torch.float32, device="cuda")
+    m.gs(r32, apply_mask=True, prec=sem.FP32)
+    z32 = torch.empty_like(r32)
+    out["apply_fp32_ms"] = time_kernel(lambda: sw.apply(r32, z32, prec=sem.FP32), 5, stream)
+    del r32, z32
+    x = torch.zeros_like(b)
+    for prec in precs:
+        x.zero_()
+        r = sw.solve(b, x, tol=1e-10, prec=getattr(sem, prec))
+        out[prec.lower()] = {"iters": r["iters"], "ms": r["ms"], "solves_per_s": 1e3 / r["ms"],
+                             "rel_res": r["rel_res"], "status": r["status"]}
+    sw.close()
+    return _sig(out)
+
+
+def large_leg(workloads=("pipe1048576_n7", "pipe131072_n11"), precs=("MIXED", "FP64")):
+    """The large configurations (E = 1,048,576 at N = 7, ~3.6e8 DOFs; E =
+    131,072 at N = 11): mesh set-up, mixed and FP64 Jacobi-PCG solves to 1e-10
+    (time, iterations, the solver's true residual) and the device memory in
+    use during the solves (cudaMemGetInfo)."""
+    import torch
+    import paper_2109_03592_gb300 as sem
+    from sem_inputs import configs, forcing
+    out = []
+    for wl in workloads:
+        desc = configs.mesh_desc(wl)
+        t0 = time.perf_counter()
+        mm = sem.Mesh(desc)
+        setup_s = time.perf_counter() - t0
+        xyz = mm.coords()
+        f = forcing.evaluate_torch(xyz, forcing.random_modes(2, L=desc.get("L", 8.0)))
+        del xyz
+        bb = torch.empty_like(f)
+        mm.rhs(f, bb)
+        del f
+        torch.cuda.empty_cache()
+        rec = {"workload": wl, "E": mm.E, "N": mm.N, "dofs": mm.E * mm.N ** 3, "setup_s": setup_s}
+        xx = torch.zeros_like(bb)
+        for prec in precs:
+            xx.zero_()
+            r = mm.solve(bb, xx, tol=1e-10, prec=getattr(sem, prec))
+            free, total = torch.cuda.mem_get_info()
+            rec[prec.lower()] = {"ms": r["ms"], "iters": r["iters"], "rel_res": r["rel_res"], "status": r["status"],
+                                 "device_used_gb": (total - free) / 1e9}
+        mm.close()
+        del bb, xx
+        torch.cuda.empty_cache()
+        out.append(_sig(rec))
+    return out
+
+
 def desc_elements(d):
     return d["nx"] * d["ny"] * d["nz"] if d["kind"] == "box" else d["nc"] * (d["nc"] + 4 * d["nr"]) * d["nzp"]
 
@@ -523,12 +664,19 @@ def run_gpu(args):
     ax32_gbs = AX_BYTES["fp32"] * P / (ax32_ms * 1e6)
     ax64_gbs = AX_BYTES["fp64"] * P / (ax64_ms * 1e6)
 
-    # ---- plain FP64 PCG on the same system (one solve)
+    # ---- plain FP64 PCG on the same system (one solve), and the mixed
+    # solution's error against it: ||x_mixed - x_fp64||_W / ||x_fp64||_W
     fp64 = None
+    mixed_err = None
     if not args.quick:
+        x_mixed = x.clone()
         x.zero_()
         r64 = m.solve(b, x, tol=1e-10, prec=sem.FP64)
         fp64 = {"ms": r64["ms"], "iters": r64["iters"], "rel_res": r64["rel_res"], "status": r64["status"]}
+        mult, _ = m.weights()
+        d = x_mixed - x
+        mixed_err = float(torch.sqrt((d * d / mult).sum() / (x * x / mult).sum()))
+        del x_mixed, d, mult
 
     # ---- end to end through host buffers (pinned), same metric
     b_host = torch.empty(m.shape, dtype=torch.float64, pin_memory=True)
@@ -555,41 +703,48 @@ def run_gpu(args):
     velocity = None
     if not args.no_velocity:
         velocity = [velocity_helmholtz_leg(w) for w in ("pipe4096_n7", "pipe32768_n7")]
+    schwarz_res = None
+    if not args.no_schwarz:
+        try:
+            schwarz_res = schwarz_leg(m, b, stream)
+        except Exception as e:  # an auxiliary leg must not cost the headline line
+            schwarz_res = {"error": f"{type(e).__name__}: {e}"}
+    mesh_E, mesh_N, mesh_glob = m.E, m.N, m.n_global
+    fp32_var, fp64_df, ax_traffic = m.ax_variant(sem.FP32), m.fp64_double_float(), fp32_ax_traffic(m)
+    large = None
+    if not args.no_large:
+        m.close()  # the large meshes need the device memory
+        del b, x
+        torch.cuda.empty_cache()
+        try:
+            large = large_leg()
+        except Exception as e:
+            large = {"error": f"{type(e).__name__}: {e}"}
 
     line = None
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu:
-            per_pt, k, el, desc_s = oracle_sample(budget_s=20.0)
-            sec = per_pt * P * (fp64["iters"] if fp64 else 5561)
-            cpu = {"value": 1.0 / sec, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": desc_s}
+            sec_pt, cores, model, desc_s = oracle_sample(budget_s=20.0)
+            iters_cpu = fp64["iters"] if fp64 else FP64_ITERS_BENCH
+            sec = sec_pt * P * iters_cpu
+            cpu = {"value": 1.0 / sec, "unit": "solves/s", "cores": cores, "cpu": model, "kind": "oracle",
+                   "sample": desc_s + f" and {iters_cpu} iterations (the FP64 PCG count of this system)"}
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer (mixed, reliable updates)",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}: O-grid pipe E={m.E} N={m.N}, mixed-precision Jacobi-PCG "
+            "config": {"workload": f"{args.workload}: O-grid pipe E={mesh_E} N={mesh_N}, mixed-precision Jacobi-PCG "
                                    f"to 1e-10 (FP32 inner, FP64 outer residual)",
-                       "E": m.E, "N": m.N, "n_local": P, "n_global": m.n_global, "tol": 1e-10,
+                       "E": mesh_E, "N": mesh_N, "n_local": P, "n_global": mesh_glob, "tol": 1e-10,
                        "l2": "inputs larger than L2 (mesh ~20 GB), no flush", "replicas": world,
                        "setup_s": round(setup_s, 2)},
-            "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "min": min(lat), "max": max(lat)},
-            "solve": {"iters": iters, "outer_iters": outers, "rel_res": rel, "wall_s": wall_s},
-            "ax": {"fp64_ms": ax64_ms, "fp64_gdofs": dof / (ax64_ms * 1e6), "fp64_gbs": ax64_gbs,
-                   "fp64_hbm_frac": ax64_gbs / hbm, "fp64_kernel": "double-float" if m.fp64_double_float() else "native",
-                   "fp32_ms": ax32_ms, "fp32_gdofs": dof / (ax32_ms * 1e6), "fp32_gbs": ax32_gbs,
-                   "fp32_hbm_frac": ax32_gbs / hbm},
-            "gs": {"fp64_ms": gs64_ms, "fp32_ms": gs32_ms},
-            "fp64_pcg": fp64,
-            "serving": serving,
-            "projection": proj,
-            "velocity_helmholtz": velocity,
-            "pressure_operator": pressure,
-            "roofline": {"bound": "hbm", "kernel": fp32_kernel_name(m.N, m.ax_variant(sem.FP32)),
+            "roofline": {"bound": "hbm", "kernel": fp32_kernel_name(mesh_N, fp32_var),
                          "timed": "sem_ax FP32 launches on the bench mesh, CUDA events on the launching stream, "
                                   "after the timed solves (the inner CG runs the fused form of the same kernel)",
                          "achieved": ax32_gbs, "peak": hbm, "unit": "GB/s", "frac": ax32_gbs / hbm,
-                         "peak_kind": peak_kind, "traffic": fp32_ax_traffic(m),
+                         "peak_kind": peak_kind, "traffic": ax_traffic,
                          "traffic_source": TRAFFIC_SOURCE,
                          "algorithmic_bytes_per_launch": AX_BYTES["fp32"] * P},
             "cpu_baseline": cpu,
@@ -597,6 +752,22 @@ def run_gpu(args):
                     "d2h_bytes_per_step": 8 * P, "ms": e2e_ms},
             "gpu_launches": launches,
             "clocks": clk.summary(),
+            "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "min": min(lat), "max": max(lat)},
+            "solve": {"iters": iters[0], "outer_iters": outers[0], "max_rel_res": max(rel), "wall_s": wall_s},
+            # auxiliary legs, compact; the headline's secondary metrics come last
+            "projection": compact_projection(proj),
+            "velocity_helmholtz": compact_velocity(velocity),
+            "pressure_operator": compact_pressure(pressure),
+            "large": large,
+            "serving": _sig(serving) if serving else serving,
+            "schwarz": schwarz_res,
+            "fp64_pcg": fp64,
+            "mixed_vs_fp64_err": mixed_err,
+            "gs": {"fp64_ms": gs64_ms, "fp32_ms": gs32_ms},
+            "ax": {"fp64_ms": ax64_ms, "fp64_gdofs": dof / (ax64_ms * 1e6), "fp64_gbs": ax64_gbs,
+                   "fp64_hbm_frac": ax64_gbs / hbm, "fp64_kernel": "double-float" if fp64_df else "native",
+                   "fp32_ms": ax32_ms, "fp32_gdofs": dof / (ax32_ms * 1e6), "fp32_gbs": ax32_gbs,
+                   "fp32_hbm_frac": ax32_gbs / hbm},
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -617,6 +788,8 @@ def main():
     ap.add_argument("--no-pressure", action="store_true", help="skip the P_N - P_{N-2} pressure-operator leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream leg")
     ap.add_argument("--no-velocity", action="store_true", help="skip the three-component velocity Helmholtz leg")
+    ap.add_argument("--no-schwarz", action="store_true", help="skip the overlapping-Schwarz leg")
+    ap.add_argument("--no-large", action="store_true", help="skip the E = 1,048,576 and N = 11 solves")
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--serving-rate", type=float, default=2.0)
     args = ap.parse_args()

@@ -414,13 +414,65 @@ sem_status sem_schwarz_fdm_1d(int N, double l, double l_lo, double l_hi, int dir
  * sem_mesh_global_ids), xyz [E][3][n^3] GLL coordinates, dirichlet_face [E][6]
  * (faces 0: i = 0, 1: i = N, 2: j = 0, 3: j = N, 4: k = 0, 5: k = N).  Mean
  * lengths are the mean over the n^2 GLL lines of the distance between their
- * ends; two element faces are neighbours when their centre nodes share a
- * global id (so N >= 2).  Outputs S_host [E][3][n][n] and lam_host [E][3][n]
+ * ends; two element faces are neighbours when their four corner nodes have
+ * the same global ids (in any orientation).  Outputs S_host [E][3][n][n] and lam_host [E][3][n]
  * (direction r, s, t); each distinct 1D problem is solved once, and
  * *n_distinct (nullable) receives their number. */
 sem_status sem_schwarz_setup_host(int64_t E, int N, const int64_t* glo, const double* xyz,
                                   const uint8_t* dirichlet_face, double* S_host, double* lam_host,
                                   int64_t* n_distinct);
+
+/* ---- overlapping Schwarz preconditioner on the device (Sec. 2, Eq. 6) ------
+ * Eq. 6 preconditions the solve with local solves on overlapping subdomains
+ * plus a coarse-grid solve.  Here (the paper leaves the pieces undefined):
+ *   M^{-1} r = mask QQ^T (W A~_e^{-1} (W r_e) for every element e) + R_0^T A_0^{-1} R_0 r
+ * - subdomain e: the element with all its GLL nodes (overlap = shared nodes);
+ *   A~_e: the separable fast-diagonalisation form of its local problem, 1D
+ *   operators from the element's mean lengths and its face neighbours' (see
+ *   sem_schwarz_setup_host), A~_e^{-1} = (S_t(x)S_s(x)S_r)(h1 (lam_r + lam_s +
+ *   lam_t) + h2)^{-1}(S_t(x)S_s(x)S_r)^T;
+ * - W = mult^{-1/2} at every local point (symmetric weighting);
+ * - coarse space: the trilinear functions of the element vertices that are
+ *   not Dirichlet; R_0 r = sum over global nodes of phi r, A_0 = R_0 A R_0^T
+ *   (Galerkin), solved through its inverse, formed once on the device
+ *   (Gauss-Jordan, SPD), when A_0 has at most SEM_SCHWARZ_DENSE_COARSE_MAX
+ *   unknowns; with more the coarse term is left out (sem_schwarz_info). */
+typedef struct sem_schwarz sem_schwarz;
+#define SEM_SCHWARZ_COARSE 1             /* flags: include the coarse-grid term */
+#define SEM_SCHWARZ_DENSE_COARSE_MAX 8192
+
+typedef struct {
+  int64_t n_distinct; /* distinct 1D eigenproblems solved on the host */
+  int64_t n_coarse;   /* coarse unknowns (free element vertices) */
+  int coarse;         /* 1 if the coarse term is applied */
+  size_t dev_bytes;   /* device memory held by the preconditioner (solver workspace excluded) */
+  double setup_ms;    /* wall time of sem_schwarz_create */
+} sem_schwarz_info_t;
+
+/* Build the preconditioner of a mesh for the operator (h1, h2), scalars
+ * (meshes with per-point coefficients: SEM_ERR_INVALID).  Synchronous; holds
+ * library-owned device memory until sem_schwarz_destroy.  The mesh must
+ * outlive it, and a later sem_mesh_set_coefficients makes it unusable
+ * (SEM_ERR_INVALID from apply/solve).  Errors: SEM_ERR_INVALID,
+ * SEM_ERR_BREAKDOWN (coarse matrix not positive definite), SEM_ERR_CUDA. */
+sem_status sem_schwarz_create(const sem_mesh* mesh, double h1, double h2, int flags, sem_schwarz** out);
+sem_status sem_schwarz_destroy(sem_schwarz* sw);
+sem_status sem_schwarz_info(const sem_schwarz* sw, sem_schwarz_info_t* info);
+
+/* z = M^{-1} r for a continuous, masked local vector r (as the CG residual):
+ * r_dev, z_dev [E][n^3] device arrays of doubles (SEM_FP64) or floats
+ * (SEM_FP32, the FP32 tables and fields), distinct; asynchronous on stream. */
+sem_status sem_schwarz_apply(const sem_schwarz* sw, const void* r_dev, void* z_dev, sem_prec prec, void* stream);
+
+/* PCG for A x = b with z = M^{-1} r in place of Jacobi; b_dev, x_dev, opts and
+ * result as sem_pcg_solve (opts->h1, h2 must be the preconditioner's).
+ * SEM_FP64: FP64 CG and FP64 preconditioner, the final true residual checked
+ * with the native FP64 operator (restarts as sem_pcg_solve).  SEM_MIXED: FP32
+ * CG with the FP32 operator and preconditioner on the system scaled by
+ * 1/||b||, FP64 reliable updates (opts->delta; <= 0 means 0.3) with the
+ * native FP64 residual.  Synchronous; one solve at a time per preconditioner. */
+sem_status sem_schwarz_solve(sem_schwarz* sw, const double* b_dev, double* x_dev, const sem_solve_opts* opts,
+                             sem_solve_result* result, void* stream);
 
 /* ---- serving ------------------------------------------------------------ */
 

@@ -55,25 +55,28 @@ def element_lengths(mesh):
     return np.stack([lr, ls, lt], axis=1)
 
 
-def face_centre_index(n, f):
-    """(k, j, i) of the face's centre-most GLL node (interior to the face for N >= 2)."""
-    c, e = n // 2, (0 if f % 2 == 0 else n - 1)
-    a = FACE_AXIS[f]
-    return (e, c, c) if a == 2 else ((c, e, c) if a == 1 else (c, c, e))
+def face_corner_indices(n, f):
+    """(k, j, i) of the four corner GLL nodes of face f of an element."""
+    N, end, a = n - 1, (0 if f % 2 == 0 else n - 1), FACE_AXIS[f]
+    out = []
+    for u in (0, N):
+        for v in (0, N):
+            out.append((end, v, u) if a == 2 else ((v, end, u) if a == 1 else (v, u, end)))
+    return out
 
 
 def face_neighbours(prob):
     """[E, 6] (element, face) across each face, (-1, -1) on the domain
-    boundary.  Two element faces are the same face when their centre nodes
-    have the same global id (N >= 2)."""
+    boundary.  Two element faces are the same face when they have the same
+    four vertices: the global ids of their corner nodes, as a set (so the two
+    elements may have any relative orientation)."""
     mesh = prob.mesh
-    if mesh.N < 2:
-        raise ValueError("face neighbours are found through face-interior nodes: N >= 2")
     glo = prob.glo.reshape(prob.shape)
     owner = {}
     for e in range(mesh.E):
         for f in range(6):
-            owner.setdefault(int(glo[(e,) + face_centre_index(mesh.n, f)]), []).append((e, f))
+            key = tuple(sorted(int(glo[(e,) + c]) for c in face_corner_indices(mesh.n, f)))
+            owner.setdefault(key, []).append((e, f))
     nb = -np.ones((mesh.E, 6, 2), dtype=np.int64)
     for pairs in owner.values():
         if len(pairs) == 2:

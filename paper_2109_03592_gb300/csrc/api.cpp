@@ -169,6 +169,7 @@ sem_status build_mesh(const sem_mesh_desc& d, cudaStream_t s, sem_mesh* m) {
   generator_dirichlet(d, E, dface);
   GsPlan plan;
   SEM_TRY(build_gs_plan(topo, dface.data(), plan));
+  m->dface = dface;
   vert.clear();
   vert.shrink_to_fit();
 

@@ -109,12 +109,19 @@ struct VecParams {
   double* partial;  // [3 * grid]
 };
 int vec_grid();
+// ext = true: an external preconditioner (its kernels write z = M^{-1} r
+// between k_pcg_update and launch_pcg_rho; init and restart read that z).
 template <typename T>
-cudaError_t launch_pcg_update(const VecParams<T>& p, cudaStream_t s);
+cudaError_t launch_pcg_update(const VecParams<T>& p, cudaStream_t s, bool ext = false);
 template <typename T>
-cudaError_t launch_pcg_init(const VecParams<T>& p, cudaStream_t s);
+cudaError_t launch_pcg_init(const VecParams<T>& p, cudaStream_t s, bool ext = false);
 template <typename T>
-cudaError_t launch_pcg_restart(const VecParams<T>& p, cudaStream_t s);
+cudaError_t launch_pcg_restart(const VecParams<T>& p, cudaStream_t s, bool ext = false);
+// rho_new = <r, z>_W, beta = rho_new / rho (skipped once st->done); with
+// zout, z (type Z) holds M^{-1} (zscale r) and zout = z / zscale is written.
+template <typename T, typename Z>
+cudaError_t launch_pcg_rho(const T* r, const Z* z, T* zout, double zscale, const uint8_t* wm, int64_t n, PcgState* st,
+                           double* partial, cudaStream_t s);
 void launch_set_bb(PcgState* st, double bb, double delta2, cudaStream_t s);
 
 void launch_mul(double* out, const double* a, const double* b, int64_t n, cudaStream_t s);

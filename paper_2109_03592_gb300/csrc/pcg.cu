@@ -82,7 +82,10 @@ struct Vec16<double> {
 // checks ||r|| <= tol ||b||, else forms beta = <r,z>_new / <r,z>_old.
 // Each thread moves 16-byte vectors (4 floats / 2 doubles per array), so a
 // resident block keeps 5 x 16 B loads per thread in flight.
-template <typename T>
+// EXT (a preconditioner applied by other kernels, e.g. overlapping Schwarz):
+// only x, r and <r, r> with the stop tests here; z = M^{-1} r and beta come
+// from the preconditioner's kernels and k_pcg_rho afterwards.
+template <typename T, bool EXT>
 __global__ void __launch_bounds__(kVecThreads) k_pcg_update(const VecParams<T> P) {
   using Acc = typename AccOf<T>::type;
   using VT = Vec16<T>;
@@ -106,7 +109,8 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(const VecParams<T> P
     const V wv = reinterpret_cast<const V*>(P.w)[q];
     V rv = reinterpret_cast<const V*>(P.r)[q];
     V xv = reinterpret_cast<const V*>(P.x)[q];
-    const V mv = reinterpret_cast<const V*>(P.minv)[q];
+    V mv;
+    if (!EXT) mv = reinterpret_cast<const V*>(P.minv)[q];
     const M wm = reinterpret_cast<const M*>(P.wm)[q];
     V zv;
 #pragma unroll
@@ -114,24 +118,28 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(const VecParams<T> P
       const T rq = VT::get(rv, k) - alpha * VT::get(wv, k);
       VT::set(xv, k, VT::get(xv, k) + alpha * VT::get(pv, k));
       VT::set(rv, k, rq);
-      const T zq = VT::get(mv, k) * rq;
-      VT::set(zv, k, zq);
       const T im = sinv[VT::getm(wm, k) & 0x7f];
-      rz.add(rq * zq * im);
+      if (!EXT) {
+        const T zq = VT::get(mv, k) * rq;
+        VT::set(zv, k, zq);
+        rz.add(rq * zq * im);
+      }
       rr.add(rq * rq * im);
     }
     reinterpret_cast<V*>(P.x)[q] = xv;
     reinterpret_cast<V*>(P.r)[q] = rv;
-    reinterpret_cast<V*>(P.z)[q] = zv;
+    if (!EXT) reinterpret_cast<V*>(P.z)[q] = zv;
   }
   for (int64_t q = nv * W + t0; q < P.n; q += stride) {  // tail (n not a multiple of W)
     const T rq = P.r[q] - alpha * P.w[q];
     P.x[q] = P.x[q] + alpha * P.p[q];
     P.r[q] = rq;
-    const T zq = P.minv[q] * rq;
-    P.z[q] = zq;
     const T im = sinv[P.wm[q] & 0x7f];
-    rz.add(rq * zq * im);
+    if (!EXT) {
+      const T zq = P.minv[q] * rq;
+      P.z[q] = zq;
+      rz.add(rq * zq * im);
+    }
     rr.add(rq * rq * im);
   }
   const double srz = block_sum(rz.get(), sred);
@@ -161,17 +169,63 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(const VecParams<T> P
         st->ru = 1;
       } else {
         if (rr_t > st->rr_max) st->rr_max = rr_t;
-        st->beta = rz_t / st->rho;
-        st->rho = rz_t;
+        if (!EXT) {
+          st->beta = rz_t / st->rho;
+          st->rho = rz_t;
+        }
       }
       st->cnt[1] = 0;
     }
   }
 }
 
+// With an external preconditioner (z = M^{-1} r written by its kernels after
+// k_pcg_update<T, true>): rho_new = <r, z>, beta = rho_new / rho_old.  If
+// ZOUT, z is FP32 (computed from r scaled by zscale) and is written back to
+// zout = z / zscale in T while the product is formed.
+template <typename T, typename Z>
+__global__ void __launch_bounds__(kVecThreads) k_pcg_rho(const T* __restrict__ r, const Z* __restrict__ z,
+                                                         T* __restrict__ zout, double zscale, const uint8_t* wm,
+                                                         int64_t n, PcgState* st, double* partial) {
+  using Acc = typename AccOf<T>::type;
+  __shared__ double sred[32];
+  __shared__ T sinv[128];
+  __shared__ int sdone;
+  if (threadIdx.x == 0) sdone = st->done;
+  fill_inv_mult(sinv);
+  __syncthreads();
+  if (sdone) return;
+  Acc rz;
+  const T inv = (T)(1.0 / zscale);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    T zq = (T)z[q];
+    if (zout) {
+      zq = zq * inv;
+      zout[q] = zq;
+    }
+    rz.add(r[q] * zq * sinv[wm[q] & 0x7f]);
+  }
+  const double a = block_sum(rz.get(), sred);
+  if (threadIdx.x == 0) partial[blockIdx.x] = a;
+  if (last_block(&st->cnt[3])) {
+    const double rz_t = sum_partials(partial, gridDim.x, 1, 0, sred);
+    if (threadIdx.x == 0) {
+      if (rz_t != rz_t) {
+        st->done = 1;
+        st->status = 5;  // SEM_ERR_BREAKDOWN (NaN)
+      } else {
+        st->beta = rz_t / st->rho;
+        st->rho = rz_t;
+      }
+      st->cnt[3] = 0;
+    }
+  }
+}
+
 // Start of a CG run on residual r (already b - A x0) and right-hand side b:
 // z = M^{-1} r, p = 0, rho = <r,z>, rr = <r,r>, bb = <b,b>, beta = 0.
-template <typename T>
+// EXT: z = M^{-1} r was written by the preconditioner's kernels (read here).
+template <typename T, bool EXT>
 __global__ void __launch_bounds__(kVecThreads) k_pcg_init(const VecParams<T> P) {
   using Acc = typename AccOf<T>::type;
   __shared__ double sred[32];
@@ -181,8 +235,13 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_init(const VecParams<T> P) 
   Acc rz, rr, bb;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P.n; q += (int64_t)gridDim.x * blockDim.x) {
     const T rq = P.r[q], bq = P.b[q];
-    const T zq = P.minv[q] * rq;
-    P.z[q] = zq;
+    T zq;
+    if (EXT) {
+      zq = P.z[q];
+    } else {
+      zq = P.minv[q] * rq;
+      P.z[q] = zq;
+    }
     P.p[q] = T(0);
     const T im = sinv[P.wm[q] & 0x7f];
     rz.add(rq * zq * im);
@@ -220,7 +279,7 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_init(const VecParams<T> P) 
 
 // Continue CG after the residual r was replaced (reliable update):
 // z = M^{-1} r, rho_new = <r,z>, beta = rho_new / rho, rr_max = <r,r>; p is kept.
-template <typename T>
+template <typename T, bool EXT>
 __global__ void __launch_bounds__(kVecThreads) k_pcg_restart(const VecParams<T> P) {
   using Acc = typename AccOf<T>::type;
   __shared__ double sred[32];
@@ -230,8 +289,13 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_restart(const VecParams<T> 
   Acc rz, rr;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P.n; q += (int64_t)gridDim.x * blockDim.x) {
     const T rq = P.r[q];
-    const T zq = P.minv[q] * rq;
-    P.z[q] = zq;
+    T zq;
+    if (EXT) {
+      zq = P.z[q];
+    } else {
+      zq = P.minv[q] * rq;
+      P.z[q] = zq;
+    }
     const T im = sinv[P.wm[q] & 0x7f];
     rz.add(rq * zq * im);
     rr.add(rq * rq * im);
@@ -260,27 +324,49 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_restart(const VecParams<T> 
 }
 
 template <typename T>
-cudaError_t launch_pcg_restart(const VecParams<T>& p, cudaStream_t s) {
-  k_pcg_restart<T><<<kVecBlocks, kVecThreads, 0, s>>>(p);
+cudaError_t launch_pcg_restart(const VecParams<T>& p, cudaStream_t s, bool ext) {
+  if (ext)
+    k_pcg_restart<T, true><<<kVecBlocks, kVecThreads, 0, s>>>(p);
+  else
+    k_pcg_restart<T, false><<<kVecBlocks, kVecThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
-template cudaError_t launch_pcg_restart<float>(const VecParams<float>&, cudaStream_t);
-template cudaError_t launch_pcg_restart<double>(const VecParams<double>&, cudaStream_t);
+template cudaError_t launch_pcg_restart<float>(const VecParams<float>&, cudaStream_t, bool);
+template cudaError_t launch_pcg_restart<double>(const VecParams<double>&, cudaStream_t, bool);
 
 template <typename T>
-cudaError_t launch_pcg_update(const VecParams<T>& p, cudaStream_t s) {
-  k_pcg_update<T><<<kVecBlocks, kVecThreads, 0, s>>>(p);
+cudaError_t launch_pcg_update(const VecParams<T>& p, cudaStream_t s, bool ext) {
+  if (ext)
+    k_pcg_update<T, true><<<kVecBlocks, kVecThreads, 0, s>>>(p);
+  else
+    k_pcg_update<T, false><<<kVecBlocks, kVecThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_pcg_init(const VecParams<T>& p, cudaStream_t s) {
-  k_pcg_init<T><<<kVecBlocks, kVecThreads, 0, s>>>(p);
+cudaError_t launch_pcg_init(const VecParams<T>& p, cudaStream_t s, bool ext) {
+  if (ext)
+    k_pcg_init<T, true><<<kVecBlocks, kVecThreads, 0, s>>>(p);
+  else
+    k_pcg_init<T, false><<<kVecBlocks, kVecThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
-template cudaError_t launch_pcg_update<double>(const VecParams<double>&, cudaStream_t);
-template cudaError_t launch_pcg_update<float>(const VecParams<float>&, cudaStream_t);
-template cudaError_t launch_pcg_init<double>(const VecParams<double>&, cudaStream_t);
-template cudaError_t launch_pcg_init<float>(const VecParams<float>&, cudaStream_t);
+template cudaError_t launch_pcg_update<double>(const VecParams<double>&, cudaStream_t, bool);
+template cudaError_t launch_pcg_update<float>(const VecParams<float>&, cudaStream_t, bool);
+template cudaError_t launch_pcg_init<double>(const VecParams<double>&, cudaStream_t, bool);
+template cudaError_t launch_pcg_init<float>(const VecParams<float>&, cudaStream_t, bool);
+
+template <typename T, typename Z>
+cudaError_t launch_pcg_rho(const T* r, const Z* z, T* zout, double zscale, const uint8_t* wm, int64_t n, PcgState* st,
+                           double* partial, cudaStream_t s) {
+  k_pcg_rho<T, Z><<<kVecBlocks, kVecThreads, 0, s>>>(r, z, zout, zscale, wm, n, st, partial);
+  return cudaGetLastError();
+}
+template cudaError_t launch_pcg_rho<double, double>(const double*, const double*, double*, double, const uint8_t*,
+                                                    int64_t, PcgState*, double*, cudaStream_t);
+template cudaError_t launch_pcg_rho<float, float>(const float*, const float*, float*, double, const uint8_t*, int64_t,
+                                                  PcgState*, double*, cudaStream_t);
+template cudaError_t launch_pcg_rho<double, float>(const double*, const float*, double*, double, const uint8_t*,
+                                                   int64_t, PcgState*, double*, cudaStream_t);
 
 // ---- small helpers ------------------------------------------------------------
 

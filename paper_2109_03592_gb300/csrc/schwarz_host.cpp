@@ -12,8 +12,10 @@
 // K removed).  The generalised eigenproblem K S = B S diag(lam), S^T B S = I,
 // is solved as the symmetric one for B^{-1/2} K B^{-1/2} (B is diagonal) by
 // cyclic Jacobi rotations.  On an axis-aligned box these local operators are
-// the exact principal submatrices of the assembled operator.
+// the exact principal submatrices of the assembled operator.  Two element
+// faces are neighbours when they have the same four vertices.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -21,6 +23,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "schwarz.h"
 #include "sem_internal.h"
 
 namespace sem {
@@ -123,29 +126,10 @@ void reference_stiffness(int N, std::vector<double>& w, std::vector<double>& Kre
 }  // namespace
 }  // namespace sem
 
-using namespace sem;
+namespace sem {
 
-extern "C" {
-
-sem_status sem_schwarz_fdm_1d(int N, double l, double l_lo, double l_hi, int dir_lo, int dir_hi, double* S_host,
-                              double* lam_host) {
-  if (N < 1 || N > kMaxN || !(l > 0.0) || !S_host || !lam_host) {
-    set_error("sem_schwarz_fdm_1d: need N in [1, 11], l > 0 and output arrays");
-    return SEM_ERR_INVALID;
-  }
-  std::vector<double> w, Kref;
-  reference_stiffness(N, w, Kref);
-  fdm_1d(N, w, Kref, l, l_lo, l_hi, dir_lo != 0, dir_hi != 0, S_host, lam_host);
-  return SEM_OK;
-}
-
-sem_status sem_schwarz_setup_host(int64_t E, int N, const int64_t* glo, const double* xyz,
-                                  const uint8_t* dirichlet_face, double* S_host, double* lam_host,
-                                  int64_t* n_distinct) {
-  if (E < 1 || N < 2 || N > kMaxN || !glo || !xyz || !dirichlet_face || !S_host || !lam_host) {
-    set_error("sem_schwarz_setup_host: need E >= 1, N in [2, 11] and non-null arrays");
-    return SEM_ERR_INVALID;
-  }
+sem_status fdm_tables(int64_t E, int N, const int64_t* glo, const double* xyz, const uint8_t* dirichlet_face,
+                      FdmTables& out) {
   const int n = N + 1, n2 = n * n, n3 = n2 * n;
   // mean element lengths along r, s, t: the mean over the n^2 GLL lines of the distance between their ends
   std::vector<double> L(3 * E);
@@ -171,16 +155,22 @@ sem_status sem_schwarz_setup_host(int64_t E, int N, const int64_t* glo, const do
       L[3 * e + a] = sum / (double)n2;
     }
   }
-  // face neighbours: two element faces are one face when their centre nodes share a global id
-  const int c = n / 2;
-  auto centre = [&](int f) {
-    const int end = (f % 2 == 0) ? 0 : N, a = f / 2;
-    return a == 0 ? end + n * c + n2 * c : (a == 1 ? c + n * end + n2 * c : c + n * c + n2 * end);
+  // face neighbours: two element faces are one face when they have the same
+  // four vertices (the sorted global ids of their corner nodes), whatever the
+  // orientation of the two elements
+  auto corner = [&](int a, int end, int u, int v) {
+    const int cu = u ? N : 0, cv = v ? N : 0;
+    return a == 0 ? end + n * cu + n2 * cv : (a == 1 ? cu + n * end + n2 * cv : cu + n * cv + n2 * end);
   };
-  std::unordered_map<int64_t, std::vector<std::pair<int64_t, int>>> owner;
-  owner.reserve((size_t)E * 3);
+  std::map<std::array<int64_t, 4>, std::vector<std::pair<int64_t, int>>> owner;
   for (int64_t e = 0; e < E; ++e)
-    for (int f = 0; f < 6; ++f) owner[glo[e * n3 + centre(f)]].push_back({e, f});
+    for (int f = 0; f < 6; ++f) {
+      const int a = f / 2, end = (f % 2 == 0) ? 0 : N;
+      std::array<int64_t, 4> key;
+      for (int q = 0; q < 4; ++q) key[q] = glo[e * n3 + corner(a, end, q & 1, q >> 1)];
+      std::sort(key.begin(), key.end());
+      owner[key].push_back({e, f});
+    }
   std::vector<double> nbl(6 * E, -1.0);
   for (const auto& kv : owner) {
     if (kv.second.size() != 2) continue;
@@ -192,25 +182,65 @@ sem_status sem_schwarz_setup_host(int64_t E, int N, const int64_t* glo, const do
   std::vector<double> w, Kref;
   reference_stiffness(N, w, Kref);
   using Key = std::tuple<double, double, double, int>;
-  std::map<Key, int64_t> seen;  // key -> first (element, direction) slot that holds it
+  std::map<Key, int32_t> seen;  // key -> row of the distinct tables
+  out.S.clear();
+  out.lam.clear();
+  out.sidx.assign(3 * E, 0);
   for (int64_t e = 0; e < E; ++e)
     for (int a = 0; a < 3; ++a) {
       const bool dlo = dirichlet_face[6 * e + 2 * a] != 0, dhi = dirichlet_face[6 * e + 2 * a + 1] != 0;
       const double llo = dlo ? 0.0 : nbl[6 * e + 2 * a], lhi = dhi ? 0.0 : nbl[6 * e + 2 * a + 1];
       const Key key{L[3 * e + a], llo, lhi, (dlo ? 1 : 0) | (dhi ? 2 : 0)};
-      const int64_t slot = 3 * e + a;
-      double* S = S_host + slot * n2;
-      double* lam = lam_host + slot * n;
       auto it = seen.find(key);
-      if (it != seen.end()) {
-        std::memcpy(S, S_host + it->second * n2, sizeof(double) * n2);
-        std::memcpy(lam, lam_host + it->second * n, sizeof(double) * n);
-      } else {
-        fdm_1d(N, w, Kref, L[3 * e + a], llo, lhi, dlo, dhi, S, lam);
-        seen.emplace(key, slot);
+      if (it == seen.end()) {
+        const int32_t row = (int32_t)seen.size();
+        out.S.resize((size_t)(row + 1) * n2);
+        out.lam.resize((size_t)(row + 1) * n);
+        fdm_1d(N, w, Kref, L[3 * e + a], llo, lhi, dlo, dhi, out.S.data() + (size_t)row * n2,
+               out.lam.data() + (size_t)row * n);
+        it = seen.emplace(key, row).first;
       }
+      out.sidx[3 * e + a] = it->second;
     }
-  if (n_distinct) *n_distinct = (int64_t)seen.size();
+  out.nd = (int64_t)seen.size();
+  return SEM_OK;
+}
+
+}  // namespace sem
+
+using namespace sem;
+
+extern "C" {
+
+sem_status sem_schwarz_fdm_1d(int N, double l, double l_lo, double l_hi, int dir_lo, int dir_hi, double* S_host,
+                              double* lam_host) {
+  if (N < 1 || N > kMaxN || !(l > 0.0) || !S_host || !lam_host) {
+    set_error("sem_schwarz_fdm_1d: need N in [1, 11], l > 0 and output arrays");
+    return SEM_ERR_INVALID;
+  }
+  std::vector<double> w, Kref;
+  reference_stiffness(N, w, Kref);
+  fdm_1d(N, w, Kref, l, l_lo, l_hi, dir_lo != 0, dir_hi != 0, S_host, lam_host);
+  return SEM_OK;
+}
+
+sem_status sem_schwarz_setup_host(int64_t E, int N, const int64_t* glo, const double* xyz,
+                                  const uint8_t* dirichlet_face, double* S_host, double* lam_host,
+                                  int64_t* n_distinct) {
+  if (E < 1 || N < 1 || N > kMaxN || !glo || !xyz || !dirichlet_face || !S_host || !lam_host) {
+    set_error("sem_schwarz_setup_host: need E >= 1, N in [1, 11] and non-null arrays");
+    return SEM_ERR_INVALID;
+  }
+  const int n = N + 1, n2 = n * n;
+  FdmTables t;
+  sem_status st = fdm_tables(E, N, glo, xyz, dirichlet_face, t);
+  if (st != SEM_OK) return st;
+  for (int64_t slot = 0; slot < 3 * E; ++slot) {
+    const int32_t row = t.sidx[slot];
+    std::memcpy(S_host + slot * n2, t.S.data() + (size_t)row * n2, sizeof(double) * n2);
+    std::memcpy(lam_host + slot * n, t.lam.data() + (size_t)row * n, sizeof(double) * n);
+  }
+  if (n_distinct) *n_distinct = t.nd;
   return SEM_OK;
 }
 

@@ -84,7 +84,8 @@ struct sem_mesh {
   int64_t n_seg = 0, n_seg_points = 0;
   size_t dev_bytes = 0;
 
-  std::vector<int64_t> glo;  // host copy of the global ids
+  std::vector<int64_t> glo;    // host copy of the global ids
+  std::vector<uint8_t> dface;  // host copy of the Dirichlet face flags [E][6]
 
   // device arrays (library-owned)
   double* xyz = nullptr;     // [E][3][n3]

@@ -117,8 +117,8 @@ cudaError_t ax64_exact(const sem_mesh* m, const double* u, double* w, double h1,
   return launch_ax_f64(m->N, m->ax_var[0], false, a, s, nullptr);
 }
 
-static cudaError_t ax32(const sem_mesh* m, const float* u, float* w, double h1, double h2, bool fused,
-                        const float* z, float* p, PcgState* st, double* part, cudaStream_t s) {
+cudaError_t ax32(const sem_mesh* m, const float* u, float* w, double h1, double h2, bool fused, const float* z,
+                 float* p, PcgState* st, double* part, cudaStream_t s) {
   AxParams<float> a{u, w, m->opG32(), m->opB32(), m->D32, (float)h1, (float)h2, h2 != 0.0, m->E, z, p, st, part,
                     m->dev_err};
   int var = m->ax_var[1];
@@ -352,7 +352,7 @@ static sem_status get_graph(sem_mesh* m, Workspace* ws, bool fp32, double h1, do
 }
 
 // Replay the chunk graph until the device reports done.
-static sem_status run_chunks(Workspace* ws, const GraphSlot& gs, int maxit, PcgState& out) {
+sem_status run_chunks(Workspace* ws, const GraphSlot& gs, int maxit, PcgState& out) {
   cudaGraphExec_t g = gs.exec;
   const int max_chunks = maxit / kChunk + 3;
   for (int c = 0; c < max_chunks; ++c) {

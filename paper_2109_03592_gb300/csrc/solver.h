@@ -32,11 +32,17 @@ void free_ws(Workspace* ws);  // a workspace from alloc_ws that is not a mesh's
 // FP64 local operator with the mesh's tuned kernel (native or double-float).
 // w = A_L u with the native FP64 kernel (exact FP64 arithmetic)
 cudaError_t ax64_exact(const sem_mesh* m, const double* u, double* w, double h1, double h2, cudaStream_t s);
+// FP32 local operator with the mesh's tuned kernel (fused: the CG prologue and <p, A_L p>).
+cudaError_t ax32(const sem_mesh* m, const float* u, float* w, double h1, double h2, bool fused, const float* z,
+                 float* p, PcgState* st, double* part, cudaStream_t s);
 cudaError_t ax64(const sem_mesh* m, const double* u, double* w, double h1, double h2, bool fused, const double* z,
                  double* p, PcgState* st, double* part, cudaStream_t s);
 // Write a fresh PcgState (tol, maxit, done) to ws->st / read it back (both synchronise ws->s).
 sem_status put_state(Workspace* ws, double tol, int maxit, int done);
 sem_status read_state(Workspace* ws, PcgState& out);
+// Replay a captured chunk graph until the device state reports done (double-buffered polling).
+sem_status run_chunks(Workspace* ws, const GraphSlot& gs, int maxit, PcgState& out);
+constexpr int kSolveChunk = 8;  // CG iterations per graph launch
 
 // w = A_L u with the mesh's tuned kernel for `prec` (SEM_FP64 or SEM_FP32).
 sem_status apply_local(const sem_mesh* m, const void* u, void* w, double h1, double h2, sem_prec prec,

@@ -58,6 +58,11 @@ class SolveResult(C.Structure):
                     status=self.status)
 
 
+class SchwarzInfo(C.Structure):
+    _fields_ = [("n_distinct", C.c_int64), ("n_coarse", C.c_int64), ("coarse", C.c_int), ("dev_bytes", C.c_size_t),
+                ("setup_ms", C.c_double)]
+
+
 class ServerOpts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_slots", C.c_int), ("max_queue", C.c_int),
                 ("device", C.c_int), ("batch", C.c_int)]
@@ -114,6 +119,11 @@ SIGNATURES = {
     "sem_pressure_basis": (C.c_int, [C.c_int, _P, _P, _P, _P]),
     "sem_schwarz_fdm_1d": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, _P, _P]),
     "sem_schwarz_setup_host": (C.c_int, [C.c_int64, C.c_int, _P, _P, _P, _P, _P, C.POINTER(C.c_int64)]),
+    "sem_schwarz_create": (C.c_int, [_P, C.c_double, C.c_double, C.c_int, C.POINTER(_P)]),
+    "sem_schwarz_destroy": (C.c_int, [_P]),
+    "sem_schwarz_info": (C.c_int, [_P, C.POINTER(SchwarzInfo)]),
+    "sem_schwarz_apply": (C.c_int, [_P, _P, _P, C.c_int, _P]),
+    "sem_schwarz_solve": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
     "sem_pressure_info": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "sem_pressure_factors": (C.c_int, [_P, _P, _P]),
     "sem_pressure_grad": (C.c_int, [_P, _P, _P, _P]),
@@ -509,6 +519,59 @@ class Projection:
     def close(self):
         if getattr(self, "_h", None):
             lib().sem_proj_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+SCHWARZ_COARSE = 1
+SCHWARZ_DENSE_COARSE_MAX = 8192
+
+
+class Schwarz:
+    """Overlapping Schwarz preconditioner of one mesh and operator
+    (sem_schwarz_*): fast-diagonalisation local solves on the elements with
+    the symmetric mult^-1/2 weights, plus the trilinear coarse grid."""
+
+    def __init__(self, mesh, h1=1.0, h2=0.0, coarse=True):
+        h = C.c_void_p()
+        _check(lib().sem_schwarz_create(mesh._h, float(h1), float(h2), SCHWARZ_COARSE if coarse else 0, C.byref(h)),
+               "sem_schwarz_create")
+        self._h, self.mesh, self.h1, self.h2 = h, mesh, float(h1), float(h2)
+
+    def info(self):
+        i = SchwarzInfo()
+        _check(lib().sem_schwarz_info(self._h, C.byref(i)), "sem_schwarz_info")
+        return {"n_distinct": i.n_distinct, "n_coarse": i.n_coarse, "coarse": bool(i.coarse),
+                "dev_bytes": i.dev_bytes, "setup_ms": i.setup_ms}
+
+    def apply(self, r, z, prec=FP64, stream=None):
+        import torch
+        dt = torch.float32 if prec == FP32 else torch.float64
+        n = self.mesh.n_local
+        _check(lib().sem_schwarz_apply(self._h, _dptr(r, dt, n), _dptr(z, dt, n), int(prec), _stream(stream)),
+               "sem_schwarz_apply")
+
+    def solve(self, b, x, stream=None, check=False, **opts):
+        import torch
+        opts.setdefault("h1", self.h1)
+        opts.setdefault("h2", self.h2)
+        o = _opts(**opts)
+        r = SolveResult()
+        n = self.mesh.n_local
+        st = lib().sem_schwarz_solve(self._h, _dptr(b, torch.float64, n), _dptr(x, torch.float64, n), C.byref(o),
+                                     C.byref(r), _stream(stream))
+        if st not in (SEM_OK, SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN) or (check and st != SEM_OK):
+            _check(st, "sem_schwarz_solve")
+        return r.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sem_schwarz_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -74,5 +74,51 @@ def test_setup_rejects_invalid_input(sem):
     m_ = mesh.box(1, 1, 1, 1)
     glo, _ = numbering.global_numbering(m_)
     with pytest.raises(sem.SemError) as ei:
-        sem.schwarz_setup_host(1, glo, m_.xyz, m_.dirichlet_face)
+        sem.schwarz_setup_host(12, glo, m_.xyz, m_.dirichlet_face)  # orders above 11 are not compiled
     assert ei.value.status == sem.SEM_ERR_INVALID
+
+
+def flipped_pair(N):
+    """Two elements sharing the face x = 1: element 0 is [0, 1]^3 with local
+    axes along x, y, z; element 1 is [1, 2.5] x [0, 1] x [0, 1] turned half a
+    turn about the x axis (local s along -y, t along -z, still right-handed).
+    The shared face is i = N of element 0 and i = 0 of element 1, with its two
+    in-face directions reversed between them.  Every other face is Dirichlet."""
+    xi, _ = mesh.gll.nodes_weights(N)
+    n = N + 1
+    u = (1.0 + xi) / 2
+    xyz = np.empty((2, 3, n, n, n))
+    xyz[0, 0] = u[None, None, :]
+    xyz[0, 1] = u[None, :, None]
+    xyz[0, 2] = u[:, None, None]
+    xyz[1, 0] = (1.0 + 1.5 * u)[None, None, :]
+    xyz[1, 1] = (1.0 - u)[None, :, None]
+    xyz[1, 2] = (1.0 - u)[:, None, None]
+    dface = np.ones((2, 6), dtype=bool)
+    dface[0, 1] = dface[1, 0] = False
+    return mesh.Mesh(N, xyz, dface)
+
+
+@pytest.mark.parametrize("N", [3, 4, 7])
+def test_faces_match_by_their_vertices_in_any_orientation(sem, N):
+    """The face-neighbour rule pairs two faces with the same four vertices
+    whatever the elements' relative orientation.  At odd N the centre-most
+    face node of one element is not that of the other here (reversed in-face
+    directions), so a rule through that node would miss the pair and drop the
+    neighbour's end entries; the oracle and the host set-up must both find it
+    (element 1 is longer, so the neighbour's length changes element 0's r
+    operator)."""
+    m_ = flipped_pair(N)
+    prob = solver.Problem(m_)
+    nb = schwarz.face_neighbours(prob)
+    assert tuple(nb[0, 1]) == (1, 0) and tuple(nb[1, 0]) == (0, 1)
+    assert (nb[0, [0, 2, 3, 4, 5]] == -1).all() and (nb[1, 1:] == -1).all()
+    sw = schwarz.Schwarz(prob, coarse=False)
+    # element 0's r operator: Dirichlet at i = 0, the neighbour's length 1.5 at i = N
+    _same_pair(sw.S[0, 0], sw.lam[0, 0], *schwarz.fdm_1d(N, 1.0, None, 1.5, True, False))
+    alone = schwarz.fdm_1d(N, 1.0, None, None, True, False)  # the same end with no neighbour found
+    assert not np.allclose(sw.lam[0, 0], alone[1])
+    S, lam, _ = sem.schwarz_setup_host(N, prob.glo, m_.xyz, m_.dirichlet_face)
+    for e in range(2):
+        for a in range(3):
+            _same_pair(S[e, a], lam[e, a], sw.S[e, a], sw.lam[e, a])
