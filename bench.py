@@ -242,41 +242,65 @@ def run_reference(args):
 
 def serving_stream(count, rate, seed=4, log2_e=(9.0, 15.0)):
     """Request stream through the batching server: Poisson arrivals at `rate`
-    per second; box or pipe meshes with E log-uniform in [512, 32768]; N in
+    per second (rate = inf: all at once, which measures the saturation
+    throughput); box or pipe meshes with E log-uniform in [512, 32768]; N in
     {5, 7, 9}; Poisson or Helmholtz (h2 log-uniform in [1e-2, 1e2]); mixed
-    precision to 1e-10.  Latency = submit -> result visible to poll."""
+    precision to 1e-10.  Latency = submit -> result visible to poll, with the
+    server's breakdown of each request (queue, mesh set-up, wait for a batch
+    slot, solve; sem_server_poll_timed)."""
     import numpy as np
     import paper_2109_03592_gb300 as sem
     from sem_inputs import serving
-    stream = serving.request_stream(seed=seed, count=count, rate=rate, log2_e=log2_e)
+    stream = serving.request_stream(seed=seed, count=count, rate=rate if math.isfinite(rate) else 1.0,
+                                    log2_e=log2_e)
     srv = sem.Server(max_slots=8)
     pending = {}
     t0 = time.perf_counter()
     for req in stream:
-        now = time.perf_counter() - t0
-        if req["arrival"] > now:
-            time.sleep(req["arrival"] - now)
+        if math.isfinite(rate):
+            now = time.perf_counter() - t0
+            if req["arrival"] > now:
+                time.sleep(req["arrival"] - now)
         d = req["desc"]
         n = d["N"] + 1
         E = d["nx"] * d["ny"] * d["nz"] if d["kind"] == "box" else d["nc"] * (d["nc"] + 4 * d["nr"]) * d["nzp"]
         f = np.random.default_rng(req["seed"]).standard_normal(E * n ** 3)
         rid = srv.submit(d, f, tol=1e-10, h1=1.0, h2=req["h2"], prec=sem.MIXED)
-        pending[rid] = (time.perf_counter(), E * n ** 3)
-    lat, worst = [], 0.0
-    for rid, (ts, nl) in pending.items():
-        st, x, res = srv.poll(rid, timeout_ms=-1)
+        pending[rid] = E * n ** 3
+    submit_s = time.perf_counter() - t0
+    lat, worst, phases = [], 0.0, {"queue_ms": [], "setup_ms": [], "wait_ms": [], "solve_ms": []}
+    for rid in pending:
+        st, x, res = srv.poll(rid, timeout_ms=-1, timing=True)
         if st != sem.SEM_OK:
             raise RuntimeError(f"serving request failed: {st} {res}")
-        lat.append(time.perf_counter() - ts)
+        tm = res["timing"]
+        lat.append(tm["total_ms"])
+        for k in phases:
+            phases[k].append(tm[k])
         worst = max(worst, res["rel_res"])
     wall = time.perf_counter() - t0
     srv.close()
-    lat_ms = sorted(v * 1e3 for v in lat)
-    return {"requests": count, "arrival_rate_per_s": rate, "throughput_solves_per_s": count / wall,
-            "latency_ms": {"p50": pct(lat_ms, 50), "p99": pct(lat_ms, 99), "max": lat_ms[-1]},
+    return {"requests": count, "arrival_rate_per_s": rate if math.isfinite(rate) else "all at once",
+            "offered_rate_per_s": count / submit_s if submit_s > 0 else None,
+            "throughput_solves_per_s": count / wall,
+            "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": max(lat)},
+            "breakdown_ms_p50": {k: pct(v, 50) for k, v in phases.items()},
+            "breakdown_ms_p99": {k: pct(v, 99) for k, v in phases.items()},
             "max_rel_res": worst, "mode": "batched per order (one CUDA graph per order per step)",
             "mix": (f"box/pipe, E log-uniform in [{2 ** log2_e[0]:.0f}, {2 ** log2_e[1]:.0f}], N in {{5,7,9}}, "
                     "Poisson/Helmholtz, tol 1e-10")}
+
+
+def serving_sweep(count, seed=4):
+    """The serving configuration's rate sweep: the saturation throughput from
+    a burst of `count` requests, then Poisson streams of `count` requests at
+    0.5x, 1x and 2x that rate."""
+    sat = serving_stream(count, float("inf"), seed=seed)
+    lam = sat["throughput_solves_per_s"]
+    out = {"saturation": sat, "rates": []}
+    for k, mult in enumerate((0.5, 1.0, 2.0)):
+        out["rates"].append(dict(serving_stream(count, mult * lam, seed=seed + 1 + k), rate_over_saturation=mult))
+    return out
 
 
 # ---------------------------------------------------------------- projection leg
@@ -691,7 +715,8 @@ def run_gpu(args):
 
     serving = None
     if not args.no_serving:
-        serving = serving_stream(args.serving_requests, args.serving_rate)
+        serving = (serving_sweep(args.serving_requests) if args.serving_sweep
+                   else serving_stream(args.serving_requests, args.serving_rate))
     proj = None
     if not args.no_projection:
         proj = projection_leg()
@@ -792,6 +817,8 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the E = 1,048,576 and N = 11 solves")
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--serving-rate", type=float, default=2.0)
+    ap.add_argument("--serving-sweep", action="store_true",
+                    help="saturation burst, then streams at 0.5x, 1x, 2x the saturation rate")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

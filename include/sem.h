@@ -508,6 +508,19 @@ sem_status sem_server_submit(sem_server* srv, const sem_mesh_desc* desc, const d
 sem_status sem_server_poll(sem_server* srv, uint64_t req_id, int timeout_ms, double* x_host,
                            sem_solve_result* result);
 
+/* Where a request's latency went, in milliseconds of host wall time:
+ * queue_ms: submit until a slot takes it (slots and HBM budget); setup_ms:
+ * building its mesh and b = mask QQ^T (B f); wait_ms: until its engine admits
+ * it into the running batch (0 when solved alone); solve_ms: until its result
+ * is copied out; total_ms: submit until the result is visible to poll. */
+typedef struct {
+  double queue_ms, setup_ms, wait_ms, solve_ms, total_ms;
+} sem_request_timing;
+
+/* sem_server_poll that also fills timing (nullable) for the completed request. */
+sem_status sem_server_poll_timed(sem_server* srv, uint64_t req_id, int timeout_ms, double* x_host,
+                                 sem_solve_result* result, sem_request_timing* timing);
+
 /* Cancel a queued request (one already running finishes). */
 sem_status sem_server_cancel(sem_server* srv, uint64_t req_id);
 

@@ -47,7 +47,15 @@ struct Request {
   sem_mesh* mesh = nullptr;
   double *f_dev = nullptr, *b_dev = nullptr, *x_dev = nullptr;
   sem::batch::Req breq;
+  // host wall-clock marks: submitted, taken by a slot, staged (mesh and b
+  // built), solve started (admitted into a batch, or at once), completed
+  using Clock = std::chrono::steady_clock;
+  Clock::time_point t_submit, t_admit, t_staged, t_solve, t_done;
 };
+
+double ms_between(std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
 
 int64_t local_points(const sem_mesh_desc& d) {
   const int64_t n = d.N + 1;
@@ -107,6 +115,7 @@ bool batchable(const Request& q) {
 void complete(sem_server* srv, const std::shared_ptr<Request>& q, sem_status st) {
   {
     std::lock_guard<std::mutex> lk(srv->mu);
+    q->t_done = Request::Clock::now();
     q->status = st;
     if (st != SEM_OK && q->error.empty()) q->error = sem_last_error();
     q->done = true;
@@ -137,6 +146,7 @@ void engine_main(sem_server* srv, EngineThread* et) {
     }
     for (auto& q : incoming) {
       sem_status st = init_st;
+      q->t_solve = Request::Clock::now();
       if (st == SEM_OK) st = eng.add(&q->breq);
       if (st != SEM_OK) {
         q->x.clear();
@@ -205,6 +215,7 @@ sem_status stage_for_batch(sem_server* srv, const std::shared_ptr<Request>& q, c
   if (q->breq.o.maxit <= 0) q->breq.o.maxit = 20000;
   if (!(q->breq.o.delta > 0.0)) q->breq.o.delta = 0.1;
   q->breq.out = &q->res;
+  q->t_staged = Request::Clock::now();
   {
     std::lock_guard<std::mutex> lk(srv->mu);
     EngineThread* et = nullptr;
@@ -244,6 +255,11 @@ sem_status run_request(sem_server* srv, Request& q, cudaStream_t s) {
     st = sem::cuda_fail(e, "server buffers");
   } else {
     st = sem_rhs(m, f, b, s);
+    if (st == SEM_OK) {
+      const cudaError_t e2 = cudaStreamSynchronize(s);
+      if (e2 != cudaSuccess) st = sem::cuda_fail(e2, "server rhs");
+    }
+    q.t_staged = q.t_solve = Request::Clock::now();
     if (st == SEM_OK) st = sem_pcg_solve(m, b, x, &q.opts, &q.res, s);
     if (st == SEM_OK || st == SEM_ERR_NOT_CONVERGED || st == SEM_ERR_BREAKDOWN) {
       q.x.resize(q.n_local);
@@ -275,6 +291,7 @@ void worker_main(sem_server* srv) {
         });
         if (it != srv->queue.end()) {
           q = *it;
+          q->t_admit = Request::Clock::now();
           srv->queue.erase(it);
           srv->in_use += q->footprint;
           srv->running++;
@@ -374,6 +391,7 @@ sem_status sem_server_submit(sem_server* srv, const sem_mesh_desc* desc, const d
   q->f.assign(f_host, f_host + q->n_local);
   {
     std::lock_guard<std::mutex> lk(srv->mu);
+    q->t_submit = Request::Clock::now();
     if (srv->stopping) {
       sem::set_error("sem_server_submit: server is stopping");
       return SEM_ERR_INVALID;
@@ -390,6 +408,11 @@ sem_status sem_server_submit(sem_server* srv, const sem_mesh_desc* desc, const d
 
 sem_status sem_server_poll(sem_server* srv, uint64_t req_id, int timeout_ms, double* x_host,
                            sem_solve_result* result) {
+  return sem_server_poll_timed(srv, req_id, timeout_ms, x_host, result, nullptr);
+}
+
+sem_status sem_server_poll_timed(sem_server* srv, uint64_t req_id, int timeout_ms, double* x_host,
+                                 sem_solve_result* result, sem_request_timing* timing) {
   if (!srv) {
     sem::set_error("sem_server_poll: null server");
     return SEM_ERR_INVALID;
@@ -408,6 +431,17 @@ sem_status sem_server_poll(sem_server* srv, uint64_t req_id, int timeout_ms, dou
     return SEM_ERR_TIMEOUT;
   if (x_host && !q->x.empty()) std::memcpy(x_host, q->x.data(), q->x.size() * sizeof(double));
   if (result) *result = q->res;
+  if (timing) {
+    const auto now = Request::Clock::now();
+    const bool ran = q->t_admit.time_since_epoch().count() != 0;  // not cancelled while queued
+    const bool staged = q->t_staged.time_since_epoch().count() != 0;
+    const bool solved = q->t_solve.time_since_epoch().count() != 0;
+    timing->queue_ms = ran ? ms_between(q->t_submit, q->t_admit) : ms_between(q->t_submit, q->t_done);
+    timing->setup_ms = ran && staged ? ms_between(q->t_admit, q->t_staged) : 0.0;
+    timing->wait_ms = staged && solved ? ms_between(q->t_staged, q->t_solve) : 0.0;
+    timing->solve_ms = solved ? ms_between(q->t_solve, q->t_done) : 0.0;
+    timing->total_ms = ms_between(q->t_submit, now);
+  }
   srv->reqs.erase(req_id);
   if (q->status != SEM_OK && !q->error.empty()) sem::set_error(q->error);
   return q->status;
@@ -423,6 +457,7 @@ sem_status sem_server_cancel(sem_server* srv, uint64_t req_id) {
   srv->queue.erase(qit);
   it->second->status = SEM_ERR_CANCELLED;
   it->second->done = true;
+  it->second->t_done = Request::Clock::now();
   srv->cancelled++;
   srv->cv_done.notify_all();
   return SEM_OK;
@@ -450,6 +485,7 @@ sem_status sem_server_destroy(sem_server* srv) {
     for (auto& q : srv->queue) {
       q->status = SEM_ERR_CANCELLED;
       q->done = true;
+      q->t_done = Request::Clock::now();
       srv->cancelled++;
     }
     srv->queue.clear();

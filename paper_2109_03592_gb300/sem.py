@@ -63,6 +63,11 @@ class SchwarzInfo(C.Structure):
                 ("setup_ms", C.c_double)]
 
 
+class RequestTiming(C.Structure):
+    _fields_ = [("queue_ms", C.c_double), ("setup_ms", C.c_double), ("wait_ms", C.c_double),
+                ("solve_ms", C.c_double), ("total_ms", C.c_double)]
+
+
 class ServerOpts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_slots", C.c_int), ("max_queue", C.c_int),
                 ("device", C.c_int), ("batch", C.c_int)]
@@ -102,6 +107,8 @@ SIGNATURES = {
     "sem_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(_P)]),
     "sem_server_submit": (C.c_int, [_P, C.POINTER(MeshDesc), _P, C.POINTER(SolveOpts), C.POINTER(C.c_uint64)]),
     "sem_server_poll": (C.c_int, [_P, C.c_uint64, C.c_int, _P, C.POINTER(SolveResult)]),
+    "sem_server_poll_timed": (C.c_int, [_P, C.c_uint64, C.c_int, _P, C.POINTER(SolveResult),
+                                        C.POINTER(RequestTiming)]),
     "sem_server_cancel": (C.c_int, [_P, C.c_uint64]),
     "sem_server_stats_get": (C.c_int, [_P, C.POINTER(ServerStats)]),
     "sem_server_destroy": (C.c_int, [_P]),
@@ -601,15 +608,22 @@ class Server:
                "sem_server_submit")
         return rid.value
 
-    def poll(self, rid, timeout_ms=-1, n_local=None):
-        """Returns (status, x or None, result dict); status SEM_ERR_TIMEOUT if not done."""
+    def poll(self, rid, timeout_ms=-1, n_local=None, timing=False):
+        """Returns (status, x or None, result dict); status SEM_ERR_TIMEOUT if
+        not done.  With timing=True the result dict also carries the request's
+        latency breakdown (sem_server_poll_timed) under "timing"."""
         r = SolveResult()
+        tm = RequestTiming()
         x = np.empty(n_local, dtype=np.float64) if n_local else None
-        st = lib().sem_server_poll(self._h, C.c_uint64(rid), int(timeout_ms),
-                                   x.ctypes.data if x is not None else None, C.byref(r))
+        st = lib().sem_server_poll_timed(self._h, C.c_uint64(rid), int(timeout_ms),
+                                         x.ctypes.data if x is not None else None, C.byref(r),
+                                         C.byref(tm) if timing else None)
         if st in (SEM_ERR_INVALID, SEM_ERR_NOT_FOUND, SEM_ERR_CUDA, SEM_ERR_OOM):
             _check(st, "sem_server_poll")
-        return st, (x if st not in (SEM_ERR_TIMEOUT,) else None), r.as_dict()
+        out = r.as_dict()
+        if timing and st != SEM_ERR_TIMEOUT:
+            out["timing"] = {k: getattr(tm, k) for k, _ in RequestTiming._fields_}
+        return st, (x if st not in (SEM_ERR_TIMEOUT,) else None), out
 
     def cancel(self, rid):
         return lib().sem_server_cancel(self._h, C.c_uint64(rid))
