@@ -436,7 +436,10 @@ sem_status sem_schwarz_setup_host(int64_t E, int N, const int64_t* glo, const do
  *   not Dirichlet; R_0 r = sum over global nodes of phi r, A_0 = R_0 A R_0^T
  *   (Galerkin), solved through its inverse, formed once on the device
  *   (Gauss-Jordan, SPD), when A_0 has at most SEM_SCHWARZ_DENSE_COARSE_MAX
- *   unknowns; with more the coarse term is left out (sem_schwarz_info). */
+ *   unknowns; larger A_0 are solved approximately by a fixed symmetric
+ *   two-level cycle (Chebyshev smoothing in diag(A_0)^-1 A_0, and the exact
+ *   correction on aggregates of about 64 vertices grouped by coordinate
+ *   bisection), so M stays a fixed SPD operator. */
 typedef struct sem_schwarz sem_schwarz;
 #define SEM_SCHWARZ_COARSE 1             /* flags: include the coarse-grid term */
 #define SEM_SCHWARZ_DENSE_COARSE_MAX 8192
@@ -444,7 +447,7 @@ typedef struct sem_schwarz sem_schwarz;
 typedef struct {
   int64_t n_distinct; /* distinct 1D eigenproblems solved on the host */
   int64_t n_coarse;   /* coarse unknowns (free element vertices) */
-  int coarse;         /* 1 if the coarse term is applied */
+  int coarse;         /* coarse term: 0 none, 1 dense inverse of A_0, 2 two-level cycle */
   size_t dev_bytes;   /* device memory held by the preconditioner (solver workspace excluded) */
   double setup_ms;    /* wall time of sem_schwarz_create */
 } sem_schwarz_info_t;

@@ -17,6 +17,7 @@
 // contractions never touch shared memory; r and s go through two padded n^3
 // arrays per element.  Per point 6n multiply-adds (n per contraction).
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.h"
 #include "sem_internal.h"
@@ -26,15 +27,54 @@ namespace sem {
 
 namespace {
 
+// Shared-memory layout of one element's n^3 values for the line-based local
+// solve.  Each contraction has a thread per line of its direction: r-lines
+// (fixed j, k), s-lines (fixed i, k) and t-lines (fixed i, j), so the three
+// access patterns of a warp are (j, k), (i, k) and (i, j) varying with the
+// third index fixed.  n = 8, FP32: rows of 8, planes padded to 72, and i
+// XOR-swizzled by f(j, k) = (2k + j / 4) mod 8, which puts the 32 lanes of all
+// three patterns on 32 distinct banks.  Other cases: rows padded to n + 1 and
+// planes to n (n + 1) + 1.
+template <int n, typename T>
+struct FdmLay {
+  static constexpr bool swz = (n == 8) && sizeof(T) == 4;
+  static constexpr int RP = swz ? 8 : n + 1;
+  static constexpr int PL = swz ? 72 : n * (n + 1) + 1;
+  static constexpr int size = n * PL;
+  __device__ static __forceinline__ int idx(int i, int j, int k) {
+    if constexpr (swz) return k * PL + j * RP + (i ^ ((2 * k + (j >> 2)) & 7));
+    return k * PL + j * RP + i;
+  }
+};
+
+// out[c] = sum_l S[l][c] x[l] (trans = false) or sum_l S[c][l] x[l] (trans =
+// true) for the n x n matrix S in shared memory, rows read as broadcasts.
+template <int n, typename T, bool TRANS>
+__device__ __forceinline__ void line_contract(const T* __restrict__ S, const T (&x)[n], T (&out)[n]) {
+#pragma unroll
+  for (int c = 0; c < n; ++c) out[c] = T(0);
+  if constexpr (!TRANS) {
+#pragma unroll
+    for (int l = 0; l < n; ++l)
+#pragma unroll
+      for (int c = 0; c < n; ++c) out[c] += S[l * n + c] * x[l];
+  } else {
+#pragma unroll
+    for (int c = 0; c < n; ++c)
+#pragma unroll
+      for (int l = 0; l < n; ++l) out[c] += S[c * n + l] * x[l];
+  }
+}
+
 template <int N, typename T, int EPB>
 __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_fdm(const FdmParams<T> P) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
-  constexpr int RP = n + 1, PL = n * RP;
+  using L = FdmLay<n, T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sS = reinterpret_cast<T*>(smem_raw);  // [EPB][3][n][n]: S_r, S_s, S_t (row l, column = eigenvector)
   T* sL = sS + EPB * 3 * n2;               // [EPB][3][n]
-  T* sa = sL + EPB * 3 * n;                // [EPB][n][PL]
-  T* sb = sa + EPB * n * PL;
+  T* sX = sL + EPB * 3 * n;                // [EPB][L::size]
+  T* sR = sX + EPB * L::size;              // [EPB][8][n^2]: coarse restriction, per column (P.rc only)
   __shared__ int sdone;
   const int tid = threadIdx.x;
   if (P.st) {
@@ -42,101 +82,115 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_fdm(const FdmParams<T
     __syncthreads();
     if (sdone) return;
   }
-  const int le = tid / n2, ij = tid - le * n2, i = ij % n, j = ij / n;
+  const int le = tid / n2, q = tid - le * n2;
+  const int a = q % n, b = q / n;  // this thread's line: (a, b) = the two fixed indices
   const int64_t e = (int64_t)blockIdx.x * EPB + le;
   const bool act = e < P.E;
   T* Se = sS + le * 3 * n2;
   T* Le = sL + le * 3 * n;
-  T* A = sa + le * n * PL;
-  T* Bm = sb + le * n * PL;
+  T* X = sX + le * L::size;
   if (act) {
-    for (int q = ij; q < 3 * n2; q += n2) {
-      const int d = q / n2;
-      Se[q] = P.S[(int64_t)P.sidx[3 * e + d] * n2 + (q - d * n2)];
+    for (int t = q; t < 3 * n2; t += n2) {
+      const int d = t / n2;
+      Se[t] = P.S[(int64_t)P.sidx[3 * e + d] * n2 + (t - d * n2)];
     }
-    for (int q = ij; q < 3 * n; q += n2) {
-      const int d = q / n;
-      Le[q] = P.lam[(int64_t)P.sidx[3 * e + d] * n + (q - d * n)];
+    for (int t = q; t < 3 * n; t += n2) {
+      const int d = t / n;
+      Le[t] = P.lam[(int64_t)P.sidx[3 * e + d] * n + (t - d * n)];
     }
   }
-  const int64_t base = e * n3 + ij;
+  // W r, coalesced: thread q holds point (i, j) = (a, b) of every k-plane
+  const int64_t base = e * n3 + q;
   T wk[n];
   if (act) {
+    T t0 = T(0), t1 = T(0);  // coarse restriction of this column: sum_k f_b(xi_k) r / mult
 #pragma unroll
     for (int k = 0; k < n; ++k) {
       wk[k] = P.wtab[P.wm[base + k * n2] & 0x7f];
-      A[k * PL + j * RP + i] = wk[k] * P.r[base + k * n2];
+      const T wr = wk[k] * P.r[base + k * n2];
+      X[L::idx(a, b, k)] = wr;
+      if (P.rc) {
+        const T rm = wk[k] * wr;  // r / mult
+        t0 += P.ftab[k] * rm;
+        t1 += P.ftab[n + k] * rm;
+      }
+    }
+    if (P.rc) {
+      T* R = sR + le * 8 * n2;
+      const T fa[2] = {P.ftab[a], P.ftab[n + a]}, fb[2] = {P.ftab[b], P.ftab[n + b]};
+#pragma unroll
+      for (int v = 0; v < 8; ++v) R[v * n2 + q] = fa[v & 1] * fb[(v >> 1) & 1] * ((v >> 2) & 1 ? t1 : t0);
     }
   }
   __syncthreads();
-  // forward: (S_t^T (x) S_s^T (x) S_r^T), r first
+  if (P.rc && act) {  // one thread per element vertex: the element's columns in order
+    for (int v = q; v < 8; v += n2) {
+      const T* R = sR + le * 8 * n2 + v * n2;
+      T sum = T(0);
+      for (int c = 0; c < n2; ++c) sum += R[c];
+      P.rc[8 * e + v] = (double)sum;
+    }
+  }
+  T x[n], y[n];
+  // forward r: line (j, k) = (a, b)
   if (act) {
 #pragma unroll
-    for (int k = 0; k < n; ++k) {
-      T s = T(0);
+    for (int l = 0; l < n; ++l) x[l] = X[L::idx(l, a, b)];
+    line_contract<n, T, false>(Se, x, y);
 #pragma unroll
-      for (int l = 0; l < n; ++l) s += Se[l * n + i] * A[k * PL + j * RP + l];
-      Bm[k * PL + j * RP + i] = s;
-    }
+    for (int l = 0; l < n; ++l) X[L::idx(l, a, b)] = y[l];
   }
   __syncthreads();
-  T y[n], v[n];
+  // forward s: line (i, k) = (a, b)
   if (act) {
 #pragma unroll
-    for (int k = 0; k < n; ++k) {
-      T s = T(0);
+    for (int l = 0; l < n; ++l) x[l] = X[L::idx(a, l, b)];
+    line_contract<n, T, false>(Se + n2, x, y);
 #pragma unroll
-      for (int l = 0; l < n; ++l) s += Se[n2 + l * n + j] * Bm[k * PL + l * RP + i];
-      y[k] = s;
-    }
-    const T lij = Le[i] + Le[n + j];
-#pragma unroll
-    for (int kp = 0; kp < n; ++kp) {
-      T s = T(0);
-#pragma unroll
-      for (int k = 0; k < n; ++k) s += Se[2 * n2 + k * n + kp] * y[k];
-      v[kp] = s / (P.h1 * (lij + Le[2 * n + kp]) + P.h2);
-    }
-    // back: (S_t (x) S_s (x) S_r), t first (in registers)
-#pragma unroll
-    for (int k = 0; k < n; ++k) {
-      T s = T(0);
-#pragma unroll
-      for (int kp = 0; kp < n; ++kp) s += Se[2 * n2 + k * n + kp] * v[kp];
-      y[k] = s;
-    }
+    for (int l = 0; l < n; ++l) X[L::idx(a, l, b)] = y[l];
   }
-  __syncthreads();  // every thread's reads of A and Bm above are done
+  __syncthreads();
+  // t: line (i, j) = (a, b): forward, divide by h1 (lam_r + lam_s + lam_t) + h2, back
   if (act) {
 #pragma unroll
-    for (int k = 0; k < n; ++k) A[k * PL + j * RP + i] = y[k];
+    for (int l = 0; l < n; ++l) x[l] = X[L::idx(a, b, l)];
+    line_contract<n, T, false>(Se + 2 * n2, x, y);
+    const T lab = Le[a] + Le[n + b];
+#pragma unroll
+    for (int l = 0; l < n; ++l) y[l] = y[l] / (P.h1 * (lab + Le[2 * n + l]) + P.h2);
+    line_contract<n, T, true>(Se + 2 * n2, y, x);
+#pragma unroll
+    for (int l = 0; l < n; ++l) X[L::idx(a, b, l)] = x[l];
+  }
+  __syncthreads();
+  // back s: line (i, k) = (a, b)
+  if (act) {
+#pragma unroll
+    for (int l = 0; l < n; ++l) x[l] = X[L::idx(a, l, b)];
+    line_contract<n, T, true>(Se + n2, x, y);
+#pragma unroll
+    for (int l = 0; l < n; ++l) X[L::idx(a, l, b)] = y[l];
+  }
+  __syncthreads();
+  // back r: line (j, k) = (a, b)
+  if (act) {
+#pragma unroll
+    for (int l = 0; l < n; ++l) x[l] = X[L::idx(l, a, b)];
+    line_contract<n, T, true>(Se, x, y);
+#pragma unroll
+    for (int l = 0; l < n; ++l) X[L::idx(l, a, b)] = y[l];
   }
   __syncthreads();
   if (act) {
 #pragma unroll
-    for (int k = 0; k < n; ++k) {
-      T s = T(0);
-#pragma unroll
-      for (int l = 0; l < n; ++l) s += Se[n2 + j * n + l] * A[k * PL + l * RP + i];
-      Bm[k * PL + j * RP + i] = s;
-    }
-  }
-  __syncthreads();
-  if (act) {
-#pragma unroll
-    for (int k = 0; k < n; ++k) {
-      T s = T(0);
-#pragma unroll
-      for (int l = 0; l < n; ++l) s += Se[i * n + l] * Bm[k * PL + j * RP + l];
-      P.z[base + k * n2] = wk[k] * s;
-    }
+    for (int k = 0; k < n; ++k) P.z[base + k * n2] = wk[k] * X[L::idx(a, b, k)];
   }
 }
 
 template <int N, typename T, int EPB>
 size_t fdm_smem() {
   constexpr int n = N + 1;
-  return sizeof(T) * ((size_t)EPB * (3 * n * n + 3 * n) + 2ull * EPB * n * n * (n + 1));
+  return sizeof(T) * ((size_t)EPB * (3 * n * n + 3 * n) + (size_t)EPB * FdmLay<n, T>::size + 8ull * EPB * n * n);
 }
 
 template <int N, typename T>
@@ -269,6 +323,86 @@ __global__ void k_coarse_prolong(T* __restrict__ z, const uint8_t* __restrict__ 
     const int64_t q = e * n3 + k * n2 + ij;
     if (wm[q] & 0x80) continue;  // Dirichlet: the masked field is 0 there
     z[q] = z[q] + (ftab[k] * a0 + ftab[n + k] * a1);
+  }
+}
+
+// z += mask R_0^T y, then <r, z>_W: a grid-stride loop over element groups
+// (fixed per block), compensated FP32 or FP64 sums per thread, fixed-order
+// block sums and a last-block sum of the block partials (deterministic).
+struct RhoAcc64 {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double get() const { return s; }
+};
+struct RhoAccF32 {  // Knuth's TwoSum on the FP32 pipe
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float t = __fadd_rn(s, v);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+    s = t;
+    c = __fadd_rn(c, err);
+  }
+  __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+};
+
+template <typename T, int EPB>
+__global__ void k_prolong_rho(T* __restrict__ z, const T* __restrict__ r, const uint8_t* __restrict__ wm,
+                              const T* __restrict__ ftab, const int32_t* __restrict__ cidx, const double* __restrict__ y,
+                              int n, int64_t E, PcgState* st, double* __restrict__ partial) {
+  using Acc = typename std::conditional<std::is_same<T, float>::value, RhoAccF32, RhoAcc64>::type;
+  __shared__ T cv[EPB][8];
+  __shared__ T sinv[128];
+  __shared__ double sred[32];
+  __shared__ int sdone;
+  if (threadIdx.x == 0) sdone = st->done;
+  for (int m = threadIdx.x; m < 128; m += blockDim.x) sinv[m] = m ? T(1) / T(m) : T(0);
+  __syncthreads();
+  if (sdone) return;
+  const int n2 = n * n, n3 = n2 * n;
+  const int le = threadIdx.x / n2, ij = threadIdx.x - le * n2, i = ij % n, j = ij / n;
+  const int64_t groups = (E + EPB - 1) / EPB;
+  Acc acc;
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    if (threadIdx.x < 8 * EPB) {
+      const int64_t e = g * EPB + threadIdx.x / 8;
+      const int c = e < E ? cidx[8 * e + (threadIdx.x & 7)] : -1;
+      cv[threadIdx.x / 8][threadIdx.x & 7] = c >= 0 ? (T)y[c] : T(0);
+    }
+    __syncthreads();
+    const int64_t e = g * EPB + le;
+    if (le < EPB && e < E) {
+      const T* c = cv[le];
+      const T fi0 = ftab[i], fi1 = ftab[n + i], fj0 = ftab[j], fj1 = ftab[n + j];
+      const T a0 = fj0 * (fi0 * c[0] + fi1 * c[1]) + fj1 * (fi0 * c[2] + fi1 * c[3]);
+      const T a1 = fj0 * (fi0 * c[4] + fi1 * c[5]) + fj1 * (fi0 * c[6] + fi1 * c[7]);
+      for (int k = 0; k < n; ++k) {
+        const int64_t q = e * n3 + k * n2 + ij;
+        const uint8_t m = wm[q];
+        T zq = z[q];
+        if (!(m & 0x80)) {
+          zq = zq + (ftab[k] * a0 + ftab[n + k] * a1);
+          z[q] = zq;
+        }
+        acc.add(r[q] * zq * sinv[m & 0x7f]);
+      }
+    }
+    __syncthreads();  // cv is rewritten for the next group
+  }
+  const double a = block_sum(acc.get(), sred);
+  if (threadIdx.x == 0) partial[blockIdx.x] = a;
+  if (last_block(&st->cnt[3])) {
+    const double rz_t = sum_partials(partial, gridDim.x, 1, 0, sred);
+    if (threadIdx.x == 0) {
+      if (rz_t != rz_t) {
+        st->done = 1;
+        st->status = 5;  // SEM_ERR_BREAKDOWN (NaN)
+      } else {
+        st->beta = rz_t / st->rho;
+        st->rho = rz_t;
+      }
+      st->cnt[3] = 0;
+    }
   }
 }
 
@@ -413,6 +547,25 @@ template cudaError_t launch_coarse_prolong<double>(double*, const uint8_t*, cons
 template cudaError_t launch_coarse_prolong<float>(float*, const uint8_t*, const float*, const int32_t*, const double*,
                                                   int, int64_t, double, const PcgState*, cudaStream_t);
 
+template <typename T>
+cudaError_t launch_prolong_rho(T* z, const T* r, const uint8_t* wm, const T* ftab, const int32_t* cidx,
+                               const double* y, int n, int64_t E, PcgState* st, double* partial, cudaStream_t s) {
+  const int grid = (int)std::min<int64_t>(152 * 4, std::max<int64_t>(1, E / 4));  // <= the vector kernels' partials
+  if (n <= 8) {
+    constexpr int EPB = 4;
+    const unsigned threads = ((EPB * n * n + 31) / 32) * 32;
+    k_prolong_rho<T, EPB><<<grid, threads, 0, s>>>(z, r, wm, ftab, cidx, y, n, E, st, partial);
+  } else {
+    const unsigned threads = ((n * n + 31) / 32) * 32;
+    k_prolong_rho<T, 1><<<grid, threads, 0, s>>>(z, r, wm, ftab, cidx, y, n, E, st, partial);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_prolong_rho<double>(double*, const double*, const uint8_t*, const double*, const int32_t*,
+                                                const double*, int, int64_t, PcgState*, double*, cudaStream_t);
+template cudaError_t launch_prolong_rho<float>(float*, const float*, const uint8_t*, const float*, const int32_t*,
+                                               const double*, int, int64_t, PcgState*, double*, cudaStream_t);
+
 cudaError_t launch_fill_phi(double* u, const uint8_t* wm, const double* xi, int n, int64_t P, int b, cudaStream_t s) {
   k_fill_phi<<<152 * 8, 256, 0, s>>>(u, wm, xi, n, P, b);
   return cudaGetLastError();
@@ -446,26 +599,33 @@ cudaError_t launch_gj_inverse(double* M, int nc, double* f, int* bad, cudaStream
 
 namespace {
 
-// d = c0 dinv r; x = d (acc = 0) or x += d (acc = 1)
+// A_0 is stored in ELL form, slot-major: row i's k-th entry at k * nc + i
+// (val, col; unused slots hold 0 and column i), so one thread per row reads
+// each slot coalesced across the rows of a warp, in a fixed order.
+
+// d = c0 dinv r; x = d (acc = 0) or x += d (acc = 1); rcopy = r (nullable)
 __global__ void k_cheb_first(const double* __restrict__ r, const double* __restrict__ dinv, double c0,
-                             double* __restrict__ d, double* __restrict__ x, int nc, int acc, const PcgState* st) {
+                             double* __restrict__ d, double* __restrict__ x, double* __restrict__ rcopy, int nc,
+                             int acc, const PcgState* st) {
   if (st && st->done) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
-    const double v = c0 * dinv[i] * r[i];
+    const double ri = r[i];
+    const double v = c0 * dinv[i] * ri;
     d[i] = v;
     x[i] = acc ? x[i] + v : v;
+    if (rcopy) rcopy[i] = ri;
   }
 }
 
 // r -= A d_prev; d_new = a d_prev + b dinv r; x += d_new (one thread per row)
-__global__ void k_cheb_step(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                            const double* __restrict__ val, const double* __restrict__ dinv,
-                            const double* __restrict__ dprev, double* __restrict__ dnew, double* __restrict__ r,
-                            double* __restrict__ x, double a, double b, int nc, const PcgState* st) {
+__global__ void k_cheb_step(const int32_t* __restrict__ col, const double* __restrict__ val, int width,
+                            const double* __restrict__ dinv, const double* __restrict__ dprev,
+                            double* __restrict__ dnew, double* __restrict__ r, double* __restrict__ x, double a,
+                            double b, int nc, const PcgState* st) {
   if (st && st->done) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) s += val[q] * dprev[col[q]];
+    for (int k = 0; k < width; ++k) s += val[(int64_t)k * nc + i] * dprev[col[(int64_t)k * nc + i]];
     const double ri = r[i] - s;
     r[i] = ri;
     const double dn = a * dprev[i] + b * dinv[i] * ri;
@@ -475,13 +635,13 @@ __global__ void k_cheb_step(const int64_t* __restrict__ ptr, const int32_t* __re
 }
 
 // r = g - A x
-__global__ void k_csr_resid(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                            const double* __restrict__ val, const double* __restrict__ g, const double* __restrict__ x,
-                            double* __restrict__ r, int nc, const PcgState* st) {
+__global__ void k_ell_resid(const int32_t* __restrict__ col, const double* __restrict__ val, int width,
+                            const double* __restrict__ g, const double* __restrict__ x, double* __restrict__ r, int nc,
+                            const PcgState* st) {
   if (st && st->done) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) s += val[q] * x[col[q]];
+    for (int k = 0; k < width; ++k) s += val[(int64_t)k * nc + i] * x[col[(int64_t)k * nc + i]];
     r[i] = g[i] - s;
   }
 }
@@ -513,31 +673,32 @@ cudaError_t launch_vcycle(const CoarseCycle& c, const double* g, double* x, cons
   double* d0 = c.work;
   double* d1 = c.work + nc;
   double* r = c.work + 2 * (size_t)nc;
-  for (int pass = 0; pass < 2; ++pass) {
-    if (pass == 0) {
-      // pre-smoothing from x = 0: r = g
-      k_cheb_first<<<grid, 256, 0, s>>>(g, c.dinv, c.cheb_c0, d0, x, nc, 0, st);
-      cudaMemcpyAsync(r, g, nc * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    } else {
-      k_csr_resid<<<grid, 256, 0, s>>>(c.ptr, c.col, c.val, g, x, r, nc, st);
-      k_cheb_first<<<grid, 256, 0, s>>>(r, c.dinv, c.cheb_c0, d0, x, nc, 1, st);
-    }
-    double* dp = d0;
-    double* dn = d1;
-    for (int k = 1; k < c.deg; ++k) {
-      k_cheb_step<<<grid, 256, 0, s>>>(c.ptr, c.col, c.val, c.dinv, dp, dn, r, x, c.cheb_a[k], c.cheb_b[k], nc, st);
-      std::swap(dp, dn);
-    }
-    if (pass == 0) {  // aggregate correction of the residual
-      k_csr_resid<<<grid, 256, 0, s>>>(c.ptr, c.col, c.val, g, x, r, nc, st);
-      k_agg_restrict<<<vgrid(c.na), 256, 0, s>>>(c.aptr, c.amem, r, c.ga, c.na, st);
-      k_dense_symv<<<std::min(152 * 8, (c.na + 7) / 8), 256, 0, s>>>(c.A00inv, c.ga, c.na, c.ya, st);
-      k_agg_prolong<<<grid, 256, 0, s>>>(c.agg, c.ya, x, nc, st);
+  for (int cyc = 0; cyc < c.cycles; ++cyc) {
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 0 && cyc == 0) {  // pre-smoothing from x = 0: r = g
+        k_cheb_first<<<grid, 256, 0, s>>>(g, c.dinv, c.cheb_c0, d0, x, r, nc, 0, st);
+      } else {
+        k_ell_resid<<<grid, 256, 0, s>>>(c.col, c.val, c.width, g, x, r, nc, st);
+        k_cheb_first<<<grid, 256, 0, s>>>(r, c.dinv, c.cheb_c0, d0, x, nullptr, nc, 1, st);
+      }
+      double* dp = d0;
+      double* dn = d1;
+      for (int k = 1; k < c.deg; ++k) {
+        k_cheb_step<<<grid, 256, 0, s>>>(c.col, c.val, c.width, c.dinv, dp, dn, r, x, c.cheb_a[k], c.cheb_b[k], nc,
+                                         st);
+        std::swap(dp, dn);
+      }
+      if (pass == 0) {  // aggregate correction of the residual
+        k_ell_resid<<<grid, 256, 0, s>>>(c.col, c.val, c.width, g, x, r, nc, st);
+        k_agg_restrict<<<vgrid(c.na), 256, 0, s>>>(c.aptr, c.amem, r, c.ga, c.na, st);
+        k_dense_symv<<<std::min(152 * 8, (c.na + 7) / 8), 256, 0, s>>>(c.A00inv, c.ga, c.na, c.ya, st);
+        k_agg_prolong<<<grid, 256, 0, s>>>(c.agg, c.ya, x, nc, st);
+      }
     }
   }
   return cudaGetLastError();
 }
 
-int vcycle_launches(const CoarseCycle& c) { return 2 * c.deg + 6; }
+int vcycle_launches(const CoarseCycle& c) { return c.cycles * (2 * c.deg + 6) - 1; }
 
 }  // namespace sem

@@ -24,6 +24,10 @@ struct FdmParams {
   T h1, h2;
   int64_t E;
   const PcgState* st;    // nullable: skipped once st->done
+  // coarse restriction fused into the same pass over r (nullable rc: none):
+  // rc[8 e + v] = sum over the element's points of phi_v r / mult
+  const T* ftab;         // [2][n]: (1 -+ xi_k) / 2
+  double* rc;
 };
 template <typename T>
 cudaError_t launch_fdm(int N, const FdmParams<T>& p, cudaStream_t s);
@@ -39,19 +43,24 @@ cudaError_t launch_dense_symv(const double* A, const double* x, int nc, double* 
 template <typename T>
 cudaError_t launch_coarse_prolong(T* z, const uint8_t* wm, const T* ftab, const int32_t* cidx, const double* y, int n,
                                   int64_t E, double zscale, const PcgState* st, cudaStream_t s);
+// z += mask R_0^T y (the coarse correction), then rho_new = <r, z>_W and
+// beta = rho_new / rho in the CG state (as launch_pcg_rho), in one pass.
+template <typename T>
+cudaError_t launch_prolong_rho(T* z, const T* r, const uint8_t* wm, const T* ftab, const int32_t* cidx,
+                               const double* y, int n, int64_t E, PcgState* st, double* partial, cudaStream_t s);
 cudaError_t launch_fill_phi(double* u, const uint8_t* wm, const double* xi, int n, int64_t P, int b, cudaStream_t s);
 cudaError_t launch_elem_coarse(const double* w, const uint8_t* wm, const double* xi, int n, int64_t E, int b,
                                double* Ae, cudaStream_t s);
 cudaError_t launch_gj_inverse(double* M, int nc, double* f, int* bad, cudaStream_t s);
 
-// Approximate coarse solve x = B g for many unknowns: one symmetric V-cycle
-// (Chebyshev smoothing in D^{-1} A_0 of degree deg, aggregate correction with
-// the dense inverse of A_00 = P^T A_0 P, Chebyshev smoothing again).
-constexpr int kChebMaxDeg = 8;
+// Approximate coarse solve x = B g for many unknowns: `cycles` symmetric
+// V-cycles (Chebyshev smoothing in D^{-1} A_0 of degree deg, aggregate
+// correction with the dense inverse of A_00 = P^T A_0 P, Chebyshev smoothing
+// again), each a linear step x += B (g - A_0 x) from x = 0.
+constexpr int kChebMaxDeg = 16;
 struct CoarseCycle {
-  int nc = 0, na = 0, deg = 0;
-  const int64_t* ptr = nullptr;  // CSR of A_0
-  const int32_t* col = nullptr;
+  int nc = 0, na = 0, deg = 0, cycles = 1, width = 0;
+  const int32_t* col = nullptr;  // A_0 in ELL form, slot-major [width][nc]
   const double* val = nullptr;
   const double* dinv = nullptr;  // 1 / diag(A_0)
   const int32_t* agg = nullptr;  // aggregate of each unknown

@@ -9,8 +9,8 @@
 // matrices of A_0 = R_0 A R_0^T on the device (the native FP64 operator
 // applied to the masked vertex functions), and A_0 assembled on the host and
 // inverted on the device (Gauss-Jordan, SPD) when it has at most
-// SEM_SCHWARZ_DENSE_COARSE_MAX unknowns.  Larger coarse problems are left out
-// (the local solves alone), which sem_schwarz_info reports.
+// SEM_SCHWARZ_DENSE_COARSE_MAX unknowns.  Larger coarse problems get a fixed
+// symmetric two-level cycle (Chebyshev smoothing, aggregate correction).
 //
 // One CG iteration with this preconditioner is
 //   ax (p = z + beta p, w = A_L p, alpha) | gs (w) | update (x, r, <r,r>, stop)
@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -54,7 +55,6 @@ struct sem_schwarz {
   double* y = nullptr;       // [nc]
   double* Ainv = nullptr;    // [nc][nc]
   // two-level cycle (coarse = 2): CSR of A_0, 1 / diag, aggregates, dense inverse of A_00
-  int64_t* aptr0 = nullptr;
   int32_t *acol = nullptr, *agg = nullptr, *aggptr = nullptr, *aggmem = nullptr;
   double *aval = nullptr, *dinv = nullptr, *A00inv = nullptr, *ga = nullptr, *ya = nullptr, *cwork = nullptr;
   sem::CoarseCycle cyc;
@@ -67,12 +67,27 @@ struct sem_schwarz {
 namespace sem {
 namespace {
 
-// Two-level coarse cycle: Chebyshev degree and range [lambda_max / kChebRange,
-// lambda_max], aggregates of about kAggSize unknowns, at most kAggMax of them.
-constexpr int kChebDeg = 3;
-constexpr double kChebRange = 20.0;
-constexpr int kAggSize = 64;
-constexpr int kAggMax = 4096;
+// Two-level coarse cycle: Chebyshev degree and range [lambda_max / range,
+// lambda_max], aggregates of about agg_size unknowns (at most kAggMax), and
+// the number of cycles per coarse solve.  SEM_SCHWARZ_CHEB_DEG,
+// SEM_SCHWARZ_CHEB_RANGE, SEM_SCHWARZ_AGG_SIZE and SEM_SCHWARZ_CYCLES
+// override the defaults (read when a preconditioner is created).
+struct CycleParams {
+  int deg = 3;
+  double range = 20.0;
+  int agg_size = 64;
+  int cycles = 1;
+};
+constexpr int kAggMax = 8192;
+
+CycleParams cycle_params() {
+  CycleParams p;
+  if (const char* v = std::getenv("SEM_SCHWARZ_CHEB_DEG")) p.deg = std::max(1, std::min(kChebMaxDeg, std::atoi(v)));
+  if (const char* v = std::getenv("SEM_SCHWARZ_CHEB_RANGE")) p.range = std::max(1.5, std::atof(v));
+  if (const char* v = std::getenv("SEM_SCHWARZ_AGG_SIZE")) p.agg_size = std::max(2, std::atoi(v));
+  if (const char* v = std::getenv("SEM_SCHWARZ_CYCLES")) p.cycles = std::max(1, std::min(8, std::atoi(v)));
+  return p;
+}
 
 // Device copy of a host array, on the set-up stream (no legacy-stream copies:
 // other threads may be capturing graphs).
@@ -92,7 +107,7 @@ void release(sem_schwarz* sw) {
   for (void* p : {(void*)sw->sidx, (void*)sw->S64, (void*)sw->lam64, (void*)sw->wtab64, (void*)sw->ftab64,
                   (void*)sw->S32, (void*)sw->lam32, (void*)sw->wtab32, (void*)sw->ftab32, (void*)sw->cidx,
                   (void*)sw->cptr, (void*)sw->cslot, (void*)sw->rc, (void*)sw->g, (void*)sw->y, (void*)sw->Ainv,
-                  (void*)sw->aptr0, (void*)sw->acol, (void*)sw->agg, (void*)sw->aggptr, (void*)sw->aggmem,
+                  (void*)sw->acol, (void*)sw->agg, (void*)sw->aggptr, (void*)sw->aggmem,
                   (void*)sw->aval, (void*)sw->dinv, (void*)sw->A00inv, (void*)sw->ga, (void*)sw->ya, (void*)sw->cwork})
     if (p) cudaFree(p);
 }
@@ -228,10 +243,12 @@ sem_status build_cycle(sem_schwarz* sw, const std::vector<int32_t>& cidx, const 
     lam = rq;
     v.swap(w);
   }
-  const double lmax = 1.1 * lam, lmin = lmax / kChebRange;
+  const CycleParams cp = cycle_params();
+  const double lmax = 1.1 * lam, lmin = lmax / cp.range;
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
   CoarseCycle& cy = sw->cyc;
-  cy.deg = kChebDeg;
+  cy.deg = cp.deg;
+  cy.cycles = cp.cycles;
   cy.cheb_c0 = 1.0 / theta;
   double rho = 1.0 / sigma;
   for (int k = 1; k < cy.deg; ++k) {
@@ -241,7 +258,7 @@ sem_status build_cycle(sem_schwarz* sw, const std::vector<int32_t>& cidx, const 
     rho = rn;
   }
   // aggregates
-  const int na = std::max(1, std::min(kAggMax, nc / kAggSize));
+  const int na = std::max(1, std::min(kAggMax, nc / cp.agg_size));
   std::vector<int32_t> idx(nc), agg(nc);
   for (int c = 0; c < nc; ++c) idx[c] = c;
   rcb(idx, 0, nc, na, 0, pts, agg);
@@ -255,10 +272,21 @@ sem_status build_cycle(sem_schwarz* sw, const std::vector<int32_t>& cidx, const 
   std::vector<double> A00((size_t)na * na, 0.0);
   for (int c = 0; c < nc; ++c)
     for (int64_t q = ptr[c]; q < ptr[c + 1]; ++q) A00[(size_t)agg[c] * na + agg[col[q]]] += val[q];
+  // ELL form, slot-major: row c's k-th entry at k * nc + c; padding entries are (c, 0)
+  int width = 0;
+  for (int c = 0; c < nc; ++c) width = std::max<int>(width, (int)(ptr[c + 1] - ptr[c]));
+  std::vector<int32_t> ecol((size_t)width * nc);
+  std::vector<double> evals((size_t)width * nc, 0.0);
+  for (int c = 0; c < nc; ++c)
+    for (int k = 0; k < width; ++k) {
+      const int64_t q = ptr[c] + k;
+      const bool has = q < ptr[c + 1];
+      ecol[(size_t)k * nc + c] = has ? col[q] : c;
+      evals[(size_t)k * nc + c] = has ? val[q] : 0.0;
+    }
   size_t& tb = sw->dev_bytes;
-  SW_TRY(upload(&sw->aptr0, ptr.data(), ptr.size(), tb, s));
-  SW_TRY(upload(&sw->acol, col.data(), col.size(), tb, s));
-  SW_TRY(upload(&sw->aval, val.data(), val.size(), tb, s));
+  SW_TRY(upload(&sw->acol, ecol.data(), ecol.size(), tb, s));
+  SW_TRY(upload(&sw->aval, evals.data(), evals.size(), tb, s));
   SW_TRY(upload(&sw->dinv, dinv.data(), dinv.size(), tb, s));
   SW_TRY(upload(&sw->agg, agg.data(), agg.size(), tb, s));
   SW_TRY(upload(&sw->aggptr, aptr.data(), aptr.size(), tb, s));
@@ -271,7 +299,7 @@ sem_status build_cycle(sem_schwarz* sw, const std::vector<int32_t>& cidx, const 
   SW_TRY(invert_spd(sw->A00inv, na, s));
   cy.nc = nc;
   cy.na = na;
-  cy.ptr = sw->aptr0;
+  cy.width = width;
   cy.col = sw->acol;
   cy.val = sw->aval;
   cy.dinv = sw->dinv;
@@ -385,11 +413,15 @@ sem_status build_coarse(sem_schwarz* sw, const std::vector<uint8_t>& wm_h, const
   return SEM_OK;
 }
 
-// z = M^{-1} r in T (st: the CG state inside a solve, nullptr outside).
+// z = M^{-1} r in T (st: the CG state inside a solve, nullptr outside).  With
+// rho (inside a CG iteration, coarse term present) the last pass, which adds
+// the coarse correction, also forms <r, z> and beta (launch_prolong_rho);
+// otherwise the caller forms them.
 template <typename T>
-sem_status apply_t(const sem_schwarz* sw, const T* r, T* z, const PcgState* st, cudaStream_t s) {
+sem_status apply_t(const sem_schwarz* sw, const T* r, T* z, PcgState* st, double* partial, bool rho, cudaStream_t s) {
   const sem_mesh* m = sw->m;
   constexpr bool f32 = std::is_same<T, float>::value;
+  const T* ft = f32 ? (const T*)sw->ftab32 : (const T*)sw->ftab64;
   FdmParams<T> fp{r,
                   z,
                   m->wm,
@@ -400,22 +432,27 @@ sem_status apply_t(const sem_schwarz* sw, const T* r, T* z, const PcgState* st, 
                   (T)sw->h1,
                   (T)sw->h2,
                   m->E,
-                  st};
-  SEM_CUDA(launch_fdm<T>(m->N, fp, s));
+                  st,
+                  ft,
+                  sw->coarse ? sw->rc : nullptr};
+  SEM_CUDA(launch_fdm<T>(m->N, fp, s));  // local solves, and the coarse restriction R_0 r
   SEM_CUDA(launch_gs<T>(z, gs_dev(m), 1, st, s));
   count_launches(2);
   if (sw->coarse) {
-    const T* ft = f32 ? (const T*)sw->ftab32 : (const T*)sw->ftab64;
-    SEM_CUDA(launch_coarse_restrict<T>(r, m->wm, ft, m->n, m->E, 1.0, sw->rc, st, s));
     SEM_CUDA(launch_coarse_gather(sw->rc, sw->cptr, sw->cslot, sw->nc, sw->g, st, s));
     if (sw->coarse == 1) {
       SEM_CUDA(launch_dense_symv(sw->Ainv, sw->g, sw->nc, sw->y, st, s));
+      count_launches(1);
     } else {
       SEM_CUDA(launch_vcycle(sw->cyc, sw->g, sw->y, st, s));
-      count_launches(vcycle_launches(sw->cyc) - 1);
+      count_launches(vcycle_launches(sw->cyc));
     }
-    SEM_CUDA(launch_coarse_prolong<T>(z, m->wm, ft, sw->cidx, sw->y, m->n, m->E, 1.0, st, s));
-    count_launches(4);
+    if (rho) {
+      SEM_CUDA(launch_prolong_rho<T>(z, r, m->wm, ft, sw->cidx, sw->y, m->n, m->E, st, partial, s));
+    } else {
+      SEM_CUDA(launch_coarse_prolong<T>(z, m->wm, ft, sw->cidx, sw->y, m->n, m->E, 1.0, st, s));
+    }
+    count_launches(2);
   }
   return SEM_OK;
 }
@@ -424,6 +461,7 @@ sem_status apply_t(const sem_schwarz* sw, const T* r, T* z, const PcgState* st, 
 sem_status iter_t(sem_schwarz* sw, bool f32) {
   sem_mesh* m = sw->m;
   Workspace* ws = sw->ws;
+  const bool fused_rho = sw->coarse != 0;
   if (f32) {
     SEM_CUDA(ax32(m, nullptr, ws->w32, sw->h1, sw->h2, true, ws->z32, ws->p32, ws->st, ws->part_ax, ws->s));
     SEM_CUDA(launch_gs<float>(ws->w32, gs_dev(m), 1, ws->st, ws->s));
@@ -431,18 +469,23 @@ sem_status iter_t(sem_schwarz* sw, bool f32) {
                        ws->part_vec};
     SEM_CUDA(launch_pcg_update<float>(v, ws->s, true));
     count_launches(3);
-    SW_TRY(apply_t<float>(sw, ws->r32, ws->z32, ws->st, ws->s));
-    SEM_CUDA((launch_pcg_rho<float, float>(ws->r32, ws->z32, nullptr, 1.0, m->wm, ws->n, ws->st, ws->part_vec, ws->s)));
+    SW_TRY(apply_t<float>(sw, ws->r32, ws->z32, ws->st, ws->part_vec, fused_rho, ws->s));
+    if (!fused_rho) {
+      SEM_CUDA((launch_pcg_rho<float, float>(ws->r32, ws->z32, nullptr, 1.0, m->wm, ws->n, ws->st, ws->part_vec, ws->s)));
+      count_launches(1);
+    }
   } else {
     SEM_CUDA(ax64(m, nullptr, ws->w, sw->h1, sw->h2, true, ws->z, ws->p, ws->st, ws->part_ax, ws->s));
     SEM_CUDA(launch_gs<double>(ws->w, gs_dev(m), 1, ws->st, ws->s));
     VecParams<double> v{ws->x, ws->r, ws->z, ws->p, ws->w, nullptr, ws->b, m->wm, ws->n, ws->st, ws->part_vec};
     SEM_CUDA(launch_pcg_update<double>(v, ws->s, true));
     count_launches(3);
-    SW_TRY(apply_t<double>(sw, ws->r, ws->z, ws->st, ws->s));
-    SEM_CUDA((launch_pcg_rho<double, double>(ws->r, ws->z, nullptr, 1.0, m->wm, ws->n, ws->st, ws->part_vec, ws->s)));
+    SW_TRY(apply_t<double>(sw, ws->r, ws->z, ws->st, ws->part_vec, fused_rho, ws->s));
+    if (!fused_rho) {
+      SEM_CUDA((launch_pcg_rho<double, double>(ws->r, ws->z, nullptr, 1.0, m->wm, ws->n, ws->st, ws->part_vec, ws->s)));
+      count_launches(1);
+    }
   }
-  count_launches(1);
   return SEM_OK;
 }
 
@@ -510,7 +553,7 @@ sem_status pcg64(sem_schwarz* sw, double tol, int maxit, Out& res) {
   for (int pass = 0;; ++pass) {
     SW_TRY(put_state(ws, tol, maxit - res.iters, 0));
     SW_TRY(true_residual(sw, 1));
-    SW_TRY(apply_t<double>(sw, ws->r, ws->z, nullptr, ws->s));
+    SW_TRY(apply_t<double>(sw, ws->r, ws->z, nullptr, nullptr, false, ws->s));
     VecParams<double> v{ws->x, ws->r, ws->z, ws->p, ws->w, nullptr, ws->b, m->wm, ws->n, ws->st, ws->part_vec};
     SEM_CUDA(launch_pcg_init<double>(v, ws->s, true));
     count_launches(1);
@@ -565,7 +608,7 @@ sem_status pcg_mixed(sem_schwarz* sw, double tol, int maxit, double delta, Out& 
   launch_scale_to_f32(ws->r32, ws->r, scale, ws->n, ws->s);
   launch_zero_f32(ws->x32, ws->n, ws->s);
   count_launches(2);
-  SW_TRY(apply_t<float>(sw, ws->r32, ws->z32, nullptr, ws->s));
+  SW_TRY(apply_t<float>(sw, ws->r32, ws->z32, nullptr, nullptr, false, ws->s));
   VecParams<float> v{ws->x32, ws->r32, ws->z32, ws->p32, ws->w32, nullptr, ws->r32, m->wm, ws->n, ws->st,
                      ws->part_vec};
   SEM_CUDA(launch_pcg_init<float>(v, ws->s, true));
@@ -594,7 +637,7 @@ sem_status pcg_mixed(sem_schwarz* sw, double tol, int maxit, double delta, Out& 
     }
     launch_scale_to_f32(ws->r32, ws->r, scale, ws->n, ws->s);
     count_launches(1);
-    SW_TRY(apply_t<float>(sw, ws->r32, ws->z32, nullptr, ws->s));
+    SW_TRY(apply_t<float>(sw, ws->r32, ws->z32, nullptr, nullptr, false, ws->s));
     SEM_CUDA(launch_pcg_restart<float>(v, ws->s, true));
     count_launches(1);
   }
@@ -720,8 +763,8 @@ sem_status sem_schwarz_apply(const sem_schwarz* sw, const void* r_dev, void* z_d
   }
   SEM_CUDA(cudaSetDevice(sw->m->device));
   cudaStream_t s = (cudaStream_t)stream;
-  if (prec == SEM_FP64) return apply_t<double>(sw, (const double*)r_dev, (double*)z_dev, nullptr, s);
-  if (prec == SEM_FP32) return apply_t<float>(sw, (const float*)r_dev, (float*)z_dev, nullptr, s);
+  if (prec == SEM_FP64) return apply_t<double>(sw, (const double*)r_dev, (double*)z_dev, nullptr, nullptr, false, s);
+  if (prec == SEM_FP32) return apply_t<float>(sw, (const float*)r_dev, (float*)z_dev, nullptr, nullptr, false, s);
   set_error("sem_schwarz_apply: prec must be SEM_FP64 or SEM_FP32");
   return SEM_ERR_INVALID;
 }

@@ -553,7 +553,7 @@ class Schwarz:
     def info(self):
         i = SchwarzInfo()
         _check(lib().sem_schwarz_info(self._h, C.byref(i)), "sem_schwarz_info")
-        return {"n_distinct": i.n_distinct, "n_coarse": i.n_coarse, "coarse": bool(i.coarse),
+        return {"n_distinct": i.n_distinct, "n_coarse": i.n_coarse, "coarse": int(i.coarse),
                 "dev_bytes": i.dev_bytes, "setup_ms": i.setup_ms}
 
     def apply(self, r, z, prec=FP64, stream=None):
