@@ -532,11 +532,12 @@ def schwarz_leg(m, b, stream, precs=("MIXED",)):
     return _sig(out)
 
 
-def large_leg(workloads=("pipe1048576_n7", "pipe131072_n11"), precs=("MIXED", "FP64")):
+def large_leg(workloads=("pipe1048576_n7", "pipe131072_n11"), precs=("MIXED",)):
     """The large configurations (E = 1,048,576 at N = 7, ~3.6e8 DOFs; E =
-    131,072 at N = 11): mesh set-up, mixed and FP64 Jacobi-PCG solves to 1e-10
-    (time, iterations, the solver's true residual) and the device memory in
-    use during the solves (cudaMemGetInfo)."""
+    131,072 at N = 11): mesh set-up, Jacobi-PCG solves to 1e-10 (time,
+    iterations, the solver's true residual; mixed precision by default, FP64
+    too with --large-fp64, ~4 more minutes) and the device memory in use
+    during the solves (cudaMemGetInfo)."""
     import torch
     import paper_2109_03592_gb300 as sem
     from sem_inputs import configs, forcing
@@ -742,7 +743,7 @@ def run_gpu(args):
         del b, x
         torch.cuda.empty_cache()
         try:
-            large = large_leg()
+            large = large_leg(precs=("MIXED", "FP64") if args.large_fp64 else ("MIXED",))
         except Exception as e:
             large = {"error": f"{type(e).__name__}: {e}"}
 
@@ -815,6 +816,7 @@ def main():
     ap.add_argument("--no-velocity", action="store_true", help="skip the three-component velocity Helmholtz leg")
     ap.add_argument("--no-schwarz", action="store_true", help="skip the overlapping-Schwarz leg")
     ap.add_argument("--no-large", action="store_true", help="skip the E = 1,048,576 and N = 11 solves")
+    ap.add_argument("--large-fp64", action="store_true", help="also the FP64 solves of the large configurations")
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--serving-rate", type=float, default=2.0)
     ap.add_argument("--serving-sweep", action="store_true",

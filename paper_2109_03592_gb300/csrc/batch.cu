@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kVecThreads) k_bupdate(Table* __restrict__ T, 
         } else if (st->iter >= st->maxit) {
           st->done = 1;
           st->status = 4;
-        } else if (st->delta2 > 0.0 && rr_t <= st->delta2 * st->rr_max) {
+        } else if (st->delta2 > 0.0 && rr_t <= st->delta2 * st->rr_max && st->iter - st->ru_iter >= kRuMinGap) {
           st->done = 1;
           st->ru = 1;
         } else {
@@ -469,15 +469,71 @@ class EngineImpl {
     return SEM_OK;
   }
 
-  // FP64 set-up of a request and its activation in a free slot.
+  // FP64 set-up of requests and their activation in free slots, in two
+  // phases so that the requests' FP64 work overlaps on the GPU: every
+  // request's initial residual is launched on its own stream with an
+  // asynchronous copy of its state, then each state is read and the request
+  // either finishes (b = 0, or x0 already meets tol) or starts its FP32 CG.
+  // Requests beyond the free slots are not taken (*taken counts those that were).
+  sem_status add_many(Req* const* qs, int count, int* taken) {
+    *taken = 0;
+    int free_slots = 0;
+    for (Req* o : slots_)
+      if (!o) ++free_slots;
+    const int k = std::min(count, free_slots);
+    for (int t = 0; t < k; ++t) {
+      sem_status st = add_begin(qs[t]);
+      if (st != SEM_OK) return st;
+      *taken = t + 1;
+    }
+    for (int t = 0; t < k; ++t) {
+      sem_status st = add_end(qs[t]);
+      if (st != SEM_OK) return st;
+    }
+    return SEM_OK;
+  }
+
   sem_status add(Req* q) {
-    int slot = -1;
-    for (int r = 0; r < kMaxSlots; ++r)
-      if (!slots_[r]) {
-        slot = r;
-        break;
-      }
-    if (slot < 0) return SEM_ERR_BUSY;
+    int taken = 0;
+    sem_status st = add_many(&q, 1, &taken);
+    if (st != SEM_OK) return st;
+    return taken ? SEM_OK : SEM_ERR_BUSY;
+  }
+
+ private:
+  // A request's state written from the pinned slot sth[1] (sth[0] receives
+  // the reads); the host rewrites sth[1] only after a read of the same
+  // stream has completed, so no synchronisation is needed here.
+  sem_status put_state_async(Workspace* ws, double tol, int maxit) {
+    PcgState h;
+    std::memset(&h, 0, sizeof(h));
+    h.tol2 = tol * tol;
+    h.maxit = maxit;
+    ws->sth[1] = h;
+    SEM_CUDA(cudaMemcpyAsync(ws->st, &ws->sth[1], sizeof(PcgState), cudaMemcpyHostToDevice, ws->s));
+    return SEM_OK;
+  }
+
+  // the FP64 residual r = b - A x of a request on its stream, then its state copied to sth[0] (event ev[0])
+  sem_status launch_residual_read(Req* q, int set_bb) {
+    Workspace* ws = q->ws;
+    sem_mesh* m = q->m;
+    SEM_CUDA(ax64_exact(m, ws->x, ws->w, q->o.h1, q->o.h2, ws->s));
+    SEM_CUDA(launch_gs<double>(ws->w, gs_dev(m), 1, nullptr, ws->s));
+    SEM_CUDA(launch_residual(ws->r, ws->b, ws->w, m->wm, ws->n, ws->st, ws->part_vec, set_bb, ws->s));
+    count_launches(3);
+    SEM_CUDA(cudaMemcpyAsync(&ws->sth[0], ws->st, sizeof(PcgState), cudaMemcpyDeviceToHost, ws->s));
+    SEM_CUDA(cudaEventRecord(ws->ev[0], ws->s));
+    return SEM_OK;
+  }
+
+  sem_status read_async_state(Workspace* ws, PcgState& out) {
+    SEM_CUDA(cudaEventSynchronize(ws->ev[0]));
+    out = ws->sth[0];
+    return SEM_OK;
+  }
+
+  sem_status add_begin(Req* q) {
     sem_mesh* m = q->m;
     if (!m->ws) {
       sem_status st = alloc_ws(m, &m->ws);
@@ -488,6 +544,8 @@ class EngineImpl {
     bool taken = false;
     for (Req* o : slots_)
       if (o && o->ws == m->ws) taken = true;
+    for (Req* o : pending_)
+      if (o->ws == m->ws) taken = true;
     if (taken) {
       Workspace* own = nullptr;
       if (!m->spare_ws.empty()) {  // one kept from an earlier batch on this mesh
@@ -503,26 +561,32 @@ class EngineImpl {
       q->ws = m->ws;
       q->own_ws = false;
     }
+    pending_.push_back(q);
     Workspace* ws = q->ws;
     const size_t bytes = (size_t)ws->n * sizeof(double);
-    // a fresh state (zero arrival counters) before the first reduction kernel
-    sem_status st0 = put_state(ws, q->o.tol, q->o.maxit, 0);
-    if (st0 != SEM_OK) return st0;
     // the request's own stream ws->s does its FP64 work; order it after ours
     SEM_CUDA(cudaEventRecord(eu_, s_));
     SEM_CUDA(cudaStreamWaitEvent(ws->s, eu_, 0));
+    // a fresh state (zero arrival counters) before the first reduction kernel
+    sem_status st0 = put_state_async(ws, q->o.tol, q->o.maxit);
+    if (st0 != SEM_OK) return st0;
     SEM_CUDA(cudaMemcpyAsync(ws->b, q->b, bytes, cudaMemcpyDeviceToDevice, ws->s));
     SEM_CUDA(cudaMemcpyAsync(ws->x, q->x, bytes, cudaMemcpyDeviceToDevice, ws->s));
     launch_mask(ws->x, m->wm, ws->n, ws->s);
     launch_minv(ws->minv, ws->minv32, m->opdK(), m->opdB(), m->wm, q->o.h1, q->o.h2, ws->n, ws->s);
     ws->minv_h1 = q->o.h1;
     ws->minv_h2 = q->o.h2;
-    SEM_CUDA(ax64_exact(m, ws->x, ws->w, q->o.h1, q->o.h2, ws->s));
-    SEM_CUDA(launch_gs<double>(ws->w, gs_dev(m), 1, nullptr, ws->s));
-    SEM_CUDA(launch_residual(ws->r, ws->b, ws->w, m->wm, ws->n, ws->st, ws->part_vec, 1, ws->s));
-    count_launches(5);
+    count_launches(2);
+    return launch_residual_read(q, 1);
+  }
+
+  sem_status add_end(Req* q) {
+    pending_.erase(std::find(pending_.begin(), pending_.end(), q));
+    Workspace* ws = q->ws;
+    sem_mesh* m = q->m;
+    const size_t bytes = (size_t)ws->n * sizeof(double);
     PcgState s0;
-    sem_status st = read_state(ws, s0);
+    sem_status st = read_async_state(ws, s0);
     if (st != SEM_OK) return st;
     if (s0.bb == 0.0) {
       SEM_CUDA(cudaMemsetAsync(ws->x, 0, bytes, ws->s));
@@ -532,7 +596,7 @@ class EngineImpl {
     q->scale = 1.0 / q->bnorm;
     const double rel = std::sqrt(s0.aux) / q->bnorm;
     if (rel <= q->o.tol) return finish(q, SEM_OK, rel, 0);
-    st = put_state(ws, kGamma * q->o.tol, q->o.maxit, 0);
+    st = put_state_async(ws, kGamma * q->o.tol, q->o.maxit);
     if (st != SEM_OK) return st;
     launch_scale_to_f32(ws->r32, ws->r, q->scale, ws->n, ws->s);
     launch_zero_f32(ws->x32, ws->n, ws->s);
@@ -543,12 +607,19 @@ class EngineImpl {
     count_launches(4);
     SEM_CUDA(cudaEventRecord(eu_, ws->s));
     SEM_CUDA(cudaStreamWaitEvent(s_, eu_, 0));
+    int slot = -1;
+    for (int r = 0; r < kMaxSlots; ++r)
+      if (!slots_[r]) {
+        slot = r;
+        break;
+      }
     q->slot = slot;
     slots_[slot] = q;
     dirty_ = true;
     return SEM_OK;
   }
 
+ public:
   bool idle() const {
     for (auto* q : slots_)
       if (q) return false;
@@ -571,19 +642,30 @@ class EngineImpl {
     int err = 0;
     SEM_CUDA(cudaMemcpyAsync(&err, d_err_, sizeof(int), cudaMemcpyDeviceToHost, s_));
     SEM_CUDA(cudaStreamSynchronize(s_));
+    // the paused requests' FP64 residuals first (each on its own stream, so
+    // they overlap), then their decisions
+    std::vector<std::pair<Req*, PcgState>> waiting;
     for (int r = 0; r < kMaxSlots; ++r) {
       Req* q = slots_[r];
       if (!q || !h_st_[r].done) continue;
-      st = on_pause(q, h_st_[r], err);
+      bool launched = false;
+      st = pause_begin(q, h_st_[r], err, &launched);
+      if (st != SEM_OK) return st;
+      if (launched) waiting.push_back({q, h_st_[r]});
+    }
+    for (auto& w : waiting) {
+      st = pause_end(w.first, w.second);
       if (st != SEM_OK) return st;
     }
     return SEM_OK;
   }
 
  private:
-  sem_status on_pause(Req* q, const PcgState& fin, int err) {
+  // x += x32 ||b|| for a paused request; a finished one (error, breakdown,
+  // maxit) completes here, any other gets its FP64 residual launched (*launched).
+  sem_status pause_begin(Req* q, const PcgState& fin, int err, bool* launched) {
+    *launched = false;
     Workspace* ws = q->ws;
-    sem_mesh* m = q->m;
     SEM_CUDA(cudaEventRecord(eu_, s_));
     SEM_CUDA(cudaStreamWaitEvent(ws->s, eu_, 0));
     launch_accumulate(ws->x, ws->x32, q->bnorm, ws->n, ws->s);
@@ -592,12 +674,17 @@ class EngineImpl {
     if (err || fin.status == SEM_ERR_DEVICE_TIMEOUT) return finish(q, SEM_ERR_DEVICE_TIMEOUT, 0.0, fin.iter);
     if (fin.status == SEM_ERR_BREAKDOWN || fin.status == SEM_ERR_NOT_CONVERGED)
       return finish(q, (sem_status)fin.status, std::sqrt(fin.rr), fin.iter);
-    SEM_CUDA(ax64_exact(m, ws->x, ws->w, q->o.h1, q->o.h2, ws->s));
-    SEM_CUDA(launch_gs<double>(ws->w, gs_dev(m), 1, nullptr, ws->s));
-    SEM_CUDA(launch_residual(ws->r, ws->b, ws->w, m->wm, ws->n, ws->st, ws->part_vec, 0, ws->s));
-    count_launches(3);
+    *launched = true;
+    return launch_residual_read(q, 0);
+  }
+
+  // The replacement's decision: finish at tol (or maxit), else r32 = r / ||b||
+  // and CG continues with its direction.
+  sem_status pause_end(Req* q, const PcgState& fin) {
+    Workspace* ws = q->ws;
+    sem_mesh* m = q->m;
     PcgState s1;
-    sem_status st = read_state(ws, s1);
+    sem_status st = read_async_state(ws, s1);
     if (st != SEM_OK) return st;
     q->outer += 1;
     const double rel = std::sqrt(s1.aux) / q->bnorm;
@@ -782,6 +869,7 @@ class EngineImpl {
   int* d_err_ = nullptr;
   cudaGraphExec_t graph_ = nullptr;
   Req* slots_[kMaxSlots] = {nullptr};
+  std::vector<Req*> pending_;  // between add_begin and add_end
   bool dirty_ = true;
 };
 
@@ -791,6 +879,7 @@ Engine::~Engine() { delete impl_; }
 sem_status Engine::init(cudaStream_t user) { return impl_->init(user); }
 sem_status Engine::attach(cudaStream_t user) { return impl_->attach(user); }
 sem_status Engine::add(Req* q) { return impl_->add(q); }
+sem_status Engine::add_many(Req* const* qs, int count, int* taken) { return impl_->add_many(qs, count, taken); }
 sem_status Engine::step() { return impl_->step(); }
 bool Engine::idle() const { return impl_->idle(); }
 int Engine::order() const { return impl_->order(); }
@@ -886,12 +975,14 @@ extern "C" sem_status sem_pcg_solve_batch(const sem_mesh* const* meshes, const d
   size_t next = 0;
   const int max_steps = 1 << 20;
   for (int step = 0; step < max_steps; ++step) {
-    // continuous admission: fill free slots from the queue
-    while (next < reqs.size()) {
-      st = eng.add(&reqs[next]);
-      if (st == SEM_ERR_BUSY) break;
+    // continuous admission: fill free slots from the queue (their FP64 set-up overlaps)
+    if (next < reqs.size()) {
+      std::vector<batch::Req*> qs;
+      for (size_t k = next; k < reqs.size(); ++k) qs.push_back(&reqs[k]);
+      int taken = 0;
+      st = eng.add_many(qs.data(), (int)qs.size(), &taken);
       if (st != SEM_OK) return st;
-      ++next;
+      next += taken;
     }
     if (eng.idle() && next == reqs.size()) break;
     st = eng.step();

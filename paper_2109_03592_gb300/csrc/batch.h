@@ -38,6 +38,9 @@ class Engine {
   // when every slot is taken.  The request may finish inside add() (b = 0 or
   // x already converged).
   sem_status add(Req* q);
+  // add() for several requests at once, their FP64 set-up overlapping on the
+  // GPU; takes at most the free slots (*taken: how many, in order).
+  sem_status add_many(Req* const* qs, int count, int* taken);
   // One graph launch, then the FP64 work of the requests that paused.
   sem_status step();
   bool idle() const;

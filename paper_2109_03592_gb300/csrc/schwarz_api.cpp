@@ -80,6 +80,13 @@ struct CycleParams {
 };
 constexpr int kAggMax = 8192;
 
+// Reliable-update threshold of the mixed Schwarz solve.  Schwarz-PCG reduces
+// the residual ~17x faster per iteration than Jacobi, so the Jacobi solver's
+// 0.3 replaced the residual every ~16 iterations; measured at E = 262,144
+// (mixed, tol 1e-10): 0.3: 329 iterations, 20 replacements, 1.93 s; 0.1: 344,
+// 11, 1.82 s; 0.03: 327, 7, 1.66 s; 0.01: 351, 6, 1.75 s.
+constexpr double kSchwarzDelta = 0.03;
+
 CycleParams cycle_params() {
   CycleParams p;
   if (const char* v = std::getenv("SEM_SCHWARZ_CHEB_DEG")) p.deg = std::max(1, std::min(kChebMaxDeg, std::atoi(v)));
@@ -724,7 +731,10 @@ sem_status sem_schwarz_create(const sem_mesh* mesh, double h1, double h2, int fl
   if ((st = upload(&sw->ftab64, ftab.data(), ftab.size(), tb, s)) != SEM_OK) return fail(st);
   if ((st = upload(&sw->ftab32, ftab32.data(), ftab32.size(), tb, s)) != SEM_OK) return fail(st);
   if (flags & SEM_SCHWARZ_COARSE) {
-    if ((st = build_coarse(sw, wm_h, xyz, SEM_SCHWARZ_DENSE_COARSE_MAX, s)) != SEM_OK) return fail(st);
+    // SEM_SCHWARZ_DENSE_MAX lowers the dense limit (to compare the two coarse forms on one mesh)
+    int dense_max = SEM_SCHWARZ_DENSE_COARSE_MAX;
+    if (const char* v = std::getenv("SEM_SCHWARZ_DENSE_MAX")) dense_max = std::max(0, std::min(dense_max, std::atoi(v)));
+    if ((st = build_coarse(sw, wm_h, xyz, dense_max, s)) != SEM_OK) return fail(st);
   }
   sw->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = sw;
@@ -807,8 +817,9 @@ sem_status sem_schwarz_solve(sem_schwarz* sw, const double* b_dev, double* x_dev
   launch_mask(ws->x, m->wm, ws->n, ws->s);
   count_launches(1);
   Out res;
-  sem_status st = opts->prec == SEM_FP64 ? pcg64(sw, tol, maxit, res)
-                                         : pcg_mixed(sw, tol, maxit, opts->delta > 0.0 ? opts->delta : 0.3, res);
+  sem_status st = opts->prec == SEM_FP64
+                      ? pcg64(sw, tol, maxit, res)
+                      : pcg_mixed(sw, tol, maxit, opts->delta > 0.0 ? opts->delta : kSchwarzDelta, res);
   if (st != SEM_OK) return st;
   SEM_CUDA(cudaMemcpyAsync(x_dev, ws->x, bytes, cudaMemcpyDeviceToDevice, ws->s));
   SEM_CUDA(cudaEventRecord(ws->e1, ws->s));

@@ -144,17 +144,25 @@ void engine_main(sem_server* srv, EngineThread* et) {
         et->ready.pop_front();
       }
     }
-    for (auto& q : incoming) {
-      sem_status st = init_st;
-      q->t_solve = Request::Clock::now();
-      if (st == SEM_OK) st = eng.add(&q->breq);
-      if (st != SEM_OK) {
-        q->x.clear();
-        free_request_device(*q);
-        complete(srv, q, st);
-        continue;
+    if (!incoming.empty()) {  // admitted together: their FP64 set-up overlaps on the GPU
+      std::vector<sem::batch::Req*> qs;
+      for (auto& q : incoming) {
+        q->t_solve = Request::Clock::now();
+        qs.push_back(&q->breq);
       }
-      et->active.push_back(q);
+      int taken = 0;
+      sem_status st = init_st;
+      if (st == SEM_OK) st = eng.add_many(qs.data(), (int)qs.size(), &taken);
+      for (size_t k = 0; k < incoming.size(); ++k) {
+        auto& q = incoming[k];
+        if (st != SEM_OK || (int)k >= taken) {
+          q->x.clear();
+          free_request_device(*q);
+          complete(srv, q, st != SEM_OK ? st : SEM_ERR_BUSY);
+          continue;
+        }
+        et->active.push_back(q);
+      }
     }
     if (!eng.idle()) {
       sem_status st = eng.step();
