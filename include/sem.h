@@ -364,6 +364,14 @@ sem_status sem_pressure_div(const sem_mesh* mesh, const double* u_dev, double* q
 /* q = E p (Sec. 2, Eq. 5).  work_dev: caller-owned scratch of 3 n_local
  * doubles (the three velocity components), overwritten; it must not overlap
  * p or q.  q may equal p (p is read in full before q is written). */
+/* q = E p in FP32 (the factors, basis matrices and fields rounded from FP64,
+ * the inverse assembled mass applied as its FP32 reciprocal): p, q [E][m^3]
+ * floats, work_dev 3 n_local floats of caller-owned scratch; p, q, work
+ * distinct.  The first call on a mesh builds the FP32 copies (synchronising
+ * the stream). */
+sem_status sem_pressure_apply_f32(const sem_mesh* mesh, const float* p_dev, float* q_dev, float* work_dev,
+                                  void* stream);
+
 sem_status sem_pressure_apply(const sem_mesh* mesh, const double* p_dev, double* q_dev, double* work_dev,
                               void* stream);
 
@@ -376,14 +384,23 @@ sem_status sem_pressure_apply(const sem_mesh* mesh, const double* p_dev, double*
  * pressure values, stopped when ||r|| <= opts->tol ||Pm g|| for the recurrence
  * residual and then for the true residual Pm (g - E p) (CG restarts from p,
  * at most 5 times, when the recurrence drifted); tol <= 0 means 1e-10,
- * maxit <= 0 means 20000, the other fields of opts are ignored.
+ * maxit <= 0 means 20000.  opts->prec: SEM_FP64 (as above) or SEM_MIXED:
+ * the same CG with E applied in FP32 (sem_pressure_apply_f32) and reliable
+ * updates -- when the recurrence residual has dropped by opts->delta (<= 0
+ * means 0.1) since the last replacement, at least 8 iterations later, or
+ * below 0.2 tol, the true residual is formed with the FP64 E and replaces it
+ * (result->outer_iters counts them); the solve stops when the true residual
+ * meets tol.  The other fields of opts are ignored.
  * result->rel_res is the true residual once converged.
  * g_dev, p_dev: [E][m^3] FP64; p_dev is output only (mean zero).  Every
  * reduction is deterministic.  Synchronous: the host reads three sums per
  * iteration.  Allocates 3 n_pressure + 3 n_local doubles of scratch for the
  * call.  Returns the solve's status (also in result->status): SEM_OK,
  * SEM_ERR_NOT_CONVERGED or SEM_ERR_BREAKDOWN (<p, E p> <= 0), with result
- * filled in; result->outer_iters is 0 and result->ms the device time. */
+ * filled in; result->outer_iters is 0 (SEM_FP64) and result->ms the device
+ * time.  SEM_MIXED allocates a further 2 n_pressure + 3 n_local floats, and
+ * keeps FP32 copies of the GL-point data on the mesh (36 B per pressure
+ * value). */
 sem_status sem_pressure_solve(const sem_mesh* mesh, const double* g_dev, double* p_dev, const sem_solve_opts* opts,
                               sem_solve_result* result, void* stream);
 

@@ -199,16 +199,15 @@ def pcg_mixed(prob, b, tol=1e-10, inner_tol=1e-5, max_outer=50, maxit=20000):
     return Result(x, total, rnorm / bnorm, st, hist, outer)
 
 
-def pcg_mixed_reliable(prob, b, tol=1e-10, delta=0.3, maxit=20000, gamma=0.2, min_gap=8):
+def pcg_mixed_reliable(prob, b, tol=1e-10, delta=0.3, maxit=20000, gamma=0.2):
     """Mixed-precision PCG with reliable updates.
 
     The CG recurrences run in FP32 on the scaled system (b / ||b||): x32 holds
     the solution increment since the last reliable update.  Whenever the FP32
     iterated residual has dropped below delta times its largest value since
-    that update, at least min_gap iterations after it (or below gamma * tol:
-    the FP32 residual must undershoot the target, otherwise a true residual
-    just above tol triggers a replacement after every few steps and stalls),
-    the increment is added to the FP64
+    that update (or below gamma * tol: the FP32 residual must undershoot the
+    target, otherwise a true residual just above tol triggers a replacement
+    after every few steps and stalls), the increment is added to the FP64
     solution, the true residual r = b - A64 x is recomputed in FP64 and
     replaces the FP32 one, and CG continues with its current direction p:
     z = M^{-1} r, beta = <r,z>_new / <r,z>_old, p = z + beta p.  The solve stops
@@ -226,7 +225,7 @@ def pcg_mixed_reliable(prob, b, tol=1e-10, delta=0.3, maxit=20000, gamma=0.2, mi
     rho = p32.dot(r, z)
     beta = np.float32(0.0)
     rr_max = p32.dot(r, r)
-    hist, updates, k_last = [1.0], 0, 0
+    hist, updates = [1.0], 0
     for k in range(1, maxit + 1):
         p = z + beta * p
         w = p32.A(p)
@@ -237,8 +236,7 @@ def pcg_mixed_reliable(prob, b, tol=1e-10, delta=0.3, maxit=20000, gamma=0.2, mi
         x32 = x32 + alpha * p
         r = r - alpha * w
         rr = p32.dot(r, r)
-        if (rr <= delta * delta * rr_max and k - k_last >= min_gap) or rr <= (gamma * tol) ** 2:
-            k_last = k
+        if rr <= delta * delta * rr_max or rr <= (gamma * tol) ** 2:
             x = x + x32.astype(np.float64) / s
             x32[:] = 0.0
             rt = b - prob.A(x)

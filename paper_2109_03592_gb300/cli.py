@@ -8,8 +8,9 @@
     python -m paper_2109_03592_gb300.cli psolve --workload pipe4096_n7 [--tol 1e-10]
 
 pressure times the consistent Poisson operator E = D B^-1 D^T of the
-P_N - P_{N-2} pressure space (sem_pressure_apply); psolve solves E p = g on
-the mean-free pressure space (sem_pressure_solve) for a seeded
+P_N - P_{N-2} pressure space (sem_pressure_apply; --prec fp32:
+sem_pressure_apply_f32); psolve solves E p = g on the mean-free pressure
+space (sem_pressure_solve, --prec fp64 or mixed) for a seeded
 standard-normal g.
 
 --coef gives the mesh seeded per-point coefficients h1(i,j,k,e), h2(i,j,k,e)
@@ -59,17 +60,24 @@ def _pressure(args):
     work = torch.empty(3 * m.n_local, dtype=torch.float64, device="cuda")
     if args.what == "psolve":
         m.pressure_apply(g, q, work)  # builds the GL-point factors
+        prec = sem.MIXED if args.prec == "mixed" else sem.FP64
         for _ in range(args.repeat):
-            r = m.pressure_solve(g, q, tol=args.tol)
-            print(json.dumps({"workload": args.workload, "pressure_values": m.pressure_size(), **r}), flush=True)
+            r = m.pressure_solve(g, q, tol=args.tol, prec=prec)
+            print(json.dumps({"workload": args.workload, "prec": "mixed" if prec == sem.MIXED else "fp64",
+                              "pressure_values": m.pressure_size(), **r}), flush=True)
     else:
+        f32 = args.prec == "fp32"
+        if f32:
+            g, q = g.float(), q.float()
+            work = work.float()
+        apply = (lambda: m.pressure_apply_f32(g, q, work)) if f32 else (lambda: m.pressure_apply(g, q, work))
         for _ in range(3):
-            m.pressure_apply(g, q, work)
+            apply()
         a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record()
         for _ in range(args.reps):
-            m.pressure_apply(g, q, work)
+            apply()
         e.record()
         torch.cuda.synchronize()
         ms = a.elapsed_time(e) / args.reps

@@ -77,6 +77,10 @@ void free_mesh_arrays(sem_mesh* m) {
   dev_free(m->Fgl);
   dev_free(m->Igl);
   dev_free(m->DIgl);
+  dev_free(m->Fgl32);
+  dev_free(m->Igl32);
+  dev_free(m->DIgl32);
+  dev_free(m->invB32);
 }
 
 #define SEM_TRY(expr)                   \

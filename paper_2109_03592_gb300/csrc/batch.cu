@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kVecThreads) k_bupdate(Table* __restrict__ T, 
         } else if (st->iter >= st->maxit) {
           st->done = 1;
           st->status = 4;
-        } else if (st->delta2 > 0.0 && rr_t <= st->delta2 * st->rr_max && st->iter - st->ru_iter >= kRuMinGap) {
+        } else if (st->delta2 > 0.0 && rr_t <= st->delta2 * st->rr_max) {
           st->done = 1;
           st->ru = 1;
         } else {

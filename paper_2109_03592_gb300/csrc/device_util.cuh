@@ -26,18 +26,9 @@ struct PcgState {
   int maxit;
   int done;      // 1 once converged / failed / paused: later kernels of the chunk return at once
   int ru;        // 1 when paused for a reliable update (FP64 residual replacement)
-  int ru_iter;   // iteration of the last replacement (or start): the next comes kRuMinGap or more later
   int status;    // sem_status of the run
   unsigned int cnt[4];  // arrival counters of the grid reductions
 };
-
-// Reliable updates: at least this many CG iterations between two residual
-// replacements triggered by the delta test (the final convergence check is
-// not delayed).  A well-conditioned system (the velocity Helmholtz solves,
-// h2 >> h1) drops its FP32 residual by more than delta every iteration, and a
-// replacement (one native FP64 operator application) after each of its few
-// iterations cost more than the iterations themselves.
-constexpr int kRuMinGap = 8;
 
 #ifdef __CUDACC__
 // Sum over a block in a fixed order (warp shuffles, then one warp over the

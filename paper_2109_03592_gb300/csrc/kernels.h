@@ -145,10 +145,20 @@ cudaError_t launch_pap_finish(const double* partial, int count, PcgState* st, cu
 size_t gl_factors_smem(int n, int m);
 cudaError_t launch_gl_factors(const double* xyz, const double* Ig, const double* DIg, const double* rho, int n, int m,
                               int64_t E, double* F, int* bad, cudaStream_t s);
-cudaError_t launch_pgrad(const double* p, const double* F, const double* Ig, const double* DIg, int n, int m,
-                         int64_t E, double* u, int64_t n_local, cudaStream_t s);
-cudaError_t launch_pdiv(const double* u, const double* dB, const double* F, const double* Ig, const double* DIg, int n,
-                        int m, int64_t E, double* out, int64_t n_local, cudaStream_t s);
+// T = double, or float for the FP32 operator (factors and basis rounded from FP64)
+template <typename T>
+cudaError_t launch_pgrad(const T* p, const T* F, const T* Ig, const T* DIg, int n, int m, int64_t E, T* u,
+                         int64_t n_local, cudaStream_t s);
+// v_a = u_a / dB (dB given), u_a invB (invB given), or u_a
+template <typename T>
+cudaError_t launch_pdiv(const T* u, const T* dB, const T* invB, const T* F, const T* Ig, const T* DIg, int n, int m,
+                        int64_t E, T* out, int64_t n_local, cudaStream_t s);
+void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+void launch_to_f64(const float* a, double* b, int64_t n, cudaStream_t s);
+void launch_recip_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+// r = (g - cg) - (w - cw), out[0] = <r, r>
+cudaError_t launch_presidual_keep(const double* g, double cg, const double* w, double cw, double* r, int64_t n,
+                                  double* partial, double* out, cudaStream_t s);
 // Pressure-CG vector kernels; each reduction writes its (deterministic) sum to
 // out[0] on the device, using partial[pressure_red_blocks()] as scratch.
 int pressure_red_blocks();

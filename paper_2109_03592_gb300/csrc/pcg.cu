@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(const VecParams<T> P
       } else if (st->iter >= st->maxit) {
         st->done = 1;
         st->status = 4;  // SEM_ERR_NOT_CONVERGED
-      } else if (st->delta2 > 0.0 && rr_t <= st->delta2 * st->rr_max && st->iter - st->ru_iter >= kRuMinGap) {
+      } else if (st->delta2 > 0.0 && rr_t <= st->delta2 * st->rr_max) {
         st->done = 1;  // pause: the host replaces r by the FP64 true residual
         st->ru = 1;
       } else {
@@ -272,7 +272,6 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_init(const VecParams<T> P) 
       st->done = (bb_t == 0.0) || (rr_t <= st->tol2 * bb_t);
       st->rr_max = rr_t;
       st->ru = 0;
-      st->ru_iter = 0;
       st->cnt[2] = 0;
     }
   }
@@ -317,7 +316,6 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_restart(const VecParams<T> 
       st->rr = rr_t;
       st->rr_max = rr_t;
       st->ru = 0;
-      st->ru_iter = st->iter;
       st->done = 0;
       st->status = 0;
       st->cnt[2] = 0;

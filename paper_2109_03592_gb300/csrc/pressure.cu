@@ -92,37 +92,39 @@ __global__ void k_gl_factors(const double* __restrict__ xyz, const double* __res
 // u_a = sum_b C_b^T (F[b][a] p) for a = 0, 1, 2 (local, unassembled).
 // Shared memory: the two 1D matrices [m][n], tb [m^3], T1 [m][m][n],
 // T2 [m][n][n], acc [n^3].  Each thread owns the acc entries q = tid + t blockDim.
-__global__ void k_pgrad(const double* __restrict__ p, const double* __restrict__ F, const double* __restrict__ Ig,
-                        const double* __restrict__ DIg, int n, int m, int64_t E, double* __restrict__ u,
-                        int64_t n_local) {
-  extern __shared__ double sm[];
+// T = double (FP64) or float (the FP32 operator of the mixed-precision solve).
+template <typename T>
+__global__ void k_pgrad(const T* __restrict__ p, const T* __restrict__ F, const T* __restrict__ Ig,
+                        const T* __restrict__ DIg, int n, int m, int64_t E, T* __restrict__ u, int64_t n_local) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);
   const int n2 = n * n, n3 = n2 * n, m2 = m * m, m3 = m2 * m;
-  double* sI = sm;
-  double* sD = sI + m * n;
-  double* tb = sD + m * n;
-  double* T1 = tb + m3;
-  double* T2 = T1 + m2 * n;
-  double* acc = T2 + m * n2;
+  T* sI = sm;
+  T* sD = sI + m * n;
+  T* tb = sD + m * n;
+  T* T1 = tb + m3;
+  T* T2 = T1 + m2 * n;
+  T* acc = T2 + m * n2;
   const int64_t e = blockIdx.x;
   if (e >= E) return;
   for (int q = threadIdx.x; q < m * n; q += blockDim.x) {
     sI[q] = Ig[q];
     sD[q] = DIg[q];
   }
-  const double* pe = p + e * m3;
+  const T* pe = p + e * m3;
   for (int a = 0; a < 3; ++a) {
-    for (int q = threadIdx.x; q < n3; q += blockDim.x) acc[q] = 0.0;
+    for (int q = threadIdx.x; q < n3; q += blockDim.x) acc[q] = T(0);
     for (int b = 0; b < 3; ++b) {
-      const double* Mi = b == 0 ? sD : sI;
-      const double* Mj = b == 1 ? sD : sI;
-      const double* Mk = b == 2 ? sD : sI;
-      const double* Fba = F + (e * 9 + 3 * b + a) * m3;
+      const T* Mi = b == 0 ? sD : sI;
+      const T* Mj = b == 1 ? sD : sI;
+      const T* Mk = b == 2 ? sD : sI;
+      const T* Fba = F + (e * 9 + 3 * b + a) * m3;
       for (int q = threadIdx.x; q < m3; q += blockDim.x) tb[q] = Fba[q] * pe[q];
       __syncthreads();
       // T1[k][j][l] = sum_i Mi[i][l] tb[k][j][i]
       for (int q = threadIdx.x; q < m2 * n; q += blockDim.x) {
         const int l = q % n, kj = q / n;
-        double s = 0.0;
+        T s = T(0);
         for (int i = 0; i < m; ++i) s += Mi[i * n + l] * tb[kj * m + i];
         T1[q] = s;
       }
@@ -130,7 +132,7 @@ __global__ void k_pgrad(const double* __restrict__ p, const double* __restrict__
       // T2[k][pp][l] = sum_j Mj[j][pp] T1[k][j][l]
       for (int q = threadIdx.x; q < m * n2; q += blockDim.x) {
         const int l = q % n, pp = (q / n) % n, k = q / n2;
-        double s = 0.0;
+        T s = T(0);
         for (int j = 0; j < m; ++j) s += Mj[j * n + pp] * T1[(k * m + j) * n + l];
         T2[q] = s;
       }
@@ -138,49 +140,52 @@ __global__ void k_pgrad(const double* __restrict__ p, const double* __restrict__
       // acc[s][pp][l] += sum_k Mk[k][s] T2[k][pp][l]
       for (int q = threadIdx.x; q < n3; q += blockDim.x) {
         const int pl = q % n2, s_ = q / n2;
-        double s = 0.0;
+        T s = T(0);
         for (int k = 0; k < m; ++k) s += Mk[k * n + s_] * T2[k * n2 + pl];
         acc[q] += s;
       }
     }
-    double* ua = u + a * n_local + e * n3;
+    T* ua = u + a * n_local + e * n3;
     for (int q = threadIdx.x; q < n3; q += blockDim.x) ua[q] = acc[q];
   }
 }
 
 // out_q = sum_a sum_b F[b][a](q) (C_b v_a)(q), v_a = u_a / dB when dB is given
-// (the inverse assembled mass), u_a itself otherwise.  Shared memory: the two
+// (the inverse assembled mass), u_a invB when invB (its reciprocal) is given,
+// u_a itself otherwise.  Shared memory: the two
 // 1D matrices, V [n^3], S1 [n][n][m], S2 [n][m][m], oacc [m^3].
-__global__ void k_pdiv(const double* __restrict__ u, const double* __restrict__ dB, const double* __restrict__ F,
-                       const double* __restrict__ Ig, const double* __restrict__ DIg, int n, int m, int64_t E,
-                       double* __restrict__ out, int64_t n_local) {
-  extern __shared__ double sm[];
+template <typename T>
+__global__ void k_pdiv(const T* __restrict__ u, const T* __restrict__ dB, const T* __restrict__ invB,
+                       const T* __restrict__ F, const T* __restrict__ Ig, const T* __restrict__ DIg, int n, int m,
+                       int64_t E, T* __restrict__ out, int64_t n_local) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);
   const int n2 = n * n, n3 = n2 * n, m2 = m * m, m3 = m2 * m;
-  double* sI = sm;
-  double* sD = sI + m * n;
-  double* V = sD + m * n;
-  double* S1 = V + n3;
-  double* S2 = S1 + n2 * m;
-  double* oacc = S2 + n * m2;
+  T* sI = sm;
+  T* sD = sI + m * n;
+  T* V = sD + m * n;
+  T* S1 = V + n3;
+  T* S2 = S1 + n2 * m;
+  T* oacc = S2 + n * m2;
   const int64_t e = blockIdx.x;
   if (e >= E) return;
   for (int q = threadIdx.x; q < m * n; q += blockDim.x) {
     sI[q] = Ig[q];
     sD[q] = DIg[q];
   }
-  for (int q = threadIdx.x; q < m3; q += blockDim.x) oacc[q] = 0.0;
+  for (int q = threadIdx.x; q < m3; q += blockDim.x) oacc[q] = T(0);
   for (int a = 0; a < 3; ++a) {
-    const double* ua = u + a * n_local + e * n3;
-    for (int q = threadIdx.x; q < n3; q += blockDim.x) V[q] = dB ? ua[q] / dB[e * n3 + q] : ua[q];
+    const T* ua = u + a * n_local + e * n3;
+    for (int q = threadIdx.x; q < n3; q += blockDim.x) V[q] = dB ? ua[q] / dB[e * n3 + q] : (invB ? ua[q] * invB[e * n3 + q] : ua[q]);
     __syncthreads();
     for (int b = 0; b < 3; ++b) {
-      const double* Mi = b == 0 ? sD : sI;
-      const double* Mj = b == 1 ? sD : sI;
-      const double* Mk = b == 2 ? sD : sI;
+      const T* Mi = b == 0 ? sD : sI;
+      const T* Mj = b == 1 ? sD : sI;
+      const T* Mk = b == 2 ? sD : sI;
       // S1[s][pp][i] = sum_l Mi[i][l] V[s][pp][l]
       for (int q = threadIdx.x; q < n2 * m; q += blockDim.x) {
         const int i = q % m, spp = q / m;
-        double s = 0.0;
+        T s = T(0);
         for (int l = 0; l < n; ++l) s += Mi[i * n + l] * V[spp * n + l];
         S1[q] = s;
       }
@@ -188,22 +193,22 @@ __global__ void k_pdiv(const double* __restrict__ u, const double* __restrict__ 
       // S2[s][j][i] = sum_pp Mj[j][pp] S1[s][pp][i]
       for (int q = threadIdx.x; q < n * m2; q += blockDim.x) {
         const int i = q % m, j = (q / m) % m, s_ = q / m2;
-        double s = 0.0;
+        T s = T(0);
         for (int pp = 0; pp < n; ++pp) s += Mj[j * n + pp] * S1[(s_ * n + pp) * m + i];
         S2[q] = s;
       }
       __syncthreads();
       // oacc[k][j][i] += F[b][a] sum_s Mk[k][s] S2[s][j][i]
-      const double* Fba = F + (e * 9 + 3 * b + a) * m3;
+      const T* Fba = F + (e * 9 + 3 * b + a) * m3;
       for (int q = threadIdx.x; q < m3; q += blockDim.x) {
         const int ji = q % m2, k = q / m2;
-        double s = 0.0;
+        T s = T(0);
         for (int s_ = 0; s_ < n; ++s_) s += Mk[k * n + s_] * S2[s_ * m2 + ji];
         oacc[q] += Fba[q] * s;
       }
     }
   }
-  double* oe = out + e * m3;
+  T* oe = out + e * m3;
   for (int q = threadIdx.x; q < m3; q += blockDim.x) oe[q] = oacc[q];
 }
 
@@ -301,6 +306,19 @@ __global__ void k_presidual(const double* __restrict__ g, double cg, const doubl
   if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
+__global__ void k_presidual_keep(const double* __restrict__ g, double cg, const double* __restrict__ w, double cw,
+                                 double* __restrict__ r, int64_t n, double* partial) {
+  __shared__ double s[kRedThreads];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
+    const double v = (g[i] - cg) - (w[i] - cw);
+    r[i] = v;
+    acc += v * v;
+  }
+  const double t = block_sum(acc, s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
 // out[0] = sum of partial[0..cnt) (one CTA)
 __global__ void k_psum_finish(const double* __restrict__ partial, int cnt, double* out) {
   __shared__ double s[kRedThreads];
@@ -310,17 +328,35 @@ __global__ void k_psum_finish(const double* __restrict__ partial, int cnt, doubl
   if (threadIdx.x == 0) out[0] = t;
 }
 
+// FP32 copies for the mixed-precision pressure solve
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void k_to_f64(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+__global__ void k_recip_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)(1.0 / a[i]);
+}
+
+// r = (g - cg) - (w - cw) (the true residual Pm (g - E x)); partial sums of r_i r_i
+__global__ void k_presidual_keep(const double* __restrict__ g, double cg, const double* __restrict__ w, double cw,
+                                 double* __restrict__ r, int64_t n, double* partial);
+
 // ---- launchers ---------------------------------------------------------------
 
 static constexpr int kPressureThreads = 256;
 static constexpr int kPressureRedBlocks = 2 * 152;  // reduction grid: two CTAs per SM
 
 size_t gl_factors_smem(int n, int m) { return sizeof(double) * (3 * n * n * n + 6 * m * n * n); }
-static size_t pgrad_smem(int n, int m) {
-  return sizeof(double) * (2 * m * n + m * m * m + m * m * n + m * n * n + n * n * n);
+static size_t pgrad_smem(int n, int m, size_t esz) {
+  return esz * (2 * m * n + m * m * m + m * m * n + m * n * n + n * n * n);
 }
-static size_t pdiv_smem(int n, int m) {
-  return sizeof(double) * (2 * m * n + n * n * n + n * n * m + n * m * m + m * m * m);
+static size_t pdiv_smem(int n, int m, size_t esz) {
+  return esz * (2 * m * n + n * n * n + n * n * m + n * m * m + m * m * m);
 }
 
 cudaError_t launch_gl_factors(const double* xyz, const double* Ig, const double* DIg, const double* rho, int n, int m,
@@ -332,22 +368,48 @@ cudaError_t launch_gl_factors(const double* xyz, const double* Ig, const double*
   return cudaGetLastError();
 }
 
-cudaError_t launch_pgrad(const double* p, const double* F, const double* Ig, const double* DIg, int n, int m,
-                         int64_t E, double* u, int64_t n_local, cudaStream_t s) {
-  const size_t smem = pgrad_smem(n, m);
-  cudaError_t err = cudaFuncSetAttribute(k_pgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename T>
+cudaError_t launch_pgrad(const T* p, const T* F, const T* Ig, const T* DIg, int n, int m, int64_t E, T* u,
+                         int64_t n_local, cudaStream_t s) {
+  const size_t smem = pgrad_smem(n, m, sizeof(T));
+  static DeviceOnce once;
+  cudaError_t err = once.get([&](int, int*) {
+    return cudaFuncSetAttribute(k_pgrad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pgrad_smem(11 + 1, 10, sizeof(T)));
+  });
   if (err != cudaSuccess) return err;
-  k_pgrad<<<(unsigned)E, kPressureThreads, smem, s>>>(p, F, Ig, DIg, n, m, E, u, n_local);
+  k_pgrad<T><<<(unsigned)E, kPressureThreads, smem, s>>>(p, F, Ig, DIg, n, m, E, u, n_local);
   return cudaGetLastError();
 }
+template cudaError_t launch_pgrad<double>(const double*, const double*, const double*, const double*, int, int, int64_t,
+                                          double*, int64_t, cudaStream_t);
+template cudaError_t launch_pgrad<float>(const float*, const float*, const float*, const float*, int, int, int64_t,
+                                         float*, int64_t, cudaStream_t);
 
-cudaError_t launch_pdiv(const double* u, const double* dB, const double* F, const double* Ig, const double* DIg, int n,
-                        int m, int64_t E, double* out, int64_t n_local, cudaStream_t s) {
-  const size_t smem = pdiv_smem(n, m);
-  cudaError_t err = cudaFuncSetAttribute(k_pdiv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename T>
+cudaError_t launch_pdiv(const T* u, const T* dB, const T* invB, const T* F, const T* Ig, const T* DIg, int n, int m,
+                        int64_t E, T* out, int64_t n_local, cudaStream_t s) {
+  const size_t smem = pdiv_smem(n, m, sizeof(T));
+  static DeviceOnce once;
+  cudaError_t err = once.get([&](int, int*) {
+    return cudaFuncSetAttribute(k_pdiv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pdiv_smem(11 + 1, 10, sizeof(T)));
+  });
   if (err != cudaSuccess) return err;
-  k_pdiv<<<(unsigned)E, kPressureThreads, smem, s>>>(u, dB, F, Ig, DIg, n, m, E, out, n_local);
+  k_pdiv<T><<<(unsigned)E, kPressureThreads, smem, s>>>(u, dB, invB, F, Ig, DIg, n, m, E, out, n_local);
   return cudaGetLastError();
+}
+template cudaError_t launch_pdiv<double>(const double*, const double*, const double*, const double*, const double*,
+                                         const double*, int, int, int64_t, double*, int64_t, cudaStream_t);
+template cudaError_t launch_pdiv<float>(const float*, const float*, const float*, const float*, const float*,
+                                        const float*, int, int, int64_t, float*, int64_t, cudaStream_t);
+
+void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
+  k_to_f32<<<kPressureRedBlocks, kRedThreads, 0, s>>>(a, b, n);
+}
+void launch_to_f64(const float* a, double* b, int64_t n, cudaStream_t s) {
+  k_to_f64<<<kPressureRedBlocks, kRedThreads, 0, s>>>(a, b, n);
+}
+void launch_recip_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
+  k_recip_f32<<<kPressureRedBlocks, kRedThreads, 0, s>>>(a, b, n);
 }
 
 int pressure_red_blocks() { return kPressureRedBlocks; }
@@ -391,5 +453,11 @@ cudaError_t launch_presidual(const double* g, double cg, const double* w, double
   return cudaGetLastError();
 }
 
-}  // namespace sem
+cudaError_t launch_presidual_keep(const double* g, double cg, const double* w, double cw, double* r, int64_t n,
+                                  double* partial, double* out, cudaStream_t s) {
+  k_presidual_keep<<<kPressureRedBlocks, kRedThreads, 0, s>>>(g, cg, w, cw, r, n, partial);
+  k_psum_finish<<<1, kRedThreads, 0, s>>>(partial, kPressureRedBlocks, out);
+  return cudaGetLastError();
+}
 
+}  // namespace sem

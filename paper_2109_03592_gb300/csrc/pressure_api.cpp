@@ -182,12 +182,204 @@ sem_status ensure_pressure(const sem_mesh* m, cudaStream_t s) {
   return SEM_OK;
 }
 
+// FP32 copies of the GL-point data and the reciprocal of the assembled mass,
+// for the FP32 operator of the mixed-precision pressure solve (built once,
+// under the mesh's p_mutex, after the FP64 data).
+sem_status ensure_pressure32(const sem_mesh* m, cudaStream_t s) {
+  SEM_TRY_STATUS(ensure_pressure(m, s));
+  std::lock_guard<std::mutex> lk(m->p_mutex);
+  if (m->Fgl32) return SEM_OK;
+  const int N = m->N, n = N + 1, mm = N - 1;
+  const int64_t nF = (int64_t)9 * mm * mm * mm * m->E;
+  float *F = nullptr, *I = nullptr, *DI = nullptr, *iB = nullptr;
+  auto release = [&]() {
+    for (float* q : {F, I, DI, iB})
+      if (q) cudaFree(q);
+  };
+  auto fail = [&](cudaError_t e, const char* what) {
+    cudaStreamSynchronize(s);
+    release();
+    return cuda_fail(e, what);
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc((void**)&F, sizeof(float) * nF)) != cudaSuccess) return fail(e, "cudaMalloc");
+  if ((e = cudaMalloc((void**)&I, sizeof(float) * mm * n)) != cudaSuccess) return fail(e, "cudaMalloc");
+  if ((e = cudaMalloc((void**)&DI, sizeof(float) * mm * n)) != cudaSuccess) return fail(e, "cudaMalloc");
+  if ((e = cudaMalloc((void**)&iB, sizeof(float) * m->n_local)) != cudaSuccess) return fail(e, "cudaMalloc");
+  launch_to_f32(m->Fgl, F, nF, s);
+  launch_to_f32(m->Igl, I, (int64_t)mm * n, s);
+  launch_to_f32(m->DIgl, DI, (int64_t)mm * n, s);
+  launch_recip_f32(m->dB, iB, m->n_local, s);
+  count_launches(4);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e, "pressure FP32 copies");
+  sem_mesh* mut = const_cast<sem_mesh*>(m);
+  mut->dev_bytes += sizeof(float) * (nF + 2 * mm * n + m->n_local);
+  m->Igl32 = I;
+  m->DIgl32 = DI;
+  m->invB32 = iB;
+  m->Fgl32 = F;
+  return SEM_OK;
+}
+
+// q = E p in FP32: weak gradient, masked QQ^T of each component, reciprocal mass, weak divergence.
+sem_status apply_E32(const sem_mesh* m, const float* p, float* q, float* work, cudaStream_t s) {
+  const int mm = m->N - 1;
+  const GsDev g = gs_dev(m);
+  SEM_CUDA(launch_pgrad<float>(p, m->Fgl32, m->Igl32, m->DIgl32, m->n, mm, m->E, work, m->n_local, s));
+  for (int a = 0; a < 3; ++a) SEM_CUDA(launch_gs<float>(work + a * m->n_local, g, 1, nullptr, s));
+  SEM_CUDA(launch_pdiv<float>(work, nullptr, m->invB32, m->Fgl32, m->Igl32, m->DIgl32, m->n, mm, m->E, q, m->n_local,
+                              s));
+  count_launches(5);
+  return SEM_OK;
+}
+
 }  // namespace
 }  // namespace sem
 
 using namespace sem;
 
 constexpr int kPressureMaxRestarts = 5;
+constexpr int kPressureRuGap = 8;  // iterations between residual replacements of the mixed pressure CG
+
+namespace sem {
+namespace {
+
+// Mixed precision for Eq. 5: CG recurrences in FP64 on the pressure values
+// with the operator applied in FP32 (E p rounded to FP32 factors and fields,
+// the costly part: the FP64 operator runs on GB300's narrow FP64 pipe), and
+// reliable updates: when the recurrence residual has dropped by delta since the
+// last replacement (at least 8 iterations later), or below 0.2 tol, the true
+// residual Pm (g - E x) is formed with the FP64 operator and replaces it, and
+// CG continues with its direction.  The solve stops when the true residual
+// meets tol.
+sem_status pressure_solve_mixed(const sem_mesh* m, const double* g_dev, double* p_dev, double tol, int maxit,
+                                double delta, sem_solve_result* result, cudaStream_t s) {
+  SEM_TRY_STATUS(ensure_pressure32(m, s));
+  const int64_t mm = m->N - 1, np = m->E * mm * mm * mm, nl = m->n_local;
+  const int nb = pressure_red_blocks();
+  double* buf = nullptr;
+  float* buf32 = nullptr;
+  SEM_CUDA(cudaMalloc((void**)&buf, (3 * (size_t)np + 3 * (size_t)nl + nb + 1) * sizeof(double)));
+  cudaError_t e0 = cudaMalloc((void**)&buf32, (2 * (size_t)np + 3 * (size_t)nl) * sizeof(float));
+  struct Free {
+    double* b;
+    float* f;
+    ~Free() {
+      if (b) cudaFree(b);
+      if (f) cudaFree(f);
+    }
+  } guard{buf, buf32};
+  if (e0 != cudaSuccess) return cuda_fail(e0, "cudaMalloc");
+  double* r = buf;
+  double* q = r + np;
+  double* w = q + np;
+  double* work = w + np;
+  double* partial = work + 3 * nl;
+  double* sum_d = partial + nb;
+  float* q32 = buf32;
+  float* w32 = q32 + np;
+  float* work32 = w32 + np;
+  const GsDev g = gs_dev(m);
+  auto read = [&](double& v) -> sem_status {
+    SEM_CUDA(cudaMemcpyAsync(&v, sum_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    return SEM_OK;
+  };
+  cudaEvent_t ev0, ev1;
+  SEM_CUDA(cudaEventCreate(&ev0));
+  SEM_CUDA(cudaEventCreate(&ev1));
+  struct Ev {
+    cudaEvent_t a, b;
+    ~Ev() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } evguard{ev0, ev1};
+  SEM_CUDA(cudaEventRecord(ev0, s));
+  uint64_t launches = 0;
+  double gsum = 0.0, rho = 0.0;
+  SEM_CUDA(launch_pdot(g_dev, nullptr, np, partial, sum_d, s));
+  launches += 2;
+  SEM_TRY_STATUS(read(gsum));
+  SEM_CUDA(launch_pstart(g_dev, gsum / (double)np, r, q, p_dev, np, partial, sum_d, s));
+  launches += 2;
+  SEM_TRY_STATUS(read(rho));
+  const double gnorm = std::sqrt(rho);
+  constexpr double kGamma = 0.2;
+  int it = 0, outer = 0, status = SEM_OK;
+  double rel = 0.0;
+  if (gnorm > 0.0) {
+    status = SEM_ERR_NOT_CONVERGED;
+    rel = 1.0;
+    double rr_max = rho;
+    int last = 0;
+    for (it = 1; it <= maxit; ++it) {
+      // w = E q with the FP32 operator, then w -= mean(w) and sigma = <q, w> in FP64
+      launch_to_f32(q, q32, np, s);
+      SEM_TRY_STATUS(apply_E32(m, q32, w32, work32, s));
+      launch_to_f64(w32, w, np, s);
+      double wsum = 0.0, sigma = 0.0, rho_new = 0.0;
+      SEM_CUDA(launch_pdot(w, nullptr, np, partial, sum_d, s));
+      SEM_TRY_STATUS(read(wsum));
+      SEM_CUDA(launch_pshift_dot(w, q, wsum / (double)np, np, partial, sum_d, s));
+      SEM_TRY_STATUS(read(sigma));
+      launches += 6;
+      if (!(sigma > 0.0)) {
+        status = SEM_ERR_BREAKDOWN;
+        break;
+      }
+      const double alpha = rho / sigma;
+      SEM_CUDA(launch_pupdate(p_dev, r, q, w, alpha, np, partial, sum_d, s));
+      launches += 2;
+      SEM_TRY_STATUS(read(rho_new));
+      rel = std::sqrt(rho_new) / gnorm;
+      const bool converged = std::sqrt(rho_new) <= kGamma * tol * gnorm;
+      if (converged || (rho_new <= delta * delta * rr_max && it - last >= kPressureRuGap)) {
+        // replace r by the true residual Pm (g - E x) with the FP64 operator
+        SEM_CUDA(launch_pgrad<double>(p_dev, m->Fgl, m->Igl, m->DIgl, m->n, (int)mm, m->E, work, nl, s));
+        for (int a = 0; a < 3; ++a) SEM_CUDA(launch_gs<double>(work + a * nl, g, 1, nullptr, s));
+        SEM_CUDA(launch_pdiv<double>(work, m->dB, nullptr, m->Fgl, m->Igl, m->DIgl, m->n, (int)mm, m->E, w, nl, s));
+        double xs = 0.0, rho_t = 0.0;
+        SEM_CUDA(launch_pdot(w, nullptr, np, partial, sum_d, s));
+        SEM_TRY_STATUS(read(xs));
+        SEM_CUDA(launch_presidual_keep(g_dev, gsum / (double)np, w, xs / (double)np, r, np, partial, sum_d, s));
+        SEM_TRY_STATUS(read(rho_t));
+        launches += 9;
+        ++outer;
+        rel = std::sqrt(rho_t) / gnorm;
+        if (std::sqrt(rho_t) <= tol * gnorm) {
+          status = SEM_OK;
+          break;
+        }
+        rr_max = rho_t;
+        last = it;
+        SEM_CUDA(launch_pdir(q, r, rho_t / rho, np, s));
+        launches += 1;
+        rho = rho_t;
+        continue;
+      }
+      if (rho_new > rr_max) rr_max = rho_new;
+      SEM_CUDA(launch_pdir(q, r, rho_new / rho, np, s));
+      launches += 1;
+      rho = rho_new;
+    }
+    if (it > maxit) it = maxit;
+  }
+  SEM_CUDA(cudaEventRecord(ev1, s));
+  SEM_CUDA(cudaEventSynchronize(ev1));
+  float ms = 0.f;
+  SEM_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+  count_launches(launches);
+  result->iters = it;
+  result->outer_iters = outer;
+  result->rel_res = rel;
+  result->ms = ms;
+  result->status = status;
+  return (sem_status)status;
+}
+
+}  // namespace
+}  // namespace sem
 
 extern "C" {
 
@@ -243,7 +435,7 @@ sem_status sem_pressure_grad(const sem_mesh* m, const double* p_dev, double* u_d
   cudaStream_t s = (cudaStream_t)stream;
   st = ensure_pressure(m, s);
   if (st != SEM_OK) return st;
-  SEM_CUDA(launch_pgrad(p_dev, m->Fgl, m->Igl, m->DIgl, m->n, m->N - 1, m->E, u_dev, m->n_local, s));
+  SEM_CUDA(launch_pgrad<double>(p_dev, m->Fgl, m->Igl, m->DIgl, m->n, m->N - 1, m->E, u_dev, m->n_local, s));
   count_launches(1);
   return SEM_OK;
 }
@@ -258,7 +450,7 @@ sem_status sem_pressure_div(const sem_mesh* m, const double* u_dev, double* q_de
   cudaStream_t s = (cudaStream_t)stream;
   st = ensure_pressure(m, s);
   if (st != SEM_OK) return st;
-  SEM_CUDA(launch_pdiv(u_dev, nullptr, m->Fgl, m->Igl, m->DIgl, m->n, m->N - 1, m->E, q_dev, m->n_local, s));
+  SEM_CUDA(launch_pdiv<double>(u_dev, nullptr, nullptr, m->Fgl, m->Igl, m->DIgl, m->n, m->N - 1, m->E, q_dev, m->n_local, s));
   count_launches(1);
   return SEM_OK;
 }
@@ -282,11 +474,24 @@ sem_status sem_pressure_apply(const sem_mesh* m, const double* p_dev, double* q_
   st = ensure_pressure(m, s);
   if (st != SEM_OK) return st;
   const GsDev g = gs_dev(m);
-  SEM_CUDA(launch_pgrad(p_dev, m->Fgl, m->Igl, m->DIgl, m->n, m->N - 1, m->E, work_dev, m->n_local, s));
+  SEM_CUDA(launch_pgrad<double>(p_dev, m->Fgl, m->Igl, m->DIgl, m->n, m->N - 1, m->E, work_dev, m->n_local, s));
   for (int a = 0; a < 3; ++a) SEM_CUDA(launch_gs<double>(work_dev + a * m->n_local, g, 1, nullptr, s));
-  SEM_CUDA(launch_pdiv(work_dev, m->dB, m->Fgl, m->Igl, m->DIgl, m->n, m->N - 1, m->E, q_dev, m->n_local, s));
+  SEM_CUDA(launch_pdiv<double>(work_dev, m->dB, nullptr, m->Fgl, m->Igl, m->DIgl, m->n, m->N - 1, m->E, q_dev, m->n_local, s));
   count_launches(5);
   return SEM_OK;
+}
+
+sem_status sem_pressure_apply_f32(const sem_mesh* m, const float* p_dev, float* q_dev, float* work_dev, void* stream) {
+  sem_status st = check_mesh(m, "sem_pressure_apply_f32");
+  if (st != SEM_OK) return st;
+  if (!p_dev || !q_dev || !work_dev || p_dev == q_dev) {
+    set_error("sem_pressure_apply_f32: null or overlapping argument");
+    return SEM_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_pressure32(m, s);
+  if (st != SEM_OK) return st;
+  return apply_E32(m, p_dev, q_dev, work_dev, s);
 }
 
 // CG on the mean-free pressure space: Pm E Pm p = Pm g, Pm = I - 1 1^T / n_p.
@@ -308,6 +513,12 @@ sem_status sem_pressure_solve(const sem_mesh* m, const double* g_dev, double* p_
   const int maxit = opts->maxit > 0 ? opts->maxit : 20000;
   *result = sem_solve_result{0, 0, 0.0, 0.0, SEM_OK};
   cudaStream_t s = (cudaStream_t)stream;
+  if (opts->prec == SEM_MIXED)
+    return pressure_solve_mixed(m, g_dev, p_dev, tol, maxit, opts->delta > 0.0 ? opts->delta : 0.1, result, s);
+  if (opts->prec != SEM_FP64) {
+    set_error("sem_pressure_solve: prec must be SEM_FP64 or SEM_MIXED");
+    return SEM_ERR_INVALID;
+  }
   st = ensure_pressure(m, s);
   if (st != SEM_OK) return st;
   const int64_t mm = m->N - 1, np = m->E * mm * mm * mm;
@@ -355,9 +566,9 @@ sem_status sem_pressure_solve(const sem_mesh* m, const double* g_dev, double* p_
   const double gnorm = std::sqrt(rho);
   // out = E v (weak gradient, QQ^T with mask on each component, inverse mass, weak divergence)
   auto apply_E = [&](const double* v, double* out) -> sem_status {
-    SEM_CUDA(launch_pgrad(v, m->Fgl, m->Igl, m->DIgl, m->n, (int)mm, m->E, work, m->n_local, s));
+    SEM_CUDA(launch_pgrad<double>(v, m->Fgl, m->Igl, m->DIgl, m->n, (int)mm, m->E, work, m->n_local, s));
     for (int a = 0; a < 3; ++a) SEM_CUDA(launch_gs<double>(work + a * m->n_local, g, 1, nullptr, s));
-    SEM_CUDA(launch_pdiv(work, m->dB, m->Fgl, m->Igl, m->DIgl, m->n, (int)mm, m->E, out, m->n_local, s));
+    SEM_CUDA(launch_pdiv<double>(work, m->dB, nullptr, m->Fgl, m->Igl, m->DIgl, m->n, (int)mm, m->E, out, m->n_local, s));
     launches += 5;
     return SEM_OK;
   };

@@ -151,6 +151,12 @@ struct sem_mesh {
   mutable double* Fgl = nullptr;
   mutable double* Igl = nullptr;
   mutable double* DIgl = nullptr;
+  // their FP32 copies and the reciprocal assembled mass [n_local], for the
+  // FP32 operator of the mixed-precision pressure solve (built on first use)
+  mutable float* Fgl32 = nullptr;
+  mutable float* Igl32 = nullptr;
+  mutable float* DIgl32 = nullptr;
+  mutable float* invB32 = nullptr;
 
   std::mutex ws_mutex;
   sem::Workspace* ws = nullptr;  // cached solver workspace

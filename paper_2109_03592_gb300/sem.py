@@ -136,6 +136,7 @@ SIGNATURES = {
     "sem_pressure_grad": (C.c_int, [_P, _P, _P, _P]),
     "sem_pressure_div": (C.c_int, [_P, _P, _P, _P]),
     "sem_pressure_apply": (C.c_int, [_P, _P, _P, _P, _P]),
+    "sem_pressure_apply_f32": (C.c_int, [_P, _P, _P, _P, _P]),
     "sem_pressure_solve": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
 }
 
@@ -379,12 +380,24 @@ class Mesh:
                "sem_pressure_apply")
         return q
 
-    def pressure_solve(self, g, p, tol=1e-10, maxit=0, stream=None, check=False):
-        """sem_pressure_solve: E p = g on the mean-free pressure space (CG);
-        returns the result record (a dict), raising on errors other than
-        not-converged / breakdown unless check=True."""
+    def pressure_apply_f32(self, p, q, work=None, stream=None):
+        """q = E p in FP32 (sem_pressure_apply_f32); work: 3 n_local floats (allocated if None)."""
         import torch
-        o = _opts(tol=tol, maxit=maxit)
+        if work is None:
+            work = torch.empty(3 * self.n_local, dtype=torch.float32, device="cuda")
+        np_ = self.pressure_size()
+        _check(lib().sem_pressure_apply_f32(self._h, _dptr(p, torch.float32, np_), _dptr(q, torch.float32, np_),
+                                            _dptr(work, torch.float32, 3 * self.n_local), _stream(stream)),
+               "sem_pressure_apply_f32")
+        return q
+
+    def pressure_solve(self, g, p, tol=1e-10, maxit=0, stream=None, check=False, prec=FP64, delta=0.0):
+        """sem_pressure_solve: E p = g on the mean-free pressure space (CG;
+        prec=MIXED: FP32 operator with FP64 reliable updates); returns the
+        result record (a dict), raising on errors other than not-converged /
+        breakdown unless check=True."""
+        import torch
+        o = _opts(tol=tol, maxit=maxit, prec=prec, delta=delta)
         r = SolveResult()
         np_ = self.pressure_size()
         st = lib().sem_pressure_solve(self._h, _dptr(g, torch.float64, np_), _dptr(p, torch.float64, np_),

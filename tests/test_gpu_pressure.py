@@ -236,3 +236,61 @@ def test_pressure_solve_on_the_4096_element_pipe():
     assert (res.norm() / gm.norm()).item() <= 2e-10
     assert abs(x.sum().item()) <= 1e-10 * x.abs().sum().item()
     m.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp32_operator_matches_oracle(name):
+    """The FP32 form of E (factors, basis and fields rounded from FP64) against
+    the oracle's FP64 E: the rounding-level bound of FP32 sum factorisation."""
+    import torch
+    m, P = setup(name)
+    p = np.random.default_rng(6).standard_normal(P.shape)
+    q = torch.full(P.shape, float("nan"), dtype=torch.float32, device="cuda")
+    m.pressure_apply_f32(to_gpu(p).float(), q)
+    assert relerr(q.double().cpu().numpy(), P.E(p)) <= 2e-5
+
+
+@pytest.mark.parametrize("name", list(SOLVE_CASES))
+def test_mixed_pressure_solve_meets_the_fp64_tolerance(name):
+    """The mixed-precision pressure CG (FP32 E, FP64 reliable updates): the
+    GPU solution's residual Pm (g - E x) recomputed with the oracle's FP64 E
+    meets 1e-10, the solution is mean-free and matches the FP64 solve."""
+    import torch
+    import paper_2109_03592_gb300 as sem
+    desc = SOLVE_CASES[name]
+    m = sem.Mesh(desc)
+    P = pressure.Pressure(solver.Problem(_oracle_mesh(desc)))
+    g = np.random.default_rng(12).standard_normal(P.shape)
+    x = torch.full(P.shape, float("nan"), dtype=torch.float64, device="cuda")
+    r = m.pressure_solve(to_gpu(g), x, tol=1e-10, prec=sem.MIXED)
+    assert r["status"] == 0, r
+    assert r["rel_res"] <= 1e-10 and r["outer_iters"] >= 1
+    xg = x.cpu().numpy()
+    gm = g - g.mean()
+    res = g - P.E(xg)
+    res = res - res.mean()
+    assert np.linalg.norm(res) <= 1.5e-10 * np.linalg.norm(gm)
+    assert abs(xg.sum()) <= 1e-10 * np.abs(xg).sum()
+    x64 = torch.empty_like(x)
+    r64 = m.pressure_solve(to_gpu(g), x64, tol=1e-10)
+    assert relerr(xg, x64.cpu().numpy()) <= 1e-6
+    assert r["iters"] <= 2 * r64["iters"] + 20, (r, r64)
+    m.close()
+
+
+def test_mixed_pressure_solve_on_the_4096_element_pipe():
+    import torch
+    import paper_2109_03592_gb300 as sem
+    m = sem.Mesh(configs.mesh_desc("pipe4096_n7"))
+    g = torch.randn(m.pressure_shape, dtype=torch.float64, device="cuda",
+                    generator=torch.Generator(device="cuda").manual_seed(4))
+    x = torch.empty_like(g)
+    r = m.pressure_solve(g, x, tol=1e-10, prec=sem.MIXED)
+    assert r["status"] == 0, r
+    Ex = torch.empty_like(g)
+    m.pressure_apply(x, Ex)
+    res = g - Ex
+    res -= res.mean()
+    gm = g - g.mean()
+    assert (res.norm() / gm.norm()).item() <= 2e-10
+    m.close()
