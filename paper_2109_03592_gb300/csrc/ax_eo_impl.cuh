@@ -19,10 +19,6 @@
 // pre-added values go through shared memory, where the contractions of the
 // other threads of the element read them.
 //
-// The contractions run their two accumulators (Ap, Bm) in the two lanes of
-// packed FP32 instructions (f32x2, sm_100 and later): one issue slot for two
-// lanes, the same rounding per lane.
-//
 // Values are kept as unnormalised pairs (s, c) with |c| of the order of the
 // rounding errors of the magnitudes summed into s; such a pair enters the
 // next product exactly like a normalised one, so the error stays ~2^-48 of
@@ -102,87 +98,6 @@ __device__ __forceinline__ Pair add(Pair a, Pair b) {
   return Pair{t, __fadd_rn(e, __fadd_rn(a.c, b.c))};
 }
 __device__ __forceinline__ Pair sub(Pair a, Pair b) { return add(a, Pair{-b.s, -b.c}); }
-
-// ---- two lanes at once: the packed FP32 instructions of sm_100+ ----------------
-// (add/sub/mul/fma.rn.f32x2, each lane rounded as its scalar instruction, so
-// every error-free transformation below holds lane by lane).  One packed
-// instruction issues in the slot of one scalar one; the contractions are
-// FP32-issue bound, and their two accumulators Ap and Bm share every step.
-typedef unsigned long long f2;
-__device__ __forceinline__ f2 pk2(float a, float b) {
-  f2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void upk2(f2 v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
-__device__ __forceinline__ f2 add2(f2 a, f2 b) {
-  f2 d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
-  f2 d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
-  f2 d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
-  f2 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-
-// A packed pair of double-float accumulators: value = s - nc in each lane
-// (nc holds the negated low parts, so the product errors come from FMAs with
-// negated coefficients and no extra negation).
-struct Acc2 {
-  f2 s, nc;
-};
-
-// Coefficients of one (output pair, l): ch = (Ep.hi, Em.hi), nch = -ch, ncl = -(Ep.lo, Em.lo).
-struct Coef2 {
-  f2 ch, nch, ncl;
-};
-
-__device__ __forceinline__ Coef2 coef2(float4 c) {  // c = (Ep.hi, Ep.lo, Em.hi, Em.lo)
-  return Coef2{pk2(c.x, c.z), pk2(-c.x, -c.z), pk2(-c.y, -c.w)};
-}
-
-// A = c * v for the lane pair, v = (vh, vl) packed (P lane, M lane)
-__device__ __forceinline__ Acc2 prod2(const Coef2& c, f2 vh, f2 vl) {
-  const f2 p = mul2(c.ch, vh);
-  f2 npe = fma2(c.nch, vh, p);  // p - ch vh = -(error of p), exactly
-  npe = fma2(c.nch, vl, npe);
-  npe = fma2(c.ncl, vh, npe);
-  return Acc2{p, npe};
-}
-
-// A += c * v (product error and Knuth's TwoSum error folded into A.nc)
-__device__ __forceinline__ void madd2(Acc2& A, const Coef2& c, f2 vh, f2 vl) {
-  const f2 p = mul2(c.ch, vh);
-  f2 npe = fma2(c.nch, vh, p);
-  npe = fma2(c.nch, vl, npe);
-  npe = fma2(c.ncl, vh, npe);
-  const f2 cc = add2(A.nc, npe);
-  const f2 t = add2(A.s, p);
-  const f2 bp = sub2(t, A.s);
-  const f2 e = add2(sub2(A.s, sub2(t, bp)), sub2(p, bp));
-  A.s = t;
-  A.nc = sub2(cc, e);
-}
-
-// the two lanes as (Ap, Bm) pairs
-__device__ __forceinline__ void unpack_acc(const Acc2& A, Pair& Ap, Pair& Bm) {
-  float s0, s1, n0, n1;
-  upk2(A.s, s0, s1);
-  upk2(A.nc, n0, n1);
-  Ap = Pair{s0, -n0};
-  Bm = Pair{s1, -n1};
-}
 
 // Shared-memory index of point (i, j, k) in one element's array of float2.
 // n = 8: XOR swizzle of i by (j, k) -- every access pattern of the kernel
@@ -315,15 +230,15 @@ __global__ void __launch_bounds__(EPB* eo_threads_per_element<N>(), eo_min_block
   Pair g[3][8];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    Coef2 cf[h];
+    float4 cf[h];
     const int own = d == 0 ? a : d == 1 ? b : c;
 #pragma unroll
-    for (int l = 0; l < h; ++l) cf[l] = coef2(sC[own * h + l]);
+    for (int l = 0; l < h; ++l) cf[l] = sC[own * h + l];
 #pragma unroll
     for (int x = 0; x < 2; ++x)
 #pragma unroll
       for (int y = 0; y < 2; ++y) {
-        Acc2 A2;
+        Pair Ap, Bm;
 #pragma unroll
         for (int l = 0; l < h; ++l) {
           float2 pv, mv;
@@ -337,14 +252,14 @@ __global__ void __launch_bounds__(EPB* eo_threads_per_element<N>(), eo_min_block
             pv = S2[L::idx(I[x], J[y], l)];
             mv = S2[L::idx(I[x], J[y], n - 1 - l)];
           }
-          const f2 vh = pk2(pv.x, mv.x), vl = pk2(pv.y, mv.y);
-          if (l == 0)
-            A2 = prod2(cf[0], vh, vl);
-          else
-            madd2(A2, cf[l], vh, vl);
+          if (l == 0) {
+            Ap = prod(cf[0].x, cf[0].y, pv.x, pv.y);
+            Bm = prod(cf[0].z, cf[0].w, mv.x, mv.y);
+          } else {
+            madd(Ap, cf[l].x, cf[l].y, pv.x, pv.y);
+            madd(Bm, cf[l].z, cf[l].w, mv.x, mv.y);
+          }
         }
-        Pair Ap, Bm;
-        unpack_acc(A2, Ap, Bm);
         // the pair's low point gets Bm + Ap, its high point Bm - Ap
         const int q0 = d == 0 ? 2 * x + 4 * y : d == 1 ? x + 4 * y : x + 2 * y;
         const int q1 = q0 + (d == 0 ? 1 : d == 1 ? 2 : 4);
@@ -410,15 +325,15 @@ __global__ void __launch_bounds__(EPB* eo_threads_per_element<N>(), eo_min_block
   Pair o[8];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    Coef2 cf[h];
+    float4 cf[h];
     const int own = d == 0 ? a : d == 1 ? b : c;
 #pragma unroll
-    for (int l = 0; l < h; ++l) cf[l] = coef2(sC[h * h + own * h + l]);
+    for (int l = 0; l < h; ++l) cf[l] = sC[h * h + own * h + l];
 #pragma unroll
     for (int x = 0; x < 2; ++x)
 #pragma unroll
       for (int y = 0; y < 2; ++y) {
-        Acc2 A2;
+        Pair Ap, Bm;
 #pragma unroll
         for (int l = 0; l < h; ++l) {
           float2 pv, mv;
@@ -432,14 +347,14 @@ __global__ void __launch_bounds__(EPB* eo_threads_per_element<N>(), eo_min_block
             pv = S2[L::idx(I[x], J[y], l)];
             mv = S2[L::idx(I[x], J[y], n - 1 - l)];
           }
-          const f2 vh = pk2(pv.x, mv.x), vl = pk2(pv.y, mv.y);
-          if (l == 0)
-            A2 = prod2(cf[0], vh, vl);
-          else
-            madd2(A2, cf[l], vh, vl);
+          if (l == 0) {
+            Ap = prod(cf[0].x, cf[0].y, pv.x, pv.y);
+            Bm = prod(cf[0].z, cf[0].w, mv.x, mv.y);
+          } else {
+            madd(Ap, cf[l].x, cf[l].y, pv.x, pv.y);
+            madd(Bm, cf[l].z, cf[l].w, mv.x, mv.y);
+          }
         }
-        Pair Ap, Bm;
-        unpack_acc(A2, Ap, Bm);
         const int q0 = d == 0 ? 2 * x + 4 * y : d == 1 ? x + 4 * y : x + 2 * y;
         const int q1 = q0 + (d == 0 ? 1 : d == 1 ? 2 : 4);
         if (d == 0) {
