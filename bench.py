@@ -431,6 +431,10 @@ def pressure_leg(m, stream, reps):
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
     apply_ms = time_kernel(lambda: m.pressure_apply(p, q, work), reps, stream)
+    p32, q32, work32 = p.float(), q.float(), work.float()
+    m.pressure_apply_f32(p32, q32, work32)
+    apply32_ms = time_kernel(lambda: m.pressure_apply_f32(p32, q32, work32), reps, stream)
+    del p32, q32, work32
     u = work.view((3,) + m.shape)
     grad_ms = time_kernel(lambda: m.pressure_grad(p, u), reps, stream)
     div_ms = time_kernel(lambda: m.pressure_div(u, q), reps, stream)
@@ -440,7 +444,8 @@ def pressure_leg(m, stream, reps):
     dofs = m.E * m3
     del p, q, work, u
     return {"workload": f"E={m.E} N={m.N}: {dofs} pressure values on the GL points",
-            "apply_ms": apply_ms, "grad_ms": grad_ms, "div_ms": div_ms, "first_call_ms": setup_ms,
+            "apply_ms": apply_ms, "apply_fp32_ms": apply32_ms, "grad_ms": grad_ms, "div_ms": div_ms,
+            "first_call_ms": setup_ms,
             "gdofs": dofs / (apply_ms * 1e6),
             "algorithmic_gbs": bytes_el * m.E / (apply_ms * 1e6),
             "fp64_tflops": 2 * fma_el * m.E / (apply_ms * 1e9),
@@ -448,10 +453,12 @@ def pressure_leg(m, stream, reps):
 
 
 def pressure_solve_leg(workload="pipe4096_n7", tol=1e-10):
-    """One solve of the pressure equation E p = g (Sec. 2, Eq. 5) on the
+    """Solves of the pressure equation E p = g (Sec. 2, Eq. 5) on the
     mean-free space (sem_pressure_solve, CG) on the E = 4096 pipe, the paper's
-    per-GPU regime, g a seeded standard-normal pressure field.  The first
-    operator call (which builds the GL-point factors) is made before timing."""
+    per-GPU regime, g a seeded standard-normal pressure field: FP64, and mixed
+    precision (FP32 E, FP64 reliable updates).  The first operator calls
+    (which build the GL-point factors and their FP32 copies) are made before
+    timing."""
     import torch
     import paper_2109_03592_gb300 as sem
     from sem_inputs import configs
@@ -460,11 +467,15 @@ def pressure_solve_leg(workload="pipe4096_n7", tol=1e-10):
                     generator=torch.Generator(device="cuda").manual_seed(4))
     x = torch.empty_like(g)
     m.pressure_apply(g, x)
+    m.pressure_apply_f32(g.float(), x.float())
     torch.cuda.synchronize()
     r = m.pressure_solve(g, x, tol=tol)
     out = {"workload": f"{workload}: E={m.E} N={m.N}, {m.pressure_size()} pressure values", "tol": tol,
            "iters": r["iters"], "ms": r["ms"], "ms_per_iter": r["ms"] / max(1, r["iters"]),
            "rel_res": r["rel_res"], "status": r["status"]}
+    rm = m.pressure_solve(g, x, tol=tol, prec=sem.MIXED)
+    out["mixed"] = {"iters": rm["iters"], "replacements": rm["outer_iters"], "ms": rm["ms"], "rel_res": rm["rel_res"],
+                    "status": rm["status"]}
     m.close()
     return out
 
@@ -498,10 +509,12 @@ def compact_velocity(v):
 def compact_pressure(p):
     if not p or "error" in p:
         return p
-    out = {k: p[k] for k in ("apply_ms", "grad_ms", "div_ms", "gdofs", "fp64_tflops", "algorithmic_gbs") if k in p}
+    out = {k: p[k] for k in ("apply_ms", "apply_fp32_ms", "grad_ms", "div_ms", "gdofs", "fp64_tflops",
+                             "algorithmic_gbs") if k in p}
     if "solve" in p:
         sv = p["solve"]
-        out["solve"] = sv if "error" in sv else {k: sv[k] for k in ("iters", "ms", "rel_res", "status")}
+        out["solve"] = sv if "error" in sv else {k: sv[k] for k in ("iters", "ms", "rel_res", "status", "mixed")
+                                                  if k in sv}
     return _sig(out)
 
 
