@@ -459,6 +459,10 @@ sem_status sem_schwarz_setup_host(int64_t E, int N, const int64_t* glo, const do
  *   bisection), so M stays a fixed SPD operator. */
 typedef struct sem_schwarz sem_schwarz;
 #define SEM_SCHWARZ_COARSE 1             /* flags: include the coarse-grid term */
+#define SEM_SCHWARZ_FP32_PRECOND 2       /* flags: SEM_FP64 solves apply the FP32 preconditioner
+                                            (z = M32 float(r), back to FP64): FP64 CG at the cost of
+                                            the FP32 application; M is then not exactly linear, which
+                                            CG tolerates at the 1e-7 level of FP32 rounding */
 #define SEM_SCHWARZ_DENSE_COARSE_MAX 8192
 
 typedef struct {

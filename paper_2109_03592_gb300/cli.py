@@ -6,12 +6,16 @@
     python -m paper_2109_03592_gb300.cli ax --workload pipe262144_n7 --prec fp32 --coef
     python -m paper_2109_03592_gb300.cli pressure --workload pipe32768_n7 [--reps 10]
     python -m paper_2109_03592_gb300.cli psolve --workload pipe4096_n7 [--tol 1e-10]
+    python -m paper_2109_03592_gb300.cli schwarz --workload pipe262144_n7 --prec mixed [--no-coarse]
 
 pressure times the consistent Poisson operator E = D B^-1 D^T of the
 P_N - P_{N-2} pressure space (sem_pressure_apply; --prec fp32:
 sem_pressure_apply_f32); psolve solves E p = g on the mean-free pressure
 space (sem_pressure_solve, --prec fp64 or mixed) for a seeded
 standard-normal g.
+
+schwarz solves with the overlapping Schwarz preconditioner (sem_schwarz_*)
+instead of Jacobi.
 
 --coef gives the mesh seeded per-point coefficients h1(i,j,k,e), h2(i,j,k,e)
 (a variable viscosity and mass coefficient) before the timed calls, which then
@@ -90,7 +94,7 @@ def _pressure(args):
 def main(argv=None):
     from . import sem
     ap = argparse.ArgumentParser(prog="python -m paper_2109_03592_gb300.cli")
-    ap.add_argument("what", choices=["solve", "ax", "gs", "pressure", "psolve"])
+    ap.add_argument("what", choices=["solve", "ax", "gs", "pressure", "psolve", "schwarz"])
     ap.add_argument("--workload", default="pipe32768_n7")
     ap.add_argument("--prec", default="mixed", choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--tol", type=float, default=1e-10)
@@ -98,6 +102,7 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--coef", action="store_true", help="per-point h1, h2 on the mesh (h1 = h2 = 1 in the calls)")
     ap.add_argument("--helmholtz", action="store_true", help="h2 = 1 (the mass term) with scalar coefficients")
+    ap.add_argument("--no-coarse", action="store_true", help="schwarz: local solves only")
     args = ap.parse_args(argv)
     import torch
     prec = {"fp64": sem.FP64, "fp32": sem.FP32, "mixed": sem.MIXED}[args.prec]
@@ -108,7 +113,16 @@ def main(argv=None):
     if args.coef:
         _set_coefficients(m)
         h2 = 1.0
-    if args.what == "solve":
+    if args.what == "schwarz":
+        sw = sem.Schwarz(m, h1, h2, coarse=not args.no_coarse)
+        x = torch.zeros_like(b)
+        for _ in range(args.repeat):
+            x.zero_()
+            r = sw.solve(b, x, tol=args.tol, prec=prec, h1=h1, h2=h2)
+            print(json.dumps({"workload": args.workload, "prec": args.prec, "preconditioner": "schwarz",
+                              **sw.info(), **r}), flush=True)
+        sw.close()
+    elif args.what == "solve":
         x = torch.zeros_like(b)
         for _ in range(args.repeat):
             x.zero_()

@@ -66,16 +66,11 @@ __device__ __forceinline__ void line_contract(const T* __restrict__ S, const T (
   }
 }
 
-// Three resident CTAs per SM for FP32 at n <= 8 (<= 85 registers): measured at
-// two CTAs (110 registers) the kernel was latency bound at 24% warp occupancy.
-template <typename T, int threads>
-constexpr int fdm_min_blocks() {
-  return (sizeof(T) == 4 && threads >= 192) ? 3 : 1;
-}
-
+// Registers: 110 at N = 7 in FP32 (two CTAs of 256 threads per SM).  Forcing
+// three CTAs per SM (80 registers, with spills) measured slower: one FP32
+// application at E = 262,144 took 1.43 ms instead of 1.32 ms.
 template <int N, typename T, int EPB>
-__global__ void __launch_bounds__(EPB*(N + 1) * (N + 1), fdm_min_blocks<T, EPB*(N + 1) * (N + 1)>())
-    k_fdm(const FdmParams<T> P) {
+__global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_fdm(const FdmParams<T> P) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
   using L = FdmLay<n, T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];

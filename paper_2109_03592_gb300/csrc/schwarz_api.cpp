@@ -39,6 +39,7 @@ struct sem_schwarz {
   uint64_t coef_gen = 0;
   int64_t nd = 0;
   int coarse = 0;  // 1: dense A_0^{-1}; 2: one symmetric two-level cycle on A_0
+  bool prec32 = false;  // FP64 solves apply the FP32 preconditioner
   int nc = 0;      // coarse unknowns
   size_t dev_bytes = 0;
   double setup_ms = 0.0;
@@ -487,12 +488,31 @@ sem_status iter_t(sem_schwarz* sw, bool f32) {
     VecParams<double> v{ws->x, ws->r, ws->z, ws->p, ws->w, nullptr, ws->b, m->wm, ws->n, ws->st, ws->part_vec};
     SEM_CUDA(launch_pcg_update<double>(v, ws->s, true));
     count_launches(3);
+    if (sw->prec32) {  // z = M32 float(r), back to FP64 with <r, z> and beta
+      launch_scale_to_f32(ws->r32, ws->r, 1.0, ws->n, ws->s);
+      SW_TRY(apply_t<float>(sw, ws->r32, ws->z32, ws->st, nullptr, false, ws->s));
+      SEM_CUDA((launch_pcg_rho<double, float>(ws->r, ws->z32, ws->z, 1.0, m->wm, ws->n, ws->st, ws->part_vec, ws->s)));
+      count_launches(2);
+      return SEM_OK;
+    }
     SW_TRY(apply_t<double>(sw, ws->r, ws->z, ws->st, ws->part_vec, fused_rho, ws->s));
     if (!fused_rho) {
       SEM_CUDA((launch_pcg_rho<double, double>(ws->r, ws->z, nullptr, 1.0, m->wm, ws->n, ws->st, ws->part_vec, ws->s)));
       count_launches(1);
     }
   }
+  return SEM_OK;
+}
+
+// z = M r for an FP64 r outside the iteration: the FP64 preconditioner, or the FP32 one.
+sem_status apply64(sem_schwarz* sw) {
+  Workspace* ws = sw->ws;
+  if (!sw->prec32) return apply_t<double>(sw, ws->r, ws->z, nullptr, nullptr, false, ws->s);
+  launch_scale_to_f32(ws->r32, ws->r, 1.0, ws->n, ws->s);
+  SW_TRY(apply_t<float>(sw, ws->r32, ws->z32, nullptr, nullptr, false, ws->s));
+  launch_to_f64(ws->z32, ws->z, ws->n, ws->s);
+  count_launches(2);
+  SEM_CUDA(cudaGetLastError());
   return SEM_OK;
 }
 
@@ -560,7 +580,7 @@ sem_status pcg64(sem_schwarz* sw, double tol, int maxit, Out& res) {
   for (int pass = 0;; ++pass) {
     SW_TRY(put_state(ws, tol, maxit - res.iters, 0));
     SW_TRY(true_residual(sw, 1));
-    SW_TRY(apply_t<double>(sw, ws->r, ws->z, nullptr, nullptr, false, ws->s));
+    SW_TRY(apply64(sw));
     VecParams<double> v{ws->x, ws->r, ws->z, ws->p, ws->w, nullptr, ws->b, m->wm, ws->n, ws->st, ws->part_vec};
     SEM_CUDA(launch_pcg_init<double>(v, ws->s, true));
     count_launches(1);
@@ -730,6 +750,7 @@ sem_status sem_schwarz_create(const sem_mesh* mesh, double h1, double h2, int fl
   if ((st = upload(&sw->wtab32, wtab32.data(), wtab32.size(), tb, s)) != SEM_OK) return fail(st);
   if ((st = upload(&sw->ftab64, ftab.data(), ftab.size(), tb, s)) != SEM_OK) return fail(st);
   if ((st = upload(&sw->ftab32, ftab32.data(), ftab32.size(), tb, s)) != SEM_OK) return fail(st);
+  sw->prec32 = (flags & SEM_SCHWARZ_FP32_PRECOND) != 0;
   if (flags & SEM_SCHWARZ_COARSE) {
     // SEM_SCHWARZ_DENSE_MAX lowers the dense limit (to compare the two coarse forms on one mesh)
     int dense_max = SEM_SCHWARZ_DENSE_COARSE_MAX;

@@ -549,6 +549,7 @@ class Projection:
 
 
 SCHWARZ_COARSE = 1
+SCHWARZ_FP32_PRECOND = 2
 SCHWARZ_DENSE_COARSE_MAX = 8192
 
 
@@ -557,10 +558,10 @@ class Schwarz:
     (sem_schwarz_*): fast-diagonalisation local solves on the elements with
     the symmetric mult^-1/2 weights, plus the trilinear coarse grid."""
 
-    def __init__(self, mesh, h1=1.0, h2=0.0, coarse=True):
+    def __init__(self, mesh, h1=1.0, h2=0.0, coarse=True, fp32_precond=False):
         h = C.c_void_p()
-        _check(lib().sem_schwarz_create(mesh._h, float(h1), float(h2), SCHWARZ_COARSE if coarse else 0, C.byref(h)),
-               "sem_schwarz_create")
+        flags = (SCHWARZ_COARSE if coarse else 0) | (SCHWARZ_FP32_PRECOND if fp32_precond else 0)
+        _check(lib().sem_schwarz_create(mesh._h, float(h1), float(h2), flags, C.byref(h)), "sem_schwarz_create")
         self._h, self.mesh, self.h1, self.h2 = h, mesh, float(h1), float(h2)
 
     def info(self):

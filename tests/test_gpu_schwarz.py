@@ -170,3 +170,24 @@ def test_invalid_arguments():
     assert ei.value.status == sem.SEM_ERR_INVALID
     sw.close()
     m.close()
+
+
+@pytest.mark.parametrize("name", ["box322_n7", "pipe423_n5"])
+def test_fp64_solve_with_the_fp32_preconditioner(name):
+    """FP64 CG with z = M32 float(r): the oracle's residual meets 1e-10, in
+    about as many iterations as with the FP64 preconditioner."""
+    import torch
+    import paper_2109_03592_gb300 as sem
+    m, P = _make(name)
+    b = _rhs(P, 14, CASES[name][0].get("L", 1.0))
+    bt = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bt)
+    ref = sem.Schwarz(m).solve(bt, x, tol=1e-10)
+    sw = sem.Schwarz(m, fp32_precond=True)
+    x.zero_()
+    res = sw.solve(bt, x, tol=1e-10)
+    assert res["status"] == 0, res
+    assert _rel_residual(P, b, x.cpu().numpy()) <= 1.1e-10
+    assert abs(res["iters"] - ref["iters"]) <= max(3, ref["iters"] // 10), (res, ref)
+    sw.close()
+    m.close()
