@@ -536,7 +536,8 @@ sem_status sem_server_poll(sem_server* srv, uint64_t req_id, int timeout_ms, dou
  * queue_ms: submit until a slot takes it (slots and HBM budget); setup_ms:
  * building its mesh and b = mask QQ^T (B f); wait_ms: until its engine admits
  * it into the running batch (0 when solved alone); solve_ms: until its result
- * is copied out; total_ms: submit until the result is visible to poll. */
+ * is copied out; total_ms: submit until the result is visible to poll
+ * (completion), whenever the caller polls. */
 typedef struct {
   double queue_ms, setup_ms, wait_ms, solve_ms, total_ms;
 } sem_request_timing;

@@ -440,7 +440,6 @@ sem_status sem_server_poll_timed(sem_server* srv, uint64_t req_id, int timeout_m
   if (x_host && !q->x.empty()) std::memcpy(x_host, q->x.data(), q->x.size() * sizeof(double));
   if (result) *result = q->res;
   if (timing) {
-    const auto now = Request::Clock::now();
     const bool ran = q->t_admit.time_since_epoch().count() != 0;  // not cancelled while queued
     const bool staged = q->t_staged.time_since_epoch().count() != 0;
     const bool solved = q->t_solve.time_since_epoch().count() != 0;
@@ -448,7 +447,7 @@ sem_status sem_server_poll_timed(sem_server* srv, uint64_t req_id, int timeout_m
     timing->setup_ms = ran && staged ? ms_between(q->t_admit, q->t_staged) : 0.0;
     timing->wait_ms = staged && solved ? ms_between(q->t_staged, q->t_solve) : 0.0;
     timing->solve_ms = solved ? ms_between(q->t_solve, q->t_done) : 0.0;
-    timing->total_ms = ms_between(q->t_submit, now);
+    timing->total_ms = ms_between(q->t_submit, q->t_done);
   }
   srv->reqs.erase(req_id);
   if (q->status != SEM_OK && !q->error.empty()) sem::set_error(q->error);
