@@ -173,6 +173,51 @@ def _oracle_slab_worker(budget_s):
     return k * m.E * 512 / el, k, el
 
 
+def _oracle_full_solve(workload):
+    """One complete FP64 Jacobi-PCG solve by the oracle on the host (one
+    core): the small configurations it can finish, with their own iteration
+    counts.  Returns (iterations, seconds, relative residual)."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    from oracle import mesh as omesh, solver as osolver
+    from sem_inputs import configs, forcing
+    d = configs.mesh_desc(workload)
+    if d["kind"] == "box":
+        m = omesh.box(d["nx"], d["ny"], d["nz"], d["N"], d["lx"], d["ly"], d["lz"])
+        f = forcing.manufactured(m.xyz)
+    else:
+        m = omesh.pipe(d["nc"], d["nr"], d["nzp"], d["N"], R=d["R"], L=d["L"], a=d["a"], beta=d["beta"], periodic=True)
+        f = forcing.evaluate(m.xyz, forcing.random_modes(2, L=d["L"]))
+    P = osolver.Problem(m)
+    b = P.rhs(f)
+    t0 = time.perf_counter()
+    res = osolver.pcg(P, b, tol=1e-10)
+    return res.iters, time.perf_counter() - t0, float(res.rel_res)
+
+
+def start_oracle_full_solves(workloads=("box4_n7", "pipe4096_n7")):
+    """The oracle's full solves of the small configurations, in spawned
+    processes started before the GPU legs (they run alongside them)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(len(workloads))
+    return pool, {w: pool.apply_async(_oracle_full_solve, (w,)) for w in workloads}
+
+
+def collect_oracle_full_solves(handle, timeout_s=120.0):
+    pool, jobs = handle
+    out = {}
+    t_end = time.perf_counter() + timeout_s
+    for w, job in jobs.items():
+        try:
+            it, sec, rel = job.get(timeout=max(1.0, t_end - time.perf_counter()))
+            out[w] = {"iters": it, "seconds": sec, "solves_per_s": 1.0 / sec, "rel_res": rel, "cores": 1}
+        except Exception as e:  # not finished within the bench's time: reported, not waited for
+            out[w] = {"error": f"{type(e).__name__}: not finished within the bench run"}
+    pool.terminate()
+    return out
+
+
 def host_cpu():
     """(logical cores, CPU model) of this host."""
     model = None
@@ -636,6 +681,9 @@ def run_gpu(args):
         if world > 1:
             dist.barrier()
 
+    full_cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        full_cpu = start_oracle_full_solves()
     desc = configs.mesh_desc(args.workload)
     t0 = time.perf_counter()
     m = sem.Mesh(desc)
@@ -769,6 +817,8 @@ def run_gpu(args):
             sec = sec_pt * P * iters_cpu
             cpu = {"value": 1.0 / sec, "unit": "solves/s", "cores": cores, "cpu": model, "kind": "oracle",
                    "sample": desc_s + f" and {iters_cpu} iterations (the FP64 PCG count of this system)"}
+            if full_cpu is not None:
+                cpu["full_solves"] = _sig(collect_oracle_full_solves(full_cpu))
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,

@@ -47,28 +47,72 @@ struct FdmLay {
   }
 };
 
+// Rows of the 1D matrices are read with volatile vector loads from shared
+// memory, at the point of use: the compiler then neither hoists the whole
+// n x n matrix into registers (110 registers at N = 7 with plain loads, two
+// CTAs per SM) nor merges the loads of the forward and back contractions.
+__device__ __forceinline__ float4 lds4(const float* p) {
+  float4 v;
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ double2 lds2(const double* p) {
+  double2 v;
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a));
+  return v;
+}
+
+// row[0..n) = S[r * n .. r * n + n) (16-byte aligned rows when n is a multiple
+// of the vector width; scalar loads otherwise)
+template <int n, typename T>
+__device__ __forceinline__ void load_row(const T* __restrict__ S, int r, T (&row)[n]) {
+  if constexpr (sizeof(T) == 4 && n % 4 == 0) {
+#pragma unroll
+    for (int c = 0; c < n; c += 4) {
+      const float4 v = lds4(reinterpret_cast<const float*>(S) + r * n + c);
+      row[c] = v.x, row[c + 1] = v.y, row[c + 2] = v.z, row[c + 3] = v.w;
+    }
+  } else if constexpr (sizeof(T) == 8 && n % 2 == 0) {
+#pragma unroll
+    for (int c = 0; c < n; c += 2) {
+      const double2 v = lds2(reinterpret_cast<const double*>(S) + r * n + c);
+      row[c] = v.x, row[c + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < n; ++c) row[c] = S[r * n + c];
+  }
+}
+
 // out[c] = sum_l S[l][c] x[l] (trans = false) or sum_l S[c][l] x[l] (trans =
 // true) for the n x n matrix S in shared memory, rows read as broadcasts.
 template <int n, typename T, bool TRANS>
 __device__ __forceinline__ void line_contract(const T* __restrict__ S, const T (&x)[n], T (&out)[n]) {
 #pragma unroll
   for (int c = 0; c < n; ++c) out[c] = T(0);
+  T row[n];
   if constexpr (!TRANS) {
 #pragma unroll
-    for (int l = 0; l < n; ++l)
+    for (int l = 0; l < n; ++l) {
+      load_row<n, T>(S, l, row);
 #pragma unroll
-      for (int c = 0; c < n; ++c) out[c] += S[l * n + c] * x[l];
+      for (int c = 0; c < n; ++c) out[c] += row[c] * x[l];
+    }
   } else {
 #pragma unroll
-    for (int c = 0; c < n; ++c)
+    for (int c = 0; c < n; ++c) {
+      load_row<n, T>(S, c, row);
 #pragma unroll
-      for (int l = 0; l < n; ++l) out[c] += S[c * n + l] * x[l];
+      for (int l = 0; l < n; ++l) out[c] += row[l] * x[l];
+    }
   }
 }
 
-// Registers: 110 at N = 7 in FP32 (two CTAs of 256 threads per SM).  Forcing
-// three CTAs per SM (80 registers, with spills) measured slower: one FP32
-// application at E = 262,144 took 1.43 ms instead of 1.32 ms.
+// (With the 1D matrices hoisted into registers, 110 registers at N = 7 in
+// FP32; forcing three CTAs per SM then spilled and measured slower, 1.43 ms
+// instead of 1.32 ms for one FP32 application at E = 262,144.)
 template <int N, typename T, int EPB>
 __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_fdm(const FdmParams<T> P) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
@@ -348,11 +392,13 @@ struct RhoAccF32 {  // Knuth's TwoSum on the FP32 pipe
   __device__ __forceinline__ double get() const { return (double)s + (double)c; }
 };
 
-template <typename T, int EPB>
-__global__ void k_prolong_rho(T* __restrict__ z, const T* __restrict__ r, const uint8_t* __restrict__ wm,
-                              const T* __restrict__ ftab, const int32_t* __restrict__ cidx, const double* __restrict__ y,
-                              int n, int64_t E, PcgState* st, double* __restrict__ partial) {
+template <typename T, int n, int EPB>
+__global__ void __launch_bounds__(((EPB * n * n + 31) / 32) * 32)
+    k_prolong_rho(T* __restrict__ z, const T* __restrict__ r, const uint8_t* __restrict__ wm,
+                  const T* __restrict__ ftab, const int32_t* __restrict__ cidx, const double* __restrict__ y,
+                  int64_t E, PcgState* st, double* __restrict__ partial) {
   using Acc = typename std::conditional<std::is_same<T, float>::value, RhoAccF32, RhoAcc64>::type;
+  constexpr int n2 = n * n, n3 = n2 * n;
   __shared__ T cv[EPB][8];
   __shared__ T sinv[128];
   __shared__ double sred[32];
@@ -361,32 +407,44 @@ __global__ void k_prolong_rho(T* __restrict__ z, const T* __restrict__ r, const 
   for (int m = threadIdx.x; m < 128; m += blockDim.x) sinv[m] = m ? T(1) / T(m) : T(0);
   __syncthreads();
   if (sdone) return;
-  const int n2 = n * n, n3 = n2 * n;
   const int le = threadIdx.x / n2, ij = threadIdx.x - le * n2, i = ij % n, j = ij / n;
   const int64_t groups = (E + EPB - 1) / EPB;
   Acc acc;
   for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
-    if (threadIdx.x < 8 * EPB) {
-      const int64_t e = g * EPB + threadIdx.x / 8;
-      const int c = e < E ? cidx[8 * e + (threadIdx.x & 7)] : -1;
-      cv[threadIdx.x / 8][threadIdx.x & 7] = c >= 0 ? (T)y[c] : T(0);
+    for (int t = threadIdx.x; t < 8 * EPB; t += blockDim.x) {
+      const int64_t e = g * EPB + t / 8;
+      const int c = e < E ? cidx[8 * e + (t & 7)] : -1;
+      cv[t / 8][t & 7] = c >= 0 ? (T)y[c] : T(0);
     }
-    __syncthreads();
     const int64_t e = g * EPB + le;
-    if (le < EPB && e < E) {
+    const bool act = le < EPB && e < E;
+    // this column's n values of z, r and the point flags, all loads in flight together
+    T zv[n], rv[n];
+    uint8_t mv[n];
+    if (act) {
+#pragma unroll
+      for (int k = 0; k < n; ++k) {
+        const int64_t q = e * n3 + k * n2 + ij;
+        zv[k] = z[q];
+        rv[k] = r[q];
+        mv[k] = wm[q];
+      }
+    }
+    __syncthreads();  // cv filled
+    if (act) {
       const T* c = cv[le];
       const T fi0 = ftab[i], fi1 = ftab[n + i], fj0 = ftab[j], fj1 = ftab[n + j];
       const T a0 = fj0 * (fi0 * c[0] + fi1 * c[1]) + fj1 * (fi0 * c[2] + fi1 * c[3]);
       const T a1 = fj0 * (fi0 * c[4] + fi1 * c[5]) + fj1 * (fi0 * c[6] + fi1 * c[7]);
+#pragma unroll
       for (int k = 0; k < n; ++k) {
         const int64_t q = e * n3 + k * n2 + ij;
-        const uint8_t m = wm[q];
-        T zq = z[q];
-        if (!(m & 0x80)) {
+        T zq = zv[k];
+        if (!(mv[k] & 0x80)) {  // Dirichlet points keep z (0 there)
           zq = zq + (ftab[k] * a0 + ftab[n + k] * a1);
           z[q] = zq;
         }
-        acc.add(r[q] * zq * sinv[m & 0x7f]);
+        acc.add(rv[k] * zq * sinv[mv[k] & 0x7f]);
       }
     }
     __syncthreads();  // cv is rewritten for the next group
@@ -549,19 +607,32 @@ template cudaError_t launch_coarse_prolong<double>(double*, const uint8_t*, cons
 template cudaError_t launch_coarse_prolong<float>(float*, const uint8_t*, const float*, const int32_t*, const double*,
                                                   int, int64_t, double, const PcgState*, cudaStream_t);
 
+template <typename T, int n>
+cudaError_t launch_prolong_rho_n(T* z, const T* r, const uint8_t* wm, const T* ftab, const int32_t* cidx,
+                                 const double* y, int64_t E, PcgState* st, double* partial, cudaStream_t s) {
+  constexpr int EPB = (256 / (n * n)) < 1 ? 1 : 256 / (n * n);
+  const int grid = (int)std::min<int64_t>(152 * 4, std::max<int64_t>(1, (E + EPB - 1) / EPB));  // <= the partials
+  k_prolong_rho<T, n, EPB><<<grid, ((EPB * n * n + 31) / 32) * 32, 0, s>>>(z, r, wm, ftab, cidx, y, E, st, partial);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_prolong_rho(T* z, const T* r, const uint8_t* wm, const T* ftab, const int32_t* cidx,
                                const double* y, int n, int64_t E, PcgState* st, double* partial, cudaStream_t s) {
-  const int grid = (int)std::min<int64_t>(152 * 4, std::max<int64_t>(1, E / 4));  // <= the vector kernels' partials
-  if (n <= 8) {
-    constexpr int EPB = 4;
-    const unsigned threads = ((EPB * n * n + 31) / 32) * 32;
-    k_prolong_rho<T, EPB><<<grid, threads, 0, s>>>(z, r, wm, ftab, cidx, y, n, E, st, partial);
-  } else {
-    const unsigned threads = ((n * n + 31) / 32) * 32;
-    k_prolong_rho<T, 1><<<grid, threads, 0, s>>>(z, r, wm, ftab, cidx, y, n, E, st, partial);
+  switch (n) {
+    case 2: return launch_prolong_rho_n<T, 2>(z, r, wm, ftab, cidx, y, E, st, partial, s);
+    case 3: return launch_prolong_rho_n<T, 3>(z, r, wm, ftab, cidx, y, E, st, partial, s);
+    case 4: return launch_prolong_rho_n<T, 4>(z, r, wm, ftab, cidx, y, E, st, partial, s);
+    case 5: return launch_prolong_rho_n<T, 5>(z, r, wm, ftab, cidx, y, E, st, partial, s);
+    case 6: return launch_prolong_rho_n<T, 6>(z, r, wm, ftab, cidx, y, E, st, partial, s);
+    case 7: return launch_prolong_rho_n<T, 7>(z, r, wm, ftab, cidx, y, E, st, partial, s);
+    case 8: return launch_prolong_rho_n<T, 8>(z, r, wm, ftab, cidx, y, E, st, partial, s);
+    case 9: return launch_prolong_rho_n<T, 9>(z, r, wm, ftab, cidx, y, E, st, partial, s);
+    case 10: return launch_prolong_rho_n<T, 10>(z, r, wm, ftab, cidx, y, E, st, partial, s);
+    case 11: return launch_prolong_rho_n<T, 11>(z, r, wm, ftab, cidx, y, E, st, partial, s);
+    case 12: return launch_prolong_rho_n<T, 12>(z, r, wm, ftab, cidx, y, E, st, partial, s);
+    default: return cudaErrorNotSupported;
   }
-  return cudaGetLastError();
 }
 template cudaError_t launch_prolong_rho<double>(double*, const double*, const uint8_t*, const double*, const int32_t*,
                                                 const double*, int, int64_t, PcgState*, double*, cudaStream_t);
