@@ -93,12 +93,16 @@ __global__ void k_gl_factors(const double* __restrict__ xyz, const double* __res
 // Shared memory: the two 1D matrices [m][n], tb [m^3], T1 [m][m][n],
 // T2 [m][n][n], acc [n^3].  Each thread owns the acc entries q = tid + t blockDim.
 // T = double (FP64) or float (the FP32 operator of the mixed-precision solve).
-template <typename T>
+// N as a template parameter: the loop bounds and the index arithmetic (q / n,
+// q % n) are compile-time constants (the kernels were integer-issue bound with
+// run-time n: ALU pipe 44-58%, issue 80-88% in FP32).
+template <typename T, int N>
 __global__ void k_pgrad(const T* __restrict__ p, const T* __restrict__ F, const T* __restrict__ Ig,
-                        const T* __restrict__ DIg, int n, int m, int64_t E, T* __restrict__ u, int64_t n_local) {
+                        const T* __restrict__ DIg, int64_t E, T* __restrict__ u, int64_t n_local) {
+  constexpr int n = N + 1, m = N - 1;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sm = reinterpret_cast<T*>(sm_raw);
-  const int n2 = n * n, n3 = n2 * n, m2 = m * m, m3 = m2 * m;
+  constexpr int n2 = n * n, n3 = n2 * n, m2 = m * m, m3 = m2 * m;
   T* sI = sm;
   T* sD = sI + m * n;
   T* tb = sD + m * n;
@@ -154,13 +158,14 @@ __global__ void k_pgrad(const T* __restrict__ p, const T* __restrict__ F, const 
 // (the inverse assembled mass), u_a invB when invB (its reciprocal) is given,
 // u_a itself otherwise.  Shared memory: the two
 // 1D matrices, V [n^3], S1 [n][n][m], S2 [n][m][m], oacc [m^3].
-template <typename T>
+template <typename T, int N>
 __global__ void k_pdiv(const T* __restrict__ u, const T* __restrict__ dB, const T* __restrict__ invB,
-                       const T* __restrict__ F, const T* __restrict__ Ig, const T* __restrict__ DIg, int n, int m,
-                       int64_t E, T* __restrict__ out, int64_t n_local) {
+                       const T* __restrict__ F, const T* __restrict__ Ig, const T* __restrict__ DIg, int64_t E,
+                       T* __restrict__ out, int64_t n_local) {
+  constexpr int n = N + 1, m = N - 1;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sm = reinterpret_cast<T*>(sm_raw);
-  const int n2 = n * n, n3 = n2 * n, m2 = m * m, m3 = m2 * m;
+  constexpr int n2 = n * n, n3 = n2 * n, m2 = m * m, m3 = m2 * m;
   T* sI = sm;
   T* sD = sI + m * n;
   T* V = sD + m * n;
@@ -368,17 +373,46 @@ cudaError_t launch_gl_factors(const double* xyz, const double* Ig, const double*
   return cudaGetLastError();
 }
 
+template <typename T, int N>
+cudaError_t launch_pgrad_n(const T* p, const T* F, const T* Ig, const T* DIg, int64_t E, T* u, int64_t n_local,
+                           cudaStream_t s) {
+  const size_t smem = pgrad_smem(N + 1, N - 1, sizeof(T));
+  static DeviceOnce once;
+  cudaError_t err = once.get([&](int, int*) {
+    return cudaFuncSetAttribute(k_pgrad<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (err != cudaSuccess) return err;
+  k_pgrad<T, N><<<(unsigned)E, kPressureThreads, smem, s>>>(p, F, Ig, DIg, E, u, n_local);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t launch_pdiv_n(const T* u, const T* dB, const T* invB, const T* F, const T* Ig, const T* DIg, int64_t E,
+                          T* out, int64_t n_local, cudaStream_t s) {
+  const size_t smem = pdiv_smem(N + 1, N - 1, sizeof(T));
+  static DeviceOnce once;
+  cudaError_t err = once.get([&](int, int*) {
+    return cudaFuncSetAttribute(k_pdiv<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (err != cudaSuccess) return err;
+  k_pdiv<T, N><<<(unsigned)E, kPressureThreads, smem, s>>>(u, dB, invB, F, Ig, DIg, E, out, n_local);
+  return cudaGetLastError();
+}
+
+#define SEM_PRESSURE_ORDERS(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11)
+
 template <typename T>
 cudaError_t launch_pgrad(const T* p, const T* F, const T* Ig, const T* DIg, int n, int m, int64_t E, T* u,
                          int64_t n_local, cudaStream_t s) {
-  const size_t smem = pgrad_smem(n, m, sizeof(T));
-  static DeviceOnce once;
-  cudaError_t err = once.get([&](int, int*) {
-    return cudaFuncSetAttribute(k_pgrad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pgrad_smem(11 + 1, 10, sizeof(T)));
-  });
-  if (err != cudaSuccess) return err;
-  k_pgrad<T><<<(unsigned)E, kPressureThreads, smem, s>>>(p, F, Ig, DIg, n, m, E, u, n_local);
-  return cudaGetLastError();
+  if (m != n - 2) return cudaErrorInvalidValue;
+  switch (n - 1) {
+#define SEM_CASE(N) \
+  case N:           \
+    return launch_pgrad_n<T, N>(p, F, Ig, DIg, E, u, n_local, s);
+    SEM_PRESSURE_ORDERS(SEM_CASE)
+#undef SEM_CASE
+    default: return cudaErrorNotSupported;
+  }
 }
 template cudaError_t launch_pgrad<double>(const double*, const double*, const double*, const double*, int, int, int64_t,
                                           double*, int64_t, cudaStream_t);
@@ -388,14 +422,15 @@ template cudaError_t launch_pgrad<float>(const float*, const float*, const float
 template <typename T>
 cudaError_t launch_pdiv(const T* u, const T* dB, const T* invB, const T* F, const T* Ig, const T* DIg, int n, int m,
                         int64_t E, T* out, int64_t n_local, cudaStream_t s) {
-  const size_t smem = pdiv_smem(n, m, sizeof(T));
-  static DeviceOnce once;
-  cudaError_t err = once.get([&](int, int*) {
-    return cudaFuncSetAttribute(k_pdiv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pdiv_smem(11 + 1, 10, sizeof(T)));
-  });
-  if (err != cudaSuccess) return err;
-  k_pdiv<T><<<(unsigned)E, kPressureThreads, smem, s>>>(u, dB, invB, F, Ig, DIg, n, m, E, out, n_local);
-  return cudaGetLastError();
+  if (m != n - 2) return cudaErrorInvalidValue;
+  switch (n - 1) {
+#define SEM_CASE(N) \
+  case N:           \
+    return launch_pdiv_n<T, N>(u, dB, invB, F, Ig, DIg, E, out, n_local, s);
+    SEM_PRESSURE_ORDERS(SEM_CASE)
+#undef SEM_CASE
+    default: return cudaErrorNotSupported;
+  }
 }
 template cudaError_t launch_pdiv<double>(const double*, const double*, const double*, const double*, const double*,
                                          const double*, int, int, int64_t, double*, int64_t, cudaStream_t);

@@ -392,7 +392,8 @@ struct RhoAccF32 {  // Knuth's TwoSum on the FP32 pipe
   __device__ __forceinline__ double get() const { return (double)s + (double)c; }
 };
 
-template <typename T, int n, int EPB>
+// RHO = false: only z += mask R_0^T y (st nullable, r unused).
+template <typename T, int n, int EPB, bool RHO>
 __global__ void __launch_bounds__(((EPB * n * n + 31) / 32) * 32)
     k_prolong_rho(T* __restrict__ z, const T* __restrict__ r, const uint8_t* __restrict__ wm,
                   const T* __restrict__ ftab, const int32_t* __restrict__ cidx, const double* __restrict__ y,
@@ -403,8 +404,9 @@ __global__ void __launch_bounds__(((EPB * n * n + 31) / 32) * 32)
   __shared__ T sinv[128];
   __shared__ double sred[32];
   __shared__ int sdone;
-  if (threadIdx.x == 0) sdone = st->done;
-  for (int m = threadIdx.x; m < 128; m += blockDim.x) sinv[m] = m ? T(1) / T(m) : T(0);
+  if (threadIdx.x == 0) sdone = st ? st->done : 0;
+  if (RHO)
+    for (int m = threadIdx.x; m < 128; m += blockDim.x) sinv[m] = m ? T(1) / T(m) : T(0);
   __syncthreads();
   if (sdone) return;
   const int le = threadIdx.x / n2, ij = threadIdx.x - le * n2, i = ij % n, j = ij / n;
@@ -426,7 +428,7 @@ __global__ void __launch_bounds__(((EPB * n * n + 31) / 32) * 32)
       for (int k = 0; k < n; ++k) {
         const int64_t q = e * n3 + k * n2 + ij;
         zv[k] = z[q];
-        rv[k] = r[q];
+        rv[k] = RHO ? r[q] : T(0);
         mv[k] = wm[q];
       }
     }
@@ -444,11 +446,12 @@ __global__ void __launch_bounds__(((EPB * n * n + 31) / 32) * 32)
           zq = zq + (ftab[k] * a0 + ftab[n + k] * a1);
           z[q] = zq;
         }
-        acc.add(rv[k] * zq * sinv[mv[k] & 0x7f]);
+        if (RHO) acc.add(rv[k] * zq * sinv[mv[k] & 0x7f]);
       }
     }
     __syncthreads();  // cv is rewritten for the next group
   }
+  if (!RHO) return;
   const double a = block_sum(acc.get(), sred);
   if (threadIdx.x == 0) partial[blockIdx.x] = a;
   if (last_block(&st->cnt[3])) {
@@ -612,7 +615,12 @@ cudaError_t launch_prolong_rho_n(T* z, const T* r, const uint8_t* wm, const T* f
                                  const double* y, int64_t E, PcgState* st, double* partial, cudaStream_t s) {
   constexpr int EPB = (256 / (n * n)) < 1 ? 1 : 256 / (n * n);
   const int grid = (int)std::min<int64_t>(152 * 4, std::max<int64_t>(1, (E + EPB - 1) / EPB));  // <= the partials
-  k_prolong_rho<T, n, EPB><<<grid, ((EPB * n * n + 31) / 32) * 32, 0, s>>>(z, r, wm, ftab, cidx, y, E, st, partial);
+  if (partial)
+    k_prolong_rho<T, n, EPB, true><<<grid, ((EPB * n * n + 31) / 32) * 32, 0, s>>>(z, r, wm, ftab, cidx, y, E, st,
+                                                                                  partial);
+  else
+    k_prolong_rho<T, n, EPB, false><<<grid, ((EPB * n * n + 31) / 32) * 32, 0, s>>>(z, r, wm, ftab, cidx, y, E, st,
+                                                                                   partial);
   return cudaGetLastError();
 }
 

@@ -44,7 +44,8 @@ template <typename T>
 cudaError_t launch_coarse_prolong(T* z, const uint8_t* wm, const T* ftab, const int32_t* cidx, const double* y, int n,
                                   int64_t E, double zscale, const PcgState* st, cudaStream_t s);
 // z += mask R_0^T y (the coarse correction), then rho_new = <r, z>_W and
-// beta = rho_new / rho in the CG state (as launch_pcg_rho), in one pass.
+// beta = rho_new / rho in the CG state (as launch_pcg_rho), in one pass;
+// partial = nullptr: the correction only (st nullable).
 template <typename T>
 cudaError_t launch_prolong_rho(T* z, const T* r, const uint8_t* wm, const T* ftab, const int32_t* cidx,
                                const double* y, int n, int64_t E, PcgState* st, double* partial, cudaStream_t s);

@@ -457,8 +457,9 @@ sem_status apply_t(const sem_schwarz* sw, const T* r, T* z, PcgState* st, double
     }
     if (rho) {
       SEM_CUDA(launch_prolong_rho<T>(z, r, m->wm, ft, sw->cidx, sw->y, m->n, m->E, st, partial, s));
-    } else {
-      SEM_CUDA(launch_coarse_prolong<T>(z, m->wm, ft, sw->cidx, sw->y, m->n, m->E, 1.0, st, s));
+    } else {  // the same pass without the product
+      SEM_CUDA(launch_prolong_rho<T>(z, r, m->wm, ft, sw->cidx, sw->y, m->n, m->E, const_cast<PcgState*>(st),
+                                     nullptr, s));
     }
     count_launches(2);
   }
