@@ -501,9 +501,10 @@ def pressure_solve_leg(workload="pipe4096_n7", tol=1e-10):
     """Solves of the pressure equation E p = g (Sec. 2, Eq. 5) on the
     mean-free space (sem_pressure_solve, CG) on the E = 4096 pipe, the paper's
     per-GPU regime, g a seeded standard-normal pressure field: FP64, and mixed
-    precision (FP32 E, FP64 reliable updates).  The first operator calls
-    (which build the GL-point factors and their FP32 copies) are made before
-    timing."""
+    precision (FP32 E, FP64 reliable updates), both Jacobi-preconditioned
+    (diag(E)), and the plain FP64 CG beside them.  The first operator calls
+    (which build the GL-point factors, their FP32 copies and the diagonal)
+    are made before timing."""
     import torch
     import paper_2109_03592_gb300 as sem
     from sem_inputs import configs
@@ -513,6 +514,7 @@ def pressure_solve_leg(workload="pipe4096_n7", tol=1e-10):
     x = torch.empty_like(g)
     m.pressure_apply(g, x)
     m.pressure_apply_f32(g.float(), x.float())
+    m.pressure_solve(g, x, tol=tol, maxit=1)  # builds diag(E)
     torch.cuda.synchronize()
     r = m.pressure_solve(g, x, tol=tol)
     out = {"workload": f"{workload}: E={m.E} N={m.N}, {m.pressure_size()} pressure values", "tol": tol,
@@ -521,6 +523,8 @@ def pressure_solve_leg(workload="pipe4096_n7", tol=1e-10):
     rm = m.pressure_solve(g, x, tol=tol, prec=sem.MIXED)
     out["mixed"] = {"iters": rm["iters"], "replacements": rm["outer_iters"], "ms": rm["ms"], "rel_res": rm["rel_res"],
                     "status": rm["status"]}
+    rp = m.pressure_solve(g, x, tol=tol, precond=sem.PRECOND_NONE)
+    out["unpreconditioned"] = {"iters": rp["iters"], "ms": rp["ms"], "rel_res": rp["rel_res"], "status": rp["status"]}
     m.close()
     return out
 
@@ -558,7 +562,8 @@ def compact_pressure(p):
                              "algorithmic_gbs") if k in p}
     if "solve" in p:
         sv = p["solve"]
-        out["solve"] = sv if "error" in sv else {k: sv[k] for k in ("iters", "ms", "rel_res", "status", "mixed")
+        out["solve"] = sv if "error" in sv else {k: sv[k] for k in ("iters", "ms", "rel_res", "status", "mixed",
+                                                                       "unpreconditioned")
                                                   if k in sv}
     return _sig(out)
 

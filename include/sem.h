@@ -200,7 +200,14 @@ typedef struct {
   double delta;     /* SEM_MIXED, refine = 0: replace the residual when the FP32 one has dropped by
                        this factor since the last replacement; <= 0 means 0.3 (sem_pcg_solve) or
                        0.1 (batched and served solves, where a replacement costs a host round trip) */
+  int precond;      /* sem_pressure_solve: SEM_PRECOND_DEFAULT (0) or SEM_PRECOND_JACOBI = diag(E)^-1,
+                       SEM_PRECOND_NONE = plain CG.  The velocity solvers are Jacobi-preconditioned
+                       always and ignore it. */
 } sem_solve_opts;
+
+#define SEM_PRECOND_DEFAULT 0
+#define SEM_PRECOND_NONE 1
+#define SEM_PRECOND_JACOBI 2
 
 typedef struct {
   int iters;       /* CG iterations (summed over inner solves for SEM_MIXED) */
@@ -379,9 +386,13 @@ sem_status sem_pressure_apply(const sem_mesh* mesh, const double* p_dev, double*
  * The constants are E's null space when the velocity is Dirichlet on the
  * whole boundary (exactly on affine meshes; on curved elements GL quadrature
  * leaves them a near-null mode), so the pressure is fixed up to a constant.
- * Solved: Pm E Pm p = Pm g with Pm = I - 1 1^T / n_pressure, by plain
- * (unpreconditioned) CG from p = 0 in the Euclidean inner product over the
- * pressure values, stopped when ||r|| <= opts->tol ||Pm g|| for the recurrence
+ * Solved: Pm E Pm p = Pm g with Pm = I - 1 1^T / n_pressure, by CG from
+ * p = 0 in the Euclidean inner product over the pressure values, Jacobi
+ * preconditioned (opts->precond SEM_PRECOND_DEFAULT or SEM_PRECOND_JACOBI:
+ * z = Pm (r / diag(E)), the scaled residual projected back to the mean-free
+ * space, so that the preconditioner is symmetric positive definite there;
+ * diag(E) is built once per mesh, see sem_pressure_diag) or plain
+ * (SEM_PRECOND_NONE: z = r), stopped when ||r|| <= opts->tol ||Pm g|| for the recurrence
  * residual and then for the true residual Pm (g - E p) (CG restarts from p,
  * at most 5 times, when the recurrence drifted); tol <= 0 means 1e-10,
  * maxit <= 0 means 20000.  opts->prec: SEM_FP64 (as above) or SEM_MIXED:
@@ -403,6 +414,15 @@ sem_status sem_pressure_apply(const sem_mesh* mesh, const double* p_dev, double*
  * value). */
 sem_status sem_pressure_solve(const sem_mesh* mesh, const double* g_dev, double* p_dev, const sem_solve_opts* opts,
                               sem_solve_result* result, void* stream);
+
+/* diag(E) of the pressure operator (the Jacobi preconditioner of
+ * sem_pressure_solve): E_qq = sum_a sum_l D_a[q, l]^2 mask_l / (QQ^T B)_l over
+ * the GLL points l of q's element (unit pressure q reaches only its own
+ * element's velocity copies; no element holds two copies of one node), with
+ * the rows D_a[q, l] = sum_b F[b][a](q) C_b[q, l] of the weak divergence,
+ * summed by factorisation in FP64.  d_dev [E][m^3] FP64, device.  Ordered on
+ * stream. */
+sem_status sem_pressure_diag(const sem_mesh* mesh, double* d_dev, void* stream);
 
 /* ---- overlapping Schwarz preconditioner: host set-up ---------------------- */
 

@@ -159,6 +159,28 @@ class Pressure:
         g = self.grad(p)
         return self.div(np.stack([self.minv(g[a]) for a in range(3)]))
 
+    def diagonal(self):
+        """diag(E), element by element.  Unit pressure q of element e gives
+        D_a^T e_q = the row D_a[q, :] on e's GLL points and zero elsewhere;
+        QQ^T leaves it unchanged at e's copies (no element holds two copies
+        of one node on these meshes), so
+            E_qq = sum_a sum_l D_a[q, l]^2 mask_l / (QQ^T B)_l,
+        with the rows D_a[q, l] = sum_b F[b, a](q) C_b[q, l] written out
+        (C_b: the GL-point derivative along b, interpolation along the other
+        two directions).  Pinned against np.diag(dense()) in the tests."""
+        N = self.N
+        I, Dg, _ = interpolation_matrices(N)
+        C = [np.einsum("Kk,Jj,Ii->KJIkji", I, I, Dg),
+             np.einsum("Kk,Jj,Ii->KJIkji", I, Dg, I),
+             np.einsum("Kk,Jj,Ii->KJIkji", Dg, I, I)]
+        wgt = self.prob.mask / self.Bg  # [E, n, n, n]
+        d = np.zeros(self.shape)
+        for e in range(self.prob.mesh.E):
+            for a in range(3):
+                row = sum(self.F[e, b, a][:, :, :, None, None, None] * C[b] for b in range(3))
+                d[e] += np.einsum("KJIkji,kji->KJI", row * row, wgt[e])
+        return d
+
     def dense(self):
         """Dense E (tiny meshes only), column c = E applied to unit pressure c."""
         P = int(np.prod(self.shape))
@@ -170,7 +192,7 @@ class Pressure:
         return A
 
 
-def cg(P, g, tol=1e-10, maxit=20000, max_restarts=5):
+def cg(P, g, tol=1e-10, maxit=20000, max_restarts=5, dinv=None):
     """CG for the pressure equation E p = g (Sec. 2, Eq. 5) on the mean-free
     subspace.  With Dirichlet velocity on the whole boundary the constants
     are the null space of E (exactly so on affine meshes; on curved elements
@@ -184,16 +206,28 @@ def cg(P, g, tol=1e-10, maxit=20000, max_restarts=5):
     ``max_restarts`` times; the paper fixes no stopping rule, and this one
     makes the returned residual the true one).  Returns (p, iterations,
     ||Pm (g - E p)|| / ||Pm g|| -- the recurrence value if not converged --,
-    status) with status as in ``solver``."""
+    status) with status as in ``solver``.
+
+    dinv (the reciprocal of ``Pressure.diagonal()``): Jacobi-preconditioned
+    CG, z = Pm (dinv r) -- scaled, then projected back to the mean-free
+    space, so that Pm D^{-1} Pm stays symmetric and positive definite there
+    -- with rho = <r, z>; the stopping rule stays on ||r||."""
     from .solver import BREAKDOWN, CONVERGED, NOT_CONVERGED
     gm = g - g.mean()
     gnorm = np.sqrt(np.sum(gm * gm))
     x = np.zeros(P.shape)
     if gnorm == 0.0:
         return x, 0, 0.0, CONVERGED
+    def precondition(r):
+        if dinv is None:
+            return r
+        z = dinv * r
+        return z - z.mean()
+
     r = gm.copy()
-    p = r.copy()
-    rho = np.sum(r * r)
+    z = precondition(r)
+    p = z.copy()
+    rho = np.sum(r * z)
     restarts = 0
     for k in range(1, maxit + 1):
         w = P.E(p)
@@ -204,18 +238,22 @@ def cg(P, g, tol=1e-10, maxit=20000, max_restarts=5):
         alpha = rho / sigma
         x = x + alpha * p
         r = r - alpha * w
-        rho_new = np.sum(r * r)
-        if np.sqrt(rho_new) <= tol * gnorm:
+        rr = np.sum(r * r)
+        if np.sqrt(rr) <= tol * gnorm:
             w = P.E(x)
             r = gm - (w - w.mean())
-            rho = np.sum(r * r)
-            if np.sqrt(rho) <= tol * gnorm:
-                return x, k, np.sqrt(rho) / gnorm, CONVERGED
+            rr = np.sum(r * r)
+            if np.sqrt(rr) <= tol * gnorm:
+                return x, k, np.sqrt(rr) / gnorm, CONVERGED
             if restarts == max_restarts:
-                return x, k, np.sqrt(rho) / gnorm, NOT_CONVERGED
+                return x, k, np.sqrt(rr) / gnorm, NOT_CONVERGED
             restarts += 1
-            p = r.copy()
+            z = precondition(r)
+            p = z.copy()
+            rho = np.sum(r * z)
             continue
-        p = r + (rho_new / rho) * p
+        z = precondition(r)
+        rho_new = np.sum(r * z)
+        p = z + (rho_new / rho) * p
         rho = rho_new
-    return x, maxit, np.sqrt(rho) / gnorm, NOT_CONVERGED
+    return x, maxit, np.sqrt(rr) / gnorm, NOT_CONVERGED

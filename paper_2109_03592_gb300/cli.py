@@ -5,7 +5,7 @@
     python -m paper_2109_03592_gb300.cli gs --workload pipe262144_n7 --prec fp32 [--reps 10]
     python -m paper_2109_03592_gb300.cli ax --workload pipe262144_n7 --prec fp32 --coef
     python -m paper_2109_03592_gb300.cli pressure --workload pipe32768_n7 [--reps 10]
-    python -m paper_2109_03592_gb300.cli psolve --workload pipe4096_n7 [--tol 1e-10]
+    python -m paper_2109_03592_gb300.cli psolve --workload pipe4096_n7 [--tol 1e-10] [--no-precond]
     python -m paper_2109_03592_gb300.cli schwarz --workload pipe262144_n7 --prec mixed [--no-coarse]
 
 pressure times the consistent Poisson operator E = D B^-1 D^T of the
@@ -65,9 +65,11 @@ def _pressure(args):
     if args.what == "psolve":
         m.pressure_apply(g, q, work)  # builds the GL-point factors
         prec = sem.MIXED if args.prec == "mixed" else sem.FP64
+        precond = sem.PRECOND_NONE if args.no_precond else sem.PRECOND_JACOBI
         for _ in range(args.repeat):
-            r = m.pressure_solve(g, q, tol=args.tol, prec=prec)
+            r = m.pressure_solve(g, q, tol=args.tol, prec=prec, precond=precond)
             print(json.dumps({"workload": args.workload, "prec": "mixed" if prec == sem.MIXED else "fp64",
+                              "precond": "none" if args.no_precond else "jacobi",
                               "pressure_values": m.pressure_size(), **r}), flush=True)
     else:
         f32 = args.prec == "fp32"
@@ -103,6 +105,7 @@ def main(argv=None):
     ap.add_argument("--coef", action="store_true", help="per-point h1, h2 on the mesh (h1 = h2 = 1 in the calls)")
     ap.add_argument("--helmholtz", action="store_true", help="h2 = 1 (the mass term) with scalar coefficients")
     ap.add_argument("--no-coarse", action="store_true", help="schwarz: local solves only")
+    ap.add_argument("--no-precond", action="store_true", help="psolve: plain CG (default: Jacobi, diag(E))")
     args = ap.parse_args(argv)
     import torch
     prec = {"fp64": sem.FP64, "fp32": sem.FP32, "mixed": sem.MIXED}[args.prec]

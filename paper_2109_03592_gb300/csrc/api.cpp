@@ -75,6 +75,7 @@ void free_mesh_arrays(sem_mesh* m) {
   dev_free(m->cB32lo);
   dev_free(m->cdB);
   dev_free(m->Fgl);
+  dev_free(m->pdinv);
   dev_free(m->Igl);
   dev_free(m->DIgl);
   dev_free(m->Fgl32);

@@ -163,6 +163,13 @@ cudaError_t launch_presidual_keep(const double* g, double cg, const double* w, d
 // out[0] on the device, using partial[pressure_red_blocks()] as scratch.
 int pressure_red_blocks();
 cudaError_t launch_pdot(const double* a, const double* b, int64_t n, double* partial, double* out, cudaStream_t s);
+// out [E m^3] = diag(E), or 1 / diag(E) with recip (the pressure operator's
+// diagonal; wm's Dirichlet bit is the velocity mask, dB the assembled mass)
+cudaError_t launch_pdiag(const double* F, const double* Ig, const double* DIg, const uint8_t* wm, const double* dB,
+                        int n, int m, int64_t E, double* out, int recip, cudaStream_t s);
+// z = dinv r; *out = sum z
+cudaError_t launch_pscale(const double* r, const double* dinv, double* z, int64_t n, double* partial, double* out,
+                          cudaStream_t s);
 cudaError_t launch_pshift_dot(double* w, const double* p, double c, int64_t n, double* partial, double* out,
                               cudaStream_t s);
 cudaError_t launch_pupdate(double* x, double* r, const double* p, const double* w, double alpha, int64_t n,

@@ -351,6 +351,96 @@ __global__ void k_recip_f32(const double* __restrict__ a, float* __restrict__ b,
 __global__ void k_presidual_keep(const double* __restrict__ g, double cg, const double* __restrict__ w, double cw,
                                  double* __restrict__ r, int64_t n, double* partial);
 
+// diag(E) (recip = 0) or its reciprocal, one CTA per element.  Unit pressure q gives
+// D_a^T e_q = the row D_a[q, :] on the element's GLL points, which QQ^T leaves
+// as it is at the element's own copies (no element holds two copies of one
+// node), so E_qq = sum_a sum_l D_a[q, l]^2 wgt_l with wgt = mask / (QQ^T B).
+// With D_a[q, l] = sum_b F[b][a](q) C_b[q, l]:
+//   E_qq = sum_a sum_{b, b'} F[b][a](q) F[b'][a](q) S_{bb'}(q),
+//   S_{bb'}(q) = sum_l C_b[q, l] C_b'[q, l] wgt_l,
+// and S_{bb'} is a sum factorisation with the 1D matrices Ig*Ig, Ig*DIg or
+// DIg*DIg (elementwise) along each direction, by how many of b, b' are that
+// direction.  Shared memory: X [3][m][n], wgt [n^3], T1 [n][n][m],
+// T2 [n][m][m], S [6][m^3].
+__global__ void k_pdiag(const double* __restrict__ F, const double* __restrict__ Ig, const double* __restrict__ DIg,
+                        const uint8_t* __restrict__ wm, const double* __restrict__ dB, int n, int m, int64_t E,
+                        double* __restrict__ out, int recip) {
+  extern __shared__ double sm[];
+  const int n2 = n * n, n3 = n2 * n, m2 = m * m, m3 = m2 * m, mn = m * n;
+  double* X = sm;
+  double* wgt = X + 3 * mn;
+  double* T1 = wgt + n3;
+  double* T2 = T1 + n2 * m;
+  double* S = T2 + n * m2;
+  const int64_t e = blockIdx.x;
+  if (e >= E) return;
+  for (int q = threadIdx.x; q < mn; q += blockDim.x) {
+    X[q] = Ig[q] * Ig[q];
+    X[mn + q] = Ig[q] * DIg[q];
+    X[2 * mn + q] = DIg[q] * DIg[q];
+  }
+  for (int q = threadIdx.x; q < n3; q += blockDim.x) {
+    const int64_t l = e * n3 + q;
+    wgt[q] = (wm[l] & 0x80) ? 0.0 : 1.0 / dB[l];
+  }
+  __syncthreads();
+  const int pb[6] = {0, 1, 2, 0, 0, 1}, pc[6] = {0, 1, 2, 1, 2, 2};
+  for (int c = 0; c < 6; ++c) {
+    const int b = pb[c], b2 = pc[c];
+    const double* Xi = X + ((b == 0) + (b2 == 0)) * mn;
+    const double* Xj = X + ((b == 1) + (b2 == 1)) * mn;
+    const double* Xk = X + ((b == 2) + (b2 == 2)) * mn;
+    // T1[k][j][I] = sum_i Xi[I][i] wgt[k][j][i]
+    for (int q = threadIdx.x; q < n2 * m; q += blockDim.x) {
+      const int I = q % m, kj = q / m;
+      double a = 0.0;
+      for (int i = 0; i < n; ++i) a += Xi[I * n + i] * wgt[kj * n + i];
+      T1[q] = a;
+    }
+    __syncthreads();
+    // T2[k][J][I] = sum_j Xj[J][j] T1[k][j][I]
+    for (int q = threadIdx.x; q < n * m2; q += blockDim.x) {
+      const int I = q % m, J = (q / m) % m, k = q / m2;
+      double a = 0.0;
+      for (int j = 0; j < n; ++j) a += Xj[J * n + j] * T1[(k * n + j) * m + I];
+      T2[q] = a;
+    }
+    __syncthreads();
+    // S_c[K][J][I] = sum_k Xk[K][k] T2[k][J][I]
+    for (int q = threadIdx.x; q < m3; q += blockDim.x) {
+      const int JI = q % m2, K = q / m2;
+      double a = 0.0;
+      for (int k = 0; k < n; ++k) a += Xk[K * n + k] * T2[k * m2 + JI];
+      S[c * m3 + q] = a;
+    }
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < m3; q += blockDim.x) {
+    const double* Fe = F + e * 9 * m3 + q;
+    double d = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      const double f0 = Fe[(0 + a) * m3], f1 = Fe[(3 + a) * m3], f2 = Fe[(6 + a) * m3];
+      d += f0 * f0 * S[q] + f1 * f1 * S[m3 + q] + f2 * f2 * S[2 * m3 + q] +
+           2.0 * (f0 * f1 * S[3 * m3 + q] + f0 * f2 * S[4 * m3 + q] + f1 * f2 * S[5 * m3 + q]);
+    }
+    out[e * m3 + q] = recip ? (d > 0.0 ? 1.0 / d : 0.0) : d;
+  }
+}
+
+// z = dinv * r; partial sums of z_i (its mean is removed by k_pshift_dot)
+__global__ void k_pscale(const double* __restrict__ r, const double* __restrict__ dinv, double* __restrict__ z,
+                         int64_t n, double* partial) {
+  __shared__ double s[kRedThreads];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
+    const double v = dinv[i] * r[i];
+    z[i] = v;
+    acc += v;
+  }
+  const double t = block_sum(acc, s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
 // ---- launchers ---------------------------------------------------------------
 
 static constexpr int kPressureThreads = 256;
@@ -451,6 +541,23 @@ int pressure_red_blocks() { return kPressureRedBlocks; }
 
 cudaError_t launch_pdot(const double* a, const double* b, int64_t n, double* partial, double* out, cudaStream_t s) {
   k_pdot<<<kPressureRedBlocks, kRedThreads, 0, s>>>(a, b, n, partial);
+  k_psum_finish<<<1, kRedThreads, 0, s>>>(partial, kPressureRedBlocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pdiag(const double* F, const double* Ig, const double* DIg, const uint8_t* wm, const double* dB,
+                        int n, int m, int64_t E, double* out, int recip, cudaStream_t s) {
+  const size_t smem = sizeof(double) * (3 * m * n + n * n * n + n * n * m + n * m * m + 6 * m * m * m);
+  cudaError_t err = cudaFuncSetAttribute(k_pdiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  if (E == 0) return cudaSuccess;
+  k_pdiag<<<(unsigned)E, kPressureThreads, smem, s>>>(F, Ig, DIg, wm, dB, n, m, E, out, recip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pscale(const double* r, const double* dinv, double* z, int64_t n, double* partial, double* out,
+                          cudaStream_t s) {
+  k_pscale<<<kPressureRedBlocks, kRedThreads, 0, s>>>(r, dinv, z, n, partial);
   k_psum_finish<<<1, kRedThreads, 0, s>>>(partial, kPressureRedBlocks, out);
   return cudaGetLastError();
 }

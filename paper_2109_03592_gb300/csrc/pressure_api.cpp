@@ -221,6 +221,30 @@ sem_status ensure_pressure32(const sem_mesh* m, cudaStream_t s) {
   return SEM_OK;
 }
 
+// 1 / diag(E), the Jacobi preconditioner of the pressure CG (built once,
+// under the mesh's p_mutex, after the FP64 GL-point data).
+sem_status ensure_pdiag(const sem_mesh* m, cudaStream_t s) {
+  SEM_TRY_STATUS(ensure_pressure(m, s));
+  std::lock_guard<std::mutex> lk(m->p_mutex);
+  if (m->pdinv) return SEM_OK;
+  const int mm = m->N - 1;
+  const int64_t np = m->E * mm * mm * mm;
+  double* d = nullptr;
+  cudaError_t e = cudaMalloc((void**)&d, sizeof(double) * np);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  e = launch_pdiag(m->Fgl, m->Igl, m->DIgl, m->wm, m->dB, m->n, mm, m->E, d, 1, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(s);
+    cudaFree(d);
+    return cuda_fail(e, "k_pdiag");
+  }
+  count_launches(1);
+  const_cast<sem_mesh*>(m)->dev_bytes += sizeof(double) * np;
+  m->pdinv = d;
+  return SEM_OK;
+}
+
 // q = E p in FP32: weak gradient, masked QQ^T of each component, reciprocal mass, weak divergence.
 sem_status apply_E32(const sem_mesh* m, const float* p, float* q, float* work, cudaStream_t s) {
   const int mm = m->N - 1;
@@ -253,13 +277,14 @@ namespace {
 // CG continues with its direction.  The solve stops when the true residual
 // meets tol.
 sem_status pressure_solve_mixed(const sem_mesh* m, const double* g_dev, double* p_dev, double tol, int maxit,
-                                double delta, sem_solve_result* result, cudaStream_t s) {
+                                double delta, bool jac, sem_solve_result* result, cudaStream_t s) {
   SEM_TRY_STATUS(ensure_pressure32(m, s));
+  if (jac) SEM_TRY_STATUS(ensure_pdiag(m, s));
   const int64_t mm = m->N - 1, np = m->E * mm * mm * mm, nl = m->n_local;
   const int nb = pressure_red_blocks();
   double* buf = nullptr;
   float* buf32 = nullptr;
-  SEM_CUDA(cudaMalloc((void**)&buf, (3 * (size_t)np + 3 * (size_t)nl + nb + 1) * sizeof(double)));
+  SEM_CUDA(cudaMalloc((void**)&buf, (4 * (size_t)np + 3 * (size_t)nl + nb + 1) * sizeof(double)));
   cudaError_t e0 = cudaMalloc((void**)&buf32, (2 * (size_t)np + 3 * (size_t)nl) * sizeof(float));
   struct Free {
     double* b;
@@ -273,7 +298,8 @@ sem_status pressure_solve_mixed(const sem_mesh* m, const double* g_dev, double* 
   double* r = buf;
   double* q = r + np;
   double* w = q + np;
-  double* work = w + np;
+  double* z = w + np;
+  double* work = z + np;
   double* partial = work + 3 * nl;
   double* sum_d = partial + nb;
   float* q32 = buf32;
@@ -305,13 +331,30 @@ sem_status pressure_solve_mixed(const sem_mesh* m, const double* g_dev, double* 
   launches += 2;
   SEM_TRY_STATUS(read(rho));
   const double gnorm = std::sqrt(rho);
+  // z = Pm (dinv r) and rho = <r, z> (Jacobi); without it z is r itself
+  auto precondition = [&](double& rz) -> sem_status {
+    double zs = 0.0;
+    SEM_CUDA(launch_pscale(r, m->pdinv, z, np, partial, sum_d, s));
+    SEM_TRY_STATUS(read(zs));
+    SEM_CUDA(launch_pshift_dot(z, r, zs / (double)np, np, partial, sum_d, s));
+    SEM_TRY_STATUS(read(rz));
+    launches += 4;
+    return SEM_OK;
+  };
+  const double* zdir = jac ? z : r;
+  const double rr0 = rho;  // <r, r>; rho becomes <r, z>
+  if (jac && gnorm > 0.0) {
+    SEM_TRY_STATUS(precondition(rho));
+    SEM_CUDA(launch_pdir(q, z, 0.0, np, s));
+    launches += 1;
+  }
   constexpr double kGamma = 0.2;
   int it = 0, outer = 0, status = SEM_OK;
   double rel = 0.0;
   if (gnorm > 0.0) {
     status = SEM_ERR_NOT_CONVERGED;
     rel = 1.0;
-    double rr_max = rho;
+    double rr_max = rr0;
     int last = 0;
     for (it = 1; it <= maxit; ++it) {
       // w = E q with the FP32 operator, then w -= mean(w) and sigma = <q, w> in FP64
@@ -329,12 +372,13 @@ sem_status pressure_solve_mixed(const sem_mesh* m, const double* g_dev, double* 
         break;
       }
       const double alpha = rho / sigma;
+      double rr_new = 0.0;
       SEM_CUDA(launch_pupdate(p_dev, r, q, w, alpha, np, partial, sum_d, s));
       launches += 2;
-      SEM_TRY_STATUS(read(rho_new));
-      rel = std::sqrt(rho_new) / gnorm;
-      const bool converged = std::sqrt(rho_new) <= kGamma * tol * gnorm;
-      if (converged || (rho_new <= delta * delta * rr_max && it - last >= kPressureRuGap)) {
+      SEM_TRY_STATUS(read(rr_new));
+      rel = std::sqrt(rr_new) / gnorm;
+      const bool converged = std::sqrt(rr_new) <= kGamma * tol * gnorm;
+      if (converged || (rr_new <= delta * delta * rr_max && it - last >= kPressureRuGap)) {
         // replace r by the true residual Pm (g - E x) with the FP64 operator
         SEM_CUDA(launch_pgrad<double>(p_dev, m->Fgl, m->Igl, m->DIgl, m->n, (int)mm, m->E, work, nl, s));
         for (int a = 0; a < 3; ++a) SEM_CUDA(launch_gs<double>(work + a * nl, g, 1, nullptr, s));
@@ -353,13 +397,17 @@ sem_status pressure_solve_mixed(const sem_mesh* m, const double* g_dev, double* 
         }
         rr_max = rho_t;
         last = it;
-        SEM_CUDA(launch_pdir(q, r, rho_t / rho, np, s));
+        if (jac) SEM_TRY_STATUS(precondition(rho_new));
+        else rho_new = rho_t;
+        SEM_CUDA(launch_pdir(q, zdir, rho_new / rho, np, s));
         launches += 1;
-        rho = rho_t;
+        rho = rho_new;
         continue;
       }
-      if (rho_new > rr_max) rr_max = rho_new;
-      SEM_CUDA(launch_pdir(q, r, rho_new / rho, np, s));
+      if (rr_new > rr_max) rr_max = rr_new;
+      if (jac) SEM_TRY_STATUS(precondition(rho_new));
+      else rho_new = rr_new;
+      SEM_CUDA(launch_pdir(q, zdir, rho_new / rho, np, s));
       launches += 1;
       rho = rho_new;
     }
@@ -501,6 +549,21 @@ sem_status sem_pressure_apply_f32(const sem_mesh* m, const float* p_dev, float* 
 // Host-driven: each iteration applies E (five launches), then three
 // deterministic reductions whose sums the host reads back to form the mean of
 // E p, alpha and beta.
+sem_status sem_pressure_diag(const sem_mesh* m, double* d_dev, void* stream) {
+  sem_status st = check_mesh(m, "sem_pressure_diag");
+  if (st != SEM_OK) return st;
+  if (!d_dev) {
+    set_error("sem_pressure_diag: null output");
+    return SEM_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_pressure(m, s);
+  if (st != SEM_OK) return st;
+  SEM_CUDA(launch_pdiag(m->Fgl, m->Igl, m->DIgl, m->wm, m->dB, m->n, m->N - 1, m->E, d_dev, 0, s));
+  count_launches(1);
+  return SEM_OK;
+}
+
 sem_status sem_pressure_solve(const sem_mesh* m, const double* g_dev, double* p_dev, const sem_solve_opts* opts,
                               sem_solve_result* result, void* stream) {
   sem_status st = check_mesh(m, "sem_pressure_solve");
@@ -513,19 +576,29 @@ sem_status sem_pressure_solve(const sem_mesh* m, const double* g_dev, double* p_
   const int maxit = opts->maxit > 0 ? opts->maxit : 20000;
   *result = sem_solve_result{0, 0, 0.0, 0.0, SEM_OK};
   cudaStream_t s = (cudaStream_t)stream;
+  if (opts->precond != SEM_PRECOND_DEFAULT && opts->precond != SEM_PRECOND_NONE &&
+      opts->precond != SEM_PRECOND_JACOBI) {
+    set_error("sem_pressure_solve: precond must be SEM_PRECOND_DEFAULT, _NONE or _JACOBI");
+    return SEM_ERR_INVALID;
+  }
+  const bool jac = opts->precond != SEM_PRECOND_NONE;
   if (opts->prec == SEM_MIXED)
-    return pressure_solve_mixed(m, g_dev, p_dev, tol, maxit, opts->delta > 0.0 ? opts->delta : 0.1, result, s);
+    return pressure_solve_mixed(m, g_dev, p_dev, tol, maxit, opts->delta > 0.0 ? opts->delta : 0.1, jac, result, s);
   if (opts->prec != SEM_FP64) {
     set_error("sem_pressure_solve: prec must be SEM_FP64 or SEM_MIXED");
     return SEM_ERR_INVALID;
   }
   st = ensure_pressure(m, s);
   if (st != SEM_OK) return st;
+  if (jac) {
+    st = ensure_pdiag(m, s);
+    if (st != SEM_OK) return st;
+  }
   const int64_t mm = m->N - 1, np = m->E * mm * mm * mm;
   const int nb = pressure_red_blocks();
-  // scratch: r, q (direction), w [np]; velocity work [3 n_local]; partials; one sum
+  // scratch: r, q (direction), w, z [np]; velocity work [3 n_local]; partials; one sum
   double* buf = nullptr;
-  const size_t count = 3 * (size_t)np + 3 * (size_t)m->n_local + nb + 1;
+  const size_t count = 4 * (size_t)np + 3 * (size_t)m->n_local + nb + 1;
   SEM_CUDA(cudaMalloc((void**)&buf, count * sizeof(double)));
   struct Free {
     double* b;
@@ -534,7 +607,8 @@ sem_status sem_pressure_solve(const sem_mesh* m, const double* g_dev, double* p_
   double* r = buf;
   double* q = r + np;
   double* w = q + np;
-  double* work = w + np;
+  double* z = w + np;
+  double* work = z + np;
   double* partial = work + 3 * m->n_local;
   double* sum_d = partial + nb;
   const GsDev g = gs_dev(m);
@@ -564,6 +638,22 @@ sem_status sem_pressure_solve(const sem_mesh* m, const double* g_dev, double* p_
   launches += 2;
   SEM_TRY_STATUS(read(rho));
   const double gnorm = std::sqrt(rho);
+  // z = Pm (dinv r) and rho = <r, z> (Jacobi); without it z is r itself
+  auto precondition = [&](double& rz) -> sem_status {
+    double zs = 0.0;
+    SEM_CUDA(launch_pscale(r, m->pdinv, z, np, partial, sum_d, s));
+    SEM_TRY_STATUS(read(zs));
+    SEM_CUDA(launch_pshift_dot(z, r, zs / (double)np, np, partial, sum_d, s));
+    SEM_TRY_STATUS(read(rz));
+    launches += 4;
+    return SEM_OK;
+  };
+  const double* zdir = jac ? z : r;
+  if (jac && gnorm > 0.0) {
+    SEM_TRY_STATUS(precondition(rho));
+    SEM_CUDA(launch_pdir(q, z, 0.0, np, s));
+    launches += 1;
+  }
   // out = E v (weak gradient, QQ^T with mask on each component, inverse mass, weak divergence)
   auto apply_E = [&](const double* v, double* out) -> sem_status {
     SEM_CUDA(launch_pgrad<double>(v, m->Fgl, m->Igl, m->DIgl, m->n, (int)mm, m->E, work, m->n_local, s));
@@ -592,29 +682,40 @@ sem_status sem_pressure_solve(const sem_mesh* m, const double* g_dev, double* p_
         break;
       }
       const double alpha = rho / sigma;
+      double rr_new = 0.0;
       SEM_CUDA(launch_pupdate(p_dev, r, q, w, alpha, np, partial, sum_d, s));
       launches += 2;
-      SEM_TRY_STATUS(read(rho_new));
-      rel = std::sqrt(rho_new) / gnorm;
-      if (std::sqrt(rho_new) <= tol * gnorm) {
+      SEM_TRY_STATUS(read(rr_new));
+      rel = std::sqrt(rr_new) / gnorm;
+      if (std::sqrt(rr_new) <= tol * gnorm) {
         // the true residual Pm (g - E x); restart from x if the recurrence drifted
         SEM_TRY_STATUS(apply_E(p_dev, w));
-        double xs = 0.0;
+        double xs = 0.0, rr_t = 0.0;
         SEM_CUDA(launch_pdot(w, nullptr, np, partial, sum_d, s));
         SEM_TRY_STATUS(read(xs));
         SEM_CUDA(launch_presidual(g_dev, gsum / (double)np, w, xs / (double)np, r, q, np, partial, sum_d, s));
         launches += 4;
-        SEM_TRY_STATUS(read(rho));
-        rel = std::sqrt(rho) / gnorm;
-        if (std::sqrt(rho) <= tol * gnorm) {
+        SEM_TRY_STATUS(read(rr_t));
+        rel = std::sqrt(rr_t) / gnorm;
+        if (std::sqrt(rr_t) <= tol * gnorm) {
           status = SEM_OK;
           break;
         }
         if (restarts == kPressureMaxRestarts) break;
         ++restarts;
-        continue;  // q = r: a steepest-descent restart
+        // a steepest-descent restart: q = z
+        if (jac) {
+          SEM_TRY_STATUS(precondition(rho));
+          SEM_CUDA(launch_pdir(q, z, 0.0, np, s));
+          launches += 1;
+        } else {
+          rho = rr_t;  // q = r already
+        }
+        continue;
       }
-      SEM_CUDA(launch_pdir(q, r, rho_new / rho, np, s));
+      if (jac) SEM_TRY_STATUS(precondition(rho_new));
+      else rho_new = rr_new;
+      SEM_CUDA(launch_pdir(q, zdir, rho_new / rho, np, s));
       launches += 1;
       rho = rho_new;
     }

@@ -148,6 +148,7 @@ struct sem_mesh {
   // under p_mutex: GL-point factors F [E][9][m^3] (rho^3 adj(J)_{ba}, index
   // 3 b + a) and the GLL basis values / derivatives at the GL points [m][n]
   mutable std::mutex p_mutex;
+  mutable double* pdinv = nullptr;  // [E m^3] 1 / diag(E), the pressure CG's Jacobi preconditioner
   mutable double* Fgl = nullptr;
   mutable double* Igl = nullptr;
   mutable double* DIgl = nullptr;

@@ -19,6 +19,7 @@ SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN, SEM_ERR_BUSY, SEM_ERR_DEVICE_TIMEOUT =
 SEM_ERR_BAD_MESH, SEM_ERR_TIMEOUT, SEM_ERR_NOT_FOUND, SEM_ERR_CANCELLED = 8, 9, 10, 11
 NOALLOC_MAX_POINTS = 1 << 18
 FP64, FP32, MIXED = 0, 1, 2
+PRECOND_DEFAULT, PRECOND_NONE, PRECOND_JACOBI = 0, 1, 2
 KIND = {"box": 0, "pipe": 1, "explicit": 2}
 
 
@@ -46,7 +47,7 @@ class MeshInfo(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("h1", C.c_double), ("h2", C.c_double), ("inner_tol", C.c_double),
                 ("maxit", C.c_int), ("max_outer", C.c_int), ("prec", C.c_int), ("refine", C.c_int),
-                ("delta", C.c_double)]
+                ("delta", C.c_double), ("precond", C.c_int)]
 
 
 class SolveResult(C.Structure):
@@ -132,6 +133,7 @@ SIGNATURES = {
     "sem_schwarz_apply": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "sem_schwarz_solve": (C.c_int, [_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveResult), _P]),
     "sem_pressure_info": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+    "sem_pressure_diag": (C.c_int, [_P, _P, _P]),
     "sem_pressure_factors": (C.c_int, [_P, _P, _P]),
     "sem_pressure_grad": (C.c_int, [_P, _P, _P, _P]),
     "sem_pressure_div": (C.c_int, [_P, _P, _P, _P]),
@@ -221,11 +223,12 @@ def make_desc(desc):
     return d, keep
 
 
-def _opts(tol=1e-10, h1=1.0, h2=0.0, prec=FP64, inner_tol=0.0, maxit=0, max_outer=0, refine=0, delta=0.0):
+def _opts(tol=1e-10, h1=1.0, h2=0.0, prec=FP64, inner_tol=0.0, maxit=0, max_outer=0, refine=0, delta=0.0,
+          precond=0):
     o = SolveOpts()
     o.tol, o.h1, o.h2, o.inner_tol = float(tol), float(h1), float(h2), float(inner_tol)
     o.maxit, o.max_outer, o.prec = int(maxit), int(max_outer), int(prec)
-    o.refine, o.delta = int(refine), float(delta)
+    o.refine, o.delta, o.precond = int(refine), float(delta), int(precond)
     return o
 
 
@@ -391,13 +394,21 @@ class Mesh:
                "sem_pressure_apply_f32")
         return q
 
-    def pressure_solve(self, g, p, tol=1e-10, maxit=0, stream=None, check=False, prec=FP64, delta=0.0):
-        """sem_pressure_solve: E p = g on the mean-free pressure space (CG;
-        prec=MIXED: FP32 operator with FP64 reliable updates); returns the
-        result record (a dict), raising on errors other than not-converged /
-        breakdown unless check=True."""
+    def pressure_diag(self, d, stream=None):
+        """sem_pressure_diag: diag(E) into the FP64 device tensor d [E, m, m, m]."""
         import torch
-        o = _opts(tol=tol, maxit=maxit, prec=prec, delta=delta)
+        _check(lib().sem_pressure_diag(self._h, _dptr(d, torch.float64, self.pressure_size()), _stream(stream)),
+               "sem_pressure_diag")
+
+    def pressure_solve(self, g, p, tol=1e-10, maxit=0, stream=None, check=False, prec=FP64, delta=0.0,
+                       precond=PRECOND_DEFAULT):
+        """sem_pressure_solve: E p = g on the mean-free pressure space (CG,
+        Jacobi-preconditioned unless precond=PRECOND_NONE; prec=MIXED: FP32
+        operator with FP64 reliable updates); returns the result record (a
+        dict), raising on errors other than not-converged / breakdown unless
+        check=True."""
+        import torch
+        o = _opts(tol=tol, maxit=maxit, prec=prec, delta=delta, precond=precond)
         r = SolveResult()
         np_ = self.pressure_size()
         st = lib().sem_pressure_solve(self._h, _dptr(g, torch.float64, np_), _dptr(p, torch.float64, np_),

@@ -172,11 +172,24 @@ SOLVE_CASES = {
 }
 
 
+@pytest.mark.parametrize("name", list(CASES))
+def test_diagonal_matches_oracle(name):
+    """diag(E) (the pressure CG's Jacobi preconditioner) against the oracle's,
+    which is itself pinned to the diagonal of the dense E."""
+    import torch
+    m, P = setup(name)
+    d = torch.full(P.shape, float("nan"), dtype=torch.float64, device="cuda")
+    m.pressure_diag(d)
+    assert relerr(d.cpu().numpy(), P.diagonal()) <= TOL
+
+
 @pytest.mark.parametrize("name", list(SOLVE_CASES))
-def test_pressure_solve_matches_oracle(name):
-    """CG on the mean-free space: iteration count within 2 of the oracle's, the
-    GPU solution's residual Pm (g - E x) recomputed with the oracle's E within
-    the tolerance, mean zero, and close to the oracle's solution."""
+@pytest.mark.parametrize("precond", ["NONE", "JACOBI"])
+def test_pressure_solve_matches_oracle(name, precond):
+    """CG on the mean-free space, plain and Jacobi-preconditioned: iteration
+    count within 2 of the oracle's, the GPU solution's residual Pm (g - E x)
+    recomputed with the oracle's E within the tolerance, mean zero, and close
+    to the oracle's solution."""
     import torch
     import paper_2109_03592_gb300 as sem
     desc = SOLVE_CASES[name]
@@ -184,9 +197,10 @@ def test_pressure_solve_matches_oracle(name):
     P = pressure.Pressure(solver.Problem(_oracle_mesh(desc)))
     g = np.random.default_rng(12).standard_normal(P.shape)
     x = torch.full(P.shape, float("nan"), dtype=torch.float64, device="cuda")
-    r = m.pressure_solve(to_gpu(g), x, tol=1e-10)
+    r = m.pressure_solve(to_gpu(g), x, tol=1e-10, precond=getattr(sem, "PRECOND_" + precond))
     assert r["status"] == 0, r
-    xo, it, rel, st = pressure.cg(P, g, tol=1e-10)
+    dinv = 1.0 / P.diagonal() if precond == "JACOBI" else None
+    xo, it, rel, st = pressure.cg(P, g, tol=1e-10, dinv=dinv)
     assert st == solver.CONVERGED
     assert abs(r["iters"] - it) <= 2, (r["iters"], it)
     assert r["rel_res"] <= 1e-10
@@ -235,6 +249,8 @@ def test_pressure_solve_on_the_4096_element_pipe():
     gm = g - g.mean()
     assert (res.norm() / gm.norm()).item() <= 2e-10
     assert abs(x.sum().item()) <= 1e-10 * x.abs().sum().item()
+    plain = m.pressure_solve(g, torch.empty_like(g), tol=1e-10, precond=sem.PRECOND_NONE)
+    assert plain["status"] == 0 and r["iters"] < plain["iters"], (r, plain)
     m.close()
 
 

@@ -189,3 +189,32 @@ def test_pressure_cg_zero_rhs_and_constant_rhs():
     for g in (np.zeros(P.shape), np.full(P.shape, 2.5)):
         x, it, rel, st = pressure.cg(P, g)
         assert st == solver.CONVERGED and it == 0 and not x.any()
+
+
+@pytest.mark.parametrize("kind,N", [("box", 2), ("box", 3), ("box", 4), ("pipe", 3), ("pipe_open", 4)])
+def test_diagonal_is_the_dense_diagonal(kind, N):
+    """Pressure.diagonal() (the Jacobi preconditioner, rows of the weak
+    divergence squared against mask / assembled mass) against the diagonal
+    of E assembled column by column from unit pressures."""
+    if kind == "box":
+        m_ = mesh.box(2, 1, 2, N, lx=1.0, ly=0.7, lz=1.3)
+    elif kind == "pipe":
+        m_ = mesh.pipe(1, 1, 3, N, L=1.5)
+    else:
+        m_ = mesh.pipe(1, 1, 3, N, L=1.5, periodic=False)
+    P = pressure.Pressure(solver.Problem(m_))
+    d = P.diagonal()
+    assert np.all(d > 0)
+    np.testing.assert_allclose(d.reshape(-1), np.diag(P.dense()), rtol=1e-13, atol=0)
+
+
+def test_jacobi_cg_reaches_the_plain_solution_in_fewer_iterations():
+    m_ = mesh.pipe(2, 1, 3, 4, L=1.5)
+    P = pressure.Pressure(solver.Problem(m_))
+    g = np.random.default_rng(5).standard_normal(P.shape)
+    x0, it0, r0, s0 = pressure.cg(P, g, tol=1e-10)
+    x1, it1, r1, s1 = pressure.cg(P, g, tol=1e-10, dinv=1.0 / P.diagonal())
+    assert s0 == solver.CONVERGED and s1 == solver.CONVERGED
+    assert r1 <= 1e-10 and it1 < it0
+    assert abs(x1.mean()) <= 1e-12 * np.abs(x1).max()
+    np.testing.assert_allclose(x1, x0, rtol=0, atol=1e-7 * np.abs(x0).max())
