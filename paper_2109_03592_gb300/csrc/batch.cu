@@ -37,7 +37,8 @@ namespace batch {
 constexpr int kMaxSlots = 32;
 constexpr int kChunk = 8;
 constexpr int kVecThreads = 256;
-constexpr int kVecW = 4;  // floats per thread per virtual block step
+constexpr int kVecW = 8;  // floats per thread per virtual block (two 16-byte vectors)
+constexpr int kTileGroup = 8;  // consecutive tiles of one request per <p, A p> partial
 constexpr int kVecPts = kVecThreads * kVecW;
 constexpr int kGsThreads = 256;
 
@@ -68,6 +69,7 @@ struct Table {
   const float* D;  // derivative matrix of the table's order (any active request's copy)
   Slot s[kMaxSlots];
   int64_t tile_off[kMaxSlots + 1];
+  int64_t grp_off[kMaxSlots + 1];  // tile groups (kTileGroup tiles) per request, prefix
   int64_t gs_vb[kMaxSlots * 9 + 1];
   int64_t vec_vb[kMaxSlots + 1];
   unsigned int cnt[kMaxSlots];
@@ -99,6 +101,7 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_bax(const Table* __re
   uint64_t* bars = reinterpret_cast<uint64_t*>(sws + EPB * n3);
   __shared__ int slive[kMaxSlots];
   __shared__ int64_t stoff[kMaxSlots + 1];
+  __shared__ int64_t sgoff[kMaxSlots + 1];
   __shared__ int snslots, sflag;
   __shared__ double sred[32];
 
@@ -109,21 +112,36 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_bax(const Table* __re
   }
   __syncthreads();
   const int ns = snslots;
-  for (int r = tid; r < ns; r += blockDim.x) slive[r] = live(T->s[r]);
-  for (int r = tid; r <= ns; r += blockDim.x) stoff[r] = T->tile_off[r];
-  if (ns > 0) {
-    for (int q = tid; q < n2; q += blockDim.x) sD[q] = T->D[q];  // one order per table
+  int any = 0;
+  for (int r = tid; r < ns; r += blockDim.x) any |= (slive[r] = live(T->s[r]));
+  // every request paused or finished (the rest of a chunk after its last
+  // iteration): return before any set-up
+  if (!__syncthreads_or(any)) return;
+  for (int r = tid; r <= ns; r += blockDim.x) {
+    stoff[r] = T->tile_off[r];
+    sgoff[r] = T->grp_off[r];
   }
+  for (int q = tid; q < n2; q += blockDim.x) sD[q] = T->D[q];  // one order per table
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) tma::mbar_init(&bars[s], 1);
     tma::fence_mbar_init();
   }
   __syncthreads();
-  if (ns == 0) return;
-  const int64_t total = stoff[ns];
-  auto next_live = [&](int64_t t) {
-    while (t < total && !slive[find_slot(stoff, ns, t)]) t += gridDim.x;
-    return t;
+  // Work comes in tile groups: kTileGroup consecutive tiles of one request,
+  // taken by the CTAs in grid strides.  A group's <p, A p> partial is summed
+  // by the one CTA that runs it, in tile order, so it does not depend on the
+  // other requests in the table (a request's result is the same alone and in
+  // a batch) and costs one block reduction per group instead of per tile.
+  const int64_t gtotal = sgoff[ns];
+  auto next_group = [&](int64_t g) {
+    while (g < gtotal && !slive[find_slot(sgoff, ns, g)]) g += gridDim.x;
+    return g;
+  };
+  auto group_tiles = [&](int64_t g, int64_t& t0) {  // first tile and tile count of group g
+    const int r = find_slot(sgoff, ns, g);
+    const int64_t lt = (g - sgoff[r]) * kTileGroup;
+    t0 = stoff[r] + lt;
+    return (int)min((int64_t)kTileGroup, stoff[r + 1] - stoff[r] - lt);
   };
   auto issue = [&](int s, int64_t t) {
     const int r = find_slot(stoff, ns, t);
@@ -137,36 +155,65 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_bax(const Table* __re
     tma::bulk_g2s(st + EPB * n3, sl.p + e0 * n3, bu, &bars[s]);
     tma::bulk_g2s(st + 2 * EPB * n3, sl.G + e0 * 6 * n3, bg, &bars[s]);
   };
-  int64_t ptile = next_live(blockIdx.x);  // producer cursor (thread 0)
-  int64_t nissued = 0;                     // tiles issued so far (thread 0)
+  // producer cursor (thread 0): group pg, tile pk of pn in it, from tile pt0
+  int64_t pg = next_group(blockIdx.x), pt0 = 0;
+  int pk = 0, pn = pg < gtotal ? group_tiles(pg, pt0) : 0;
+  auto padvance = [&]() {
+    if (++pk < pn) return;
+    pg = next_group(pg + gridDim.x);
+    pk = 0;
+    pn = pg < gtotal ? group_tiles(pg, pt0) : 0;
+  };
+  int64_t nissued = 0;  // tiles issued so far (thread 0)
   if (tid == 0) {
-    for (int s = 0; s < STAGES && ptile < total; ++s) {
-      issue(s, ptile);
+    for (int s = 0; s < STAGES && pg < gtotal; ++s) {
+      issue(s, pt0 + pk);
       ++nissued;
-      ptile = next_live(ptile + gridDim.x);
+      padvance();
     }
   }
 
   const int le = tid / n2, ij = tid - le * n2, i = ij % n, j = ij / n;
   int64_t it = 0;
-  for (int64_t tile = next_live(blockIdx.x); tile < total; tile = next_live(tile + gridDim.x), ++it) {
+  int64_t cg = next_group(blockIdx.x), ct0 = 0;
+  int ck = 0, cn = cg < gtotal ? group_tiles(cg, ct0) : 0;
+  double pwg = 0.0;  // this thread's part of the group's <p, A p>
+  // the group's request, its fields in registers: read once per group, and
+  // before any store through its pointers (which could alias the table)
+  float *slp = nullptr, *slw = nullptr;
+  const float* slB = nullptr;
+  float h1 = 0.f, h2 = 0.f, beta = 0.f;
+  int helm = 0;
+  int64_t sE = 0, sT0 = 0;
+  for (; cg < gtotal; ++it) {
+    const int64_t tile = ct0 + ck;
     const int s = (int)(it % STAGES);
+    if (ck == 0) {
+      const int r = find_slot(stoff, ns, tile);
+      const Slot& sl = T->s[r];
+      slp = sl.p;
+      slw = sl.w;
+      slB = sl.B;
+      h1 = sl.h1;
+      h2 = sl.h2;
+      helm = sl.helm;
+      sE = sl.E;
+      sT0 = stoff[r];
+      beta = (float)sl.st->beta;
+    }
     if (!tma::mbar_wait(&bars[s], (uint32_t)((it / STAGES) & 1))) sflag = 1;
     __syncthreads();
     if (sflag) break;
-    const int r = find_slot(stoff, ns, tile);
-    const Slot& sl = T->s[r];
     float* st = stage0 + s * Lay::stage_floats;
     float* su = st + le * n3;
     const float* sG = st + 2 * EPB * n3 + le * 6 * n3;
-    const int64_t e = (tile - stoff[r]) * EPB + le;
-    const bool act = e < sl.E;
+    const int64_t e = (tile - sT0) * EPB + le;
+    const bool act = e < sE;
     const int64_t base = e * n3 + ij;
-    const float beta = (float)sl.st->beta;
     // B loaded ahead of the stores of this tile (see the single-mesh kernel)
     float rb[n];
 #pragma unroll
-    for (int k = 0; k < n; ++k) rb[k] = (act && sl.helm) ? __ldg(sl.B + base + k * n2) : 0.f;
+    for (int k = 0; k < n; ++k) rb[k] = (act && helm) ? __ldg(slB + base + k * n2) : 0.f;
 
     float ru[n];
     if (act) {
@@ -174,7 +221,7 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_bax(const Table* __re
       for (int k = 0; k < n; ++k) {
         const float v = su[k * n2 + ij] + beta * st[EPB * n3 + le * n3 + k * n2 + ij];
         su[k * n2 + ij] = v;
-        sl.p[base + k * n2] = v;
+        slp[base + k * n2] = v;
         ru[k] = v;
       }
     }
@@ -202,11 +249,11 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_bax(const Table* __re
       }
     }
     __syncthreads();
-    if (tid == 0 && ptile < total) {
+    if (tid == 0 && pg < gtotal) {
       tma::fence_async_smem();
-      issue(s, ptile);
+      issue(s, pt0 + pk);
       ++nissued;
-      ptile = next_live(ptile + gridDim.x);
+      padvance();
     }
     float pw = 0.f;
     if (act) {
@@ -216,14 +263,21 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_bax(const Table* __re
 #pragma unroll
         for (int l = 0; l < n; ++l)
           acc += sD[l * n + i] * swr[le * n3 + k * n2 + j * n + l] + sD[l * n + j] * sws[le * n3 + k * n2 + l * n + i];
-        float out = sl.h1 * acc;
-        if (sl.helm) out += sl.h2 * rb[k] * ru[k];
-        sl.w[base + k * n2] = out;
+        float out = h1 * acc;
+        if (helm) out += h2 * rb[k] * ru[k];
+        slw[base + k * n2] = out;
         pw += ru[k] * out;
       }
     }
-    const double bs = block_sum((double)pw, sred);
-    if (tid == 0) part_tile[tile] = bs;
+    pwg += (double)pw;
+    if (++ck == cn) {  // the group's last tile: its partial
+      const double bs = block_sum(pwg, sred);
+      if (tid == 0) part_tile[cg] = bs;
+      pwg = 0.0;
+      cg = next_group(cg + gridDim.x);
+      ck = 0;
+      cn = cg < gtotal ? group_tiles(cg, ct0) : 0;
+    }
     __syncthreads();
   }
   if (sflag && tid == 0) {
@@ -244,7 +298,7 @@ __global__ void __launch_bounds__(256) k_balpha(const Table* __restrict__ T, con
   if (r >= T->nslots) return;
   const Slot& sl = T->s[r];
   if (!sl.active || sl.st->done) return;
-  const int64_t b = T->tile_off[r], e = T->tile_off[r + 1];
+  const int64_t b = T->grp_off[r], e = T->grp_off[r + 1];
   double v = 0.0;
   for (int64_t q = b + threadIdx.x; q < e; q += blockDim.x) v += part_tile[q];
   const double pAp = block_sum(v, sred);
@@ -269,36 +323,56 @@ __device__ __forceinline__ void bgs_node(float* __restrict__ v, const int32_t* _
   for (int c = 1; c < M; ++c) v[id[c]] = acc;
 }
 
+// Live flags and the slots' virtual-block offsets staged in shared memory
+// once per CTA; false when no request is live (the CTA returns at once).
+// A dead slot's virtual blocks are skipped in whole grid strides.
+__device__ __forceinline__ int64_t skip_dead(const int64_t* off, int r, int64_t vb) {
+  const int64_t end = off[r + 1];
+  return vb + ((end - vb - 1) / gridDim.x) * gridDim.x;  // this CTA's last block before end
+}
+
 __global__ void __launch_bounds__(kGsThreads) k_bgs(const Table* __restrict__ T) {
+  __shared__ int64_t svb[kMaxSlots * 9 + 1];
+  __shared__ int slive[kMaxSlots];
   const int ns = T->nslots;
-  const int64_t total = T->gs_vb[ns * 9];
+  int any = 0;
+  for (int r = threadIdx.x; r < ns; r += blockDim.x) any |= (slive[r] = live(T->s[r]));
+  if (!__syncthreads_or(any)) return;
+  for (int q = threadIdx.x; q <= ns * 9; q += blockDim.x) svb[q] = T->gs_vb[q];
+  __syncthreads();
+  const int64_t total = svb[ns * 9];
   for (int64_t vb = blockIdx.x; vb < total; vb += gridDim.x) {
-    const int rc = find_slot(T->gs_vb, ns * 9, vb);
+    const int rc = find_slot(svb, ns * 9, vb);
     const int r = rc / 9, c = rc % 9;
+    if (!slive[r]) {
+      vb = skip_dead(svb, rc, vb);
+      continue;
+    }
     const Slot& sl = T->s[r];
-    if (!sl.active || sl.st->done) continue;
-    const int64_t t = (vb - T->gs_vb[rc]) * kGsThreads + threadIdx.x;
+    const int64_t t = (vb - svb[rc]) * kGsThreads + threadIdx.x;
     if (t >= sl.gs_cnt[c]) continue;
+    float* const w = sl.w;
     const int32_t* base = sl.gs_idx + sl.gs_off[c];
     if (c < 7) {
       const int M = c + 2;
       const int32_t* id = base + t * M;
       if (id[0] < 0) {  // Dirichlet node: masked to zero
-        sl.w[id[0] & 0x7fffffff] = 0.f;
-        for (int q = 1; q < M; ++q) sl.w[id[q]] = 0.f;
+        w[id[0] & 0x7fffffff] = 0.f;
+        for (int q = 1; q < M; ++q) w[id[q]] = 0.f;
       } else {
-        bgs_node(sl.w, id, M);
+        bgs_node(w, id, M);
       }
     } else if (c == 7) {
-      const int32_t b0 = sl.gs_ptr[t], e0 = sl.gs_ptr[t + 1];
+      const int32_t* gp = sl.gs_ptr;
+      const int32_t b0 = gp[t], e0 = gp[t + 1];
       if (base[b0] < 0) {
-        sl.w[base[b0] & 0x7fffffff] = 0.f;
-        for (int32_t q = b0 + 1; q < e0; ++q) sl.w[base[q]] = 0.f;
+        w[base[b0] & 0x7fffffff] = 0.f;
+        for (int32_t q = b0 + 1; q < e0; ++q) w[base[q]] = 0.f;
       } else {
-        bgs_node(sl.w, base + b0, e0 - b0);
+        bgs_node(w, base + b0, e0 - b0);
       }
     } else {
-      sl.w[base[t] & 0x7fffffff] = 0.f;
+      w[base[t] & 0x7fffffff] = 0.f;
     }
   }
 }
@@ -315,32 +389,80 @@ struct AccF {
   __device__ __forceinline__ double get() const { return (double)s + (double)c; }
 };
 
-__global__ void __launch_bounds__(kVecThreads) k_bupdate(Table* __restrict__ T, double* part_vec) {
+__global__ void __launch_bounds__(kVecThreads, 4) k_bupdate(Table* __restrict__ T, double* part_vec) {
   __shared__ double sred[32];
   __shared__ float sinv[128];
   __shared__ bool is_last;
+  __shared__ int64_t svb[kMaxSlots + 1];
+  __shared__ int slive[kMaxSlots];
+  const int ns = T->nslots;
+  int any = 0;
+  for (int r = threadIdx.x; r < ns; r += blockDim.x) any |= (slive[r] = live(T->s[r]));
+  if (!__syncthreads_or(any)) return;
+  for (int r = threadIdx.x; r <= ns; r += blockDim.x) svb[r] = T->vec_vb[r];
   for (int m = threadIdx.x; m < 128; m += blockDim.x) sinv[m] = m ? 1.f / (float)m : 0.f;
   __syncthreads();
-  const int ns = T->nslots;
-  const int64_t total = T->vec_vb[ns];
+  const int64_t total = svb[ns];
   for (int64_t vb = blockIdx.x; vb < total; vb += gridDim.x) {
-    const int r = find_slot(T->vec_vb, ns, vb);
+    const int r = find_slot(svb, ns, vb);
+    if (!slive[r]) {
+      vb = skip_dead(svb, r, vb);
+      continue;
+    }
+    // the slot's fields in registers before the first store (see k_bax)
     Slot& sl = T->s[r];
-    if (!sl.active || sl.st->done) continue;
+    float4* const x = reinterpret_cast<float4*>(sl.x);
+    float4* const rv = reinterpret_cast<float4*>(sl.r);
+    float4* const z = reinterpret_cast<float4*>(sl.z);
+    const float4* const p = reinterpret_cast<const float4*>(sl.p);
+    const float4* const w = reinterpret_cast<const float4*>(sl.w);
+    const float4* const minv = reinterpret_cast<const float4*>(sl.minv);
+    const uchar4* const wm = reinterpret_cast<const uchar4*>(sl.wm);
+    const int64_t nl = sl.n_local;
     const float alpha = (float)sl.st->alpha;
-    const int64_t p0 = (vb - T->vec_vb[r]) * kVecPts;
+    // kVecW / 4 16-byte vectors per thread, each of 4 consecutive points (n_local
+    // is a multiple of 8 for every odd order, and the vectors are 16-byte
+    // aligned); all loads issued before the first store
+    const int64_t q0 = (vb - svb[r]) * (kVecPts / 4) + threadIdx.x;
+    constexpr int U = kVecW / 4;
     AccF rz, rr;
-    for (int k = 0; k < kVecW; ++k) {
-      const int64_t q = p0 + (int64_t)k * kVecThreads + threadIdx.x;
-      if (q >= sl.n_local) break;
-      const float rq = sl.r[q] - alpha * sl.w[q];
-      sl.x[q] = sl.x[q] + alpha * sl.p[q];
-      sl.r[q] = rq;
-      const float zq = sl.minv[q] * rq;
-      sl.z[q] = zq;
-      const float im = sinv[sl.wm[q] & 0x7f];
-      rz.add(rq * zq * im);
-      rr.add(rq * rq * im);
+    float4 pv[U], wv[U], mv[U], xv[U], rq[U];
+    uchar4 mk[U];
+    bool in[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t q = q0 + (int64_t)u * kVecThreads;
+      in[u] = 4 * q < nl;
+      if (in[u]) {
+        pv[u] = p[q];
+        wv[u] = w[q];
+        mv[u] = minv[q];
+        xv[u] = x[q];
+        rq[u] = rv[q];
+        mk[u] = wm[q];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!in[u]) continue;
+      const int64_t q = q0 + (int64_t)u * kVecThreads;
+      float4 a = xv[u], b = rq[u];
+      a.x += alpha * pv[u].x; a.y += alpha * pv[u].y; a.z += alpha * pv[u].z; a.w += alpha * pv[u].w;
+      b.x -= alpha * wv[u].x; b.y -= alpha * wv[u].y; b.z -= alpha * wv[u].z; b.w -= alpha * wv[u].w;
+      const float4 zq = make_float4(mv[u].x * b.x, mv[u].y * b.y, mv[u].z * b.z, mv[u].w * b.w);
+      x[q] = a;
+      rv[q] = b;
+      z[q] = zq;
+      const float i0 = sinv[mk[u].x & 0x7f], i1 = sinv[mk[u].y & 0x7f], i2 = sinv[mk[u].z & 0x7f],
+                  i3 = sinv[mk[u].w & 0x7f];
+      rz.add(b.x * zq.x * i0);
+      rz.add(b.y * zq.y * i1);
+      rz.add(b.z * zq.z * i2);
+      rz.add(b.w * zq.w * i3);
+      rr.add(b.x * b.x * i0);
+      rr.add(b.y * b.y * i1);
+      rr.add(b.z * b.z * i2);
+      rr.add(b.w * b.w * i3);
     }
     const double a = block_sum(rz.get(), sred);
     const double b = block_sum(rr.get(), sred);
@@ -348,14 +470,14 @@ __global__ void __launch_bounds__(kVecThreads) k_bupdate(Table* __restrict__ T, 
       part_vec[2 * vb] = a;
       part_vec[2 * vb + 1] = b;
       __threadfence();
-      const unsigned int nvb = (unsigned int)(T->vec_vb[r + 1] - T->vec_vb[r]);
+      const unsigned int nvb = (unsigned int)(svb[r + 1] - svb[r]);
       is_last = atomicAdd(&T->cnt[r], 1u) == nvb - 1;
     }
     __syncthreads();
     if (is_last) {
       __threadfence();
       double vz = 0.0, vr = 0.0;
-      for (int64_t q = T->vec_vb[r] + threadIdx.x; q < T->vec_vb[r + 1]; q += blockDim.x) {
+      for (int64_t q = svb[r] + threadIdx.x; q < svb[r + 1]; q += blockDim.x) {
         vz += __ldcg(part_vec + 2 * q);
         vr += __ldcg(part_vec + 2 * q + 1);
       }
@@ -736,9 +858,10 @@ class EngineImpl {
       if (slots_[r]) ns = r + 1;
     T.nslots = ns;
     const int epb = ax_elems_per_block(N_, 1);
-    int64_t tiles = 0, gvb = 0, vvb = 0;
+    int64_t tiles = 0, groups = 0, gvb = 0, vvb = 0;
     for (int r = 0; r < ns; ++r) {
       T.tile_off[r] = tiles;
+      T.grp_off[r] = groups;
       T.vec_vb[r] = vvb;
       Req* q = slots_[r];
       Slot& sl = T.s[r];
@@ -770,7 +893,9 @@ class EngineImpl {
         sl.active = 1;
         sl.E = m->E;
         sl.n_local = m->n_local;
-        tiles += (m->E + epb - 1) / epb;
+        const int64_t nt = (m->E + epb - 1) / epb;
+        tiles += nt;
+        groups += (nt + kTileGroup - 1) / kTileGroup;
         vvb += (m->n_local + kVecPts - 1) / kVecPts;
         for (int c = 0; c < 9; ++c) {
           T.gs_vb[r * 9 + c] = gvb;
@@ -783,6 +908,7 @@ class EngineImpl {
       }
     }
     T.tile_off[ns] = tiles;
+    T.grp_off[ns] = groups;
     T.vec_vb[ns] = vvb;
     T.gs_vb[ns * 9] = gvb;
     if (tiles > cap_tiles_ || vvb > cap_vb_) {
