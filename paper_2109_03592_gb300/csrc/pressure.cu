@@ -10,9 +10,12 @@
 //     differentiates along direction b and interpolates along the other two
 //     (DIg along b, Ig elsewhere);
 //   * weak gradient    u_a = sum_b C_b^T (F[b][a] p), the transpose of D.
-// Every kernel runs one CTA per element and applies each C_b as three 1D
-// contractions through shared memory (sum factorisation), in FP64.
+// The factors and the diagonal run one CTA per element in FP64; the weak
+// gradient and divergence (pressure_line.cuh) apply each C_b as 1D
+// contractions of whole lines held in registers, several elements per CTA,
+// in FP64 or FP32.
 #include "kernels.h"
+#include "pressure_line.cuh"
 
 namespace sem {
 
@@ -89,133 +92,8 @@ __global__ void k_gl_factors(const double* __restrict__ xyz, const double* __res
   }
 }
 
-// u_a = sum_b C_b^T (F[b][a] p) for a = 0, 1, 2 (local, unassembled).
-// Shared memory: the two 1D matrices [m][n], tb [m^3], T1 [m][m][n],
-// T2 [m][n][n], acc [n^3].  Each thread owns the acc entries q = tid + t blockDim.
-// T = double (FP64) or float (the FP32 operator of the mixed-precision solve).
-// N as a template parameter: the loop bounds and the index arithmetic (q / n,
-// q % n) are compile-time constants (the kernels were integer-issue bound with
-// run-time n: ALU pipe 44-58%, issue 80-88% in FP32).
-template <typename T, int N>
-__global__ void k_pgrad(const T* __restrict__ p, const T* __restrict__ F, const T* __restrict__ Ig,
-                        const T* __restrict__ DIg, int64_t E, T* __restrict__ u, int64_t n_local) {
-  constexpr int n = N + 1, m = N - 1;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  T* sm = reinterpret_cast<T*>(sm_raw);
-  constexpr int n2 = n * n, n3 = n2 * n, m2 = m * m, m3 = m2 * m;
-  T* sI = sm;
-  T* sD = sI + m * n;
-  T* tb = sD + m * n;
-  T* T1 = tb + m3;
-  T* T2 = T1 + m2 * n;
-  T* acc = T2 + m * n2;
-  const int64_t e = blockIdx.x;
-  if (e >= E) return;
-  for (int q = threadIdx.x; q < m * n; q += blockDim.x) {
-    sI[q] = Ig[q];
-    sD[q] = DIg[q];
-  }
-  const T* pe = p + e * m3;
-  for (int a = 0; a < 3; ++a) {
-    for (int q = threadIdx.x; q < n3; q += blockDim.x) acc[q] = T(0);
-    for (int b = 0; b < 3; ++b) {
-      const T* Mi = b == 0 ? sD : sI;
-      const T* Mj = b == 1 ? sD : sI;
-      const T* Mk = b == 2 ? sD : sI;
-      const T* Fba = F + (e * 9 + 3 * b + a) * m3;
-      for (int q = threadIdx.x; q < m3; q += blockDim.x) tb[q] = Fba[q] * pe[q];
-      __syncthreads();
-      // T1[k][j][l] = sum_i Mi[i][l] tb[k][j][i]
-      for (int q = threadIdx.x; q < m2 * n; q += blockDim.x) {
-        const int l = q % n, kj = q / n;
-        T s = T(0);
-        for (int i = 0; i < m; ++i) s += Mi[i * n + l] * tb[kj * m + i];
-        T1[q] = s;
-      }
-      __syncthreads();
-      // T2[k][pp][l] = sum_j Mj[j][pp] T1[k][j][l]
-      for (int q = threadIdx.x; q < m * n2; q += blockDim.x) {
-        const int l = q % n, pp = (q / n) % n, k = q / n2;
-        T s = T(0);
-        for (int j = 0; j < m; ++j) s += Mj[j * n + pp] * T1[(k * m + j) * n + l];
-        T2[q] = s;
-      }
-      __syncthreads();
-      // acc[s][pp][l] += sum_k Mk[k][s] T2[k][pp][l]
-      for (int q = threadIdx.x; q < n3; q += blockDim.x) {
-        const int pl = q % n2, s_ = q / n2;
-        T s = T(0);
-        for (int k = 0; k < m; ++k) s += Mk[k * n + s_] * T2[k * n2 + pl];
-        acc[q] += s;
-      }
-    }
-    T* ua = u + a * n_local + e * n3;
-    for (int q = threadIdx.x; q < n3; q += blockDim.x) ua[q] = acc[q];
-  }
-}
-
-// out_q = sum_a sum_b F[b][a](q) (C_b v_a)(q), v_a = u_a / dB when dB is given
-// (the inverse assembled mass), u_a invB when invB (its reciprocal) is given,
-// u_a itself otherwise.  Shared memory: the two
-// 1D matrices, V [n^3], S1 [n][n][m], S2 [n][m][m], oacc [m^3].
-template <typename T, int N>
-__global__ void k_pdiv(const T* __restrict__ u, const T* __restrict__ dB, const T* __restrict__ invB,
-                       const T* __restrict__ F, const T* __restrict__ Ig, const T* __restrict__ DIg, int64_t E,
-                       T* __restrict__ out, int64_t n_local) {
-  constexpr int n = N + 1, m = N - 1;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  T* sm = reinterpret_cast<T*>(sm_raw);
-  constexpr int n2 = n * n, n3 = n2 * n, m2 = m * m, m3 = m2 * m;
-  T* sI = sm;
-  T* sD = sI + m * n;
-  T* V = sD + m * n;
-  T* S1 = V + n3;
-  T* S2 = S1 + n2 * m;
-  T* oacc = S2 + n * m2;
-  const int64_t e = blockIdx.x;
-  if (e >= E) return;
-  for (int q = threadIdx.x; q < m * n; q += blockDim.x) {
-    sI[q] = Ig[q];
-    sD[q] = DIg[q];
-  }
-  for (int q = threadIdx.x; q < m3; q += blockDim.x) oacc[q] = T(0);
-  for (int a = 0; a < 3; ++a) {
-    const T* ua = u + a * n_local + e * n3;
-    for (int q = threadIdx.x; q < n3; q += blockDim.x) V[q] = dB ? ua[q] / dB[e * n3 + q] : (invB ? ua[q] * invB[e * n3 + q] : ua[q]);
-    __syncthreads();
-    for (int b = 0; b < 3; ++b) {
-      const T* Mi = b == 0 ? sD : sI;
-      const T* Mj = b == 1 ? sD : sI;
-      const T* Mk = b == 2 ? sD : sI;
-      // S1[s][pp][i] = sum_l Mi[i][l] V[s][pp][l]
-      for (int q = threadIdx.x; q < n2 * m; q += blockDim.x) {
-        const int i = q % m, spp = q / m;
-        T s = T(0);
-        for (int l = 0; l < n; ++l) s += Mi[i * n + l] * V[spp * n + l];
-        S1[q] = s;
-      }
-      __syncthreads();
-      // S2[s][j][i] = sum_pp Mj[j][pp] S1[s][pp][i]
-      for (int q = threadIdx.x; q < n * m2; q += blockDim.x) {
-        const int i = q % m, j = (q / m) % m, s_ = q / m2;
-        T s = T(0);
-        for (int pp = 0; pp < n; ++pp) s += Mj[j * n + pp] * S1[(s_ * n + pp) * m + i];
-        S2[q] = s;
-      }
-      __syncthreads();
-      // oacc[k][j][i] += F[b][a] sum_s Mk[k][s] S2[s][j][i]
-      const T* Fba = F + (e * 9 + 3 * b + a) * m3;
-      for (int q = threadIdx.x; q < m3; q += blockDim.x) {
-        const int ji = q % m2, k = q / m2;
-        T s = T(0);
-        for (int s_ = 0; s_ < n; ++s_) s += Mk[k * n + s_] * S2[s_ * m2 + ji];
-        oacc[q] += Fba[q] * s;
-      }
-    }
-  }
-  T* oe = out + e * m3;
-  for (int q = threadIdx.x; q < m3; q += blockDim.x) oe[q] = oacc[q];
-}
+// The weak gradient and divergence (k_pgrad_line, k_pdiv_line) are in
+// pressure_line.cuh.
 
 // ---- vector kernels of the pressure CG (pressure values, Euclidean products) ----
 // Reductions are deterministic: block b sums its grid-stride slice in a fixed
@@ -447,13 +325,6 @@ static constexpr int kPressureThreads = 256;
 static constexpr int kPressureRedBlocks = 2 * 152;  // reduction grid: two CTAs per SM
 
 size_t gl_factors_smem(int n, int m) { return sizeof(double) * (3 * n * n * n + 6 * m * n * n); }
-static size_t pgrad_smem(int n, int m, size_t esz) {
-  return esz * (2 * m * n + m * m * m + m * m * n + m * n * n + n * n * n);
-}
-static size_t pdiv_smem(int n, int m, size_t esz) {
-  return esz * (2 * m * n + n * n * n + n * n * m + n * m * m + m * m * m);
-}
-
 cudaError_t launch_gl_factors(const double* xyz, const double* Ig, const double* DIg, const double* rho, int n, int m,
                               int64_t E, double* F, int* bad, cudaStream_t s) {
   const size_t smem = gl_factors_smem(n, m);
@@ -466,26 +337,30 @@ cudaError_t launch_gl_factors(const double* xyz, const double* Ig, const double*
 template <typename T, int N>
 cudaError_t launch_pgrad_n(const T* p, const T* F, const T* Ig, const T* DIg, int64_t E, T* u, int64_t n_local,
                            cudaStream_t s) {
-  const size_t smem = pgrad_smem(N + 1, N - 1, sizeof(T));
+  using S = pline::Shape<T, N>;
   static DeviceOnce once;
   cudaError_t err = once.get([&](int, int*) {
-    return cudaFuncSetAttribute(k_pgrad<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(pline::k_pgrad_line<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
   });
   if (err != cudaSuccess) return err;
-  k_pgrad<T, N><<<(unsigned)E, kPressureThreads, smem, s>>>(p, F, Ig, DIg, E, u, n_local);
+  if (E == 0) return cudaSuccess;
+  pline::k_pgrad_line<T, N><<<(unsigned)((E + S::EPB - 1) / S::EPB), pline::kThreads, S::smem, s>>>(p, F, Ig, DIg, E,
+                                                                                                  u, n_local);
   return cudaGetLastError();
 }
 
 template <typename T, int N>
 cudaError_t launch_pdiv_n(const T* u, const T* dB, const T* invB, const T* F, const T* Ig, const T* DIg, int64_t E,
                           T* out, int64_t n_local, cudaStream_t s) {
-  const size_t smem = pdiv_smem(N + 1, N - 1, sizeof(T));
+  using S = pline::Shape<T, N>;
   static DeviceOnce once;
   cudaError_t err = once.get([&](int, int*) {
-    return cudaFuncSetAttribute(k_pdiv<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(pline::k_pdiv_line<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
   });
   if (err != cudaSuccess) return err;
-  k_pdiv<T, N><<<(unsigned)E, kPressureThreads, smem, s>>>(u, dB, invB, F, Ig, DIg, E, out, n_local);
+  if (E == 0) return cudaSuccess;
+  pline::k_pdiv_line<T, N><<<(unsigned)((E + S::EPB - 1) / S::EPB), pline::kThreads, S::smem, s>>>(
+      u, dB, invB, F, Ig, DIg, E, out, n_local);
   return cudaGetLastError();
 }
 
