@@ -404,9 +404,11 @@ sem_status sem_pressure_apply(const sem_mesh* mesh, const double* p_dev, double*
  * meets tol.  The other fields of opts are ignored.
  * result->rel_res is the true residual once converged.
  * g_dev, p_dev: [E][m^3] FP64; p_dev is output only (mean zero).  Every
- * reduction is deterministic.  Synchronous: the host reads three sums per
- * iteration.  Allocates 3 n_pressure + 3 n_local doubles of scratch for the
- * call.  Returns the solve's status (also in result->status): SEM_OK,
+ * reduction is deterministic.  The iteration runs on the device: its scalars
+ * stay in device memory and 8 iterations are one CUDA graph, launched on a
+ * stream of the call's own (ordered after `stream`); the host reads the
+ * state once per graph and synchronises before returning.  Allocates
+ * 4 n_pressure + 3 n_local doubles of scratch for the call.  Returns the solve's status (also in result->status): SEM_OK,
  * SEM_ERR_NOT_CONVERGED or SEM_ERR_BREAKDOWN (<p, E p> <= 0), with result
  * filled in; result->outer_iters is 0 (SEM_FP64) and result->ms the device
  * time.  SEM_MIXED allocates a further 2 n_pressure + 3 n_local floats, and

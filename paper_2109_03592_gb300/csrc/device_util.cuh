@@ -22,6 +22,8 @@ struct PcgState {
   double aux;    // scratch scalar (outer residual norms)
   double rr_max; // largest <r, r> since the last reliable update
   double delta2; // reliable-update trigger: pause when <r,r> <= delta2 * rr_max (0 = never)
+  double cz;     // pressure CG: mean of D^-1 r (aux holds the mean of E q)
+  int last;      // pressure CG: iteration of the last residual replacement
   int iter;
   int maxit;
   int done;      // 1 once converged / failed / paused: later kernels of the chunk return at once

@@ -167,6 +167,16 @@ cudaError_t launch_pdot(const double* a, const double* b, int64_t n, double* par
 // diagonal; wm's Dirichlet bit is the velocity mask, dB the assembled mass)
 cudaError_t launch_pdiag(const double* F, const double* Ig, const double* DIg, const uint8_t* wm, const double* dB,
                         int n, int m, int64_t E, double* out, int recip, cudaStream_t s);
+// Device-resident pressure CG steps (state in a PcgState, see pressure.cu):
+// sigma and alpha; the update with the stop / pause tests; the direction.
+// partial holds pressure_partials() doubles.
+cudaError_t launch_pcg_psig(const double* q, const double* w, int64_t n, PcgState* st, double* partial,
+                            cudaStream_t s);
+cudaError_t launch_pcg_pupd(bool jac, bool mixed, double* x, double* r, const double* q, const double* w,
+                            const double* dinv, double* z, int64_t n, PcgState* st, double* partial, double gamma2,
+                            int gap, cudaStream_t s);
+cudaError_t launch_pcg_pdir(double* q, const double* zd, int64_t n, const PcgState* st, cudaStream_t s);
+int pressure_partials();
 // z = dinv r; *out = sum z
 cudaError_t launch_pscale(const double* r, const double* dinv, double* z, int64_t n, double* partial, double* out,
                           cudaStream_t s);

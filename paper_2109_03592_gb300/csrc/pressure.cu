@@ -211,6 +211,155 @@ __global__ void k_psum_finish(const double* __restrict__ partial, int cnt, doubl
   if (threadIdx.x == 0) out[0] = t;
 }
 
+// ---- device-resident pressure CG (one PcgState; no host round trip per iteration) ----
+// rho = <r, z>, rr = <r, r>, bb = ||Pm g||^2, pAp = sigma = <q, E q - mean>, aux = mean(E q),
+// cz = mean(D^-1 r).  Every kernel returns at once when st->done.  Each reduction is a
+// fixed per-block tree plus a fixed-order sum of the block partials by the last block.
+
+// Sums of w, q w and q; the last block forms aux = mean(w), sigma = <q, w> - aux sum(q)
+// (= <q, w - aux>), and alpha = rho / sigma (breakdown when sigma <= 0).
+__global__ void k_pcg_psig(const double* __restrict__ q, const double* __restrict__ w, int64_t n, PcgState* st,
+                           double* partial) {
+  __shared__ double s[kRedThreads];
+  __shared__ int sdone;
+  if (threadIdx.x == 0) sdone = st->done;
+  __syncthreads();
+  if (sdone) return;
+  double aw = 0.0, aqw = 0.0, aq = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
+    const double wv = w[i], qv = q[i];
+    aw += wv;
+    aqw += qv * wv;
+    aq += qv;
+  }
+  const double tw = block_sum(aw, s), tqw = block_sum(aqw, s), tq = block_sum(aq, s);
+  if (threadIdx.x == 0) {
+    partial[3 * blockIdx.x] = tw;
+    partial[3 * blockIdx.x + 1] = tqw;
+    partial[3 * blockIdx.x + 2] = tq;
+  }
+  if (last_block(&st->cnt[0])) {
+    double bw = 0.0, bqw = 0.0, bq = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kRedThreads) {
+      bw += __ldcg(partial + 3 * b);
+      bqw += __ldcg(partial + 3 * b + 1);
+      bq += __ldcg(partial + 3 * b + 2);
+    }
+    const double sw = block_sum(bw, s), sqw = block_sum(bqw, s), sq = block_sum(bq, s);
+    if (threadIdx.x == 0) {
+      const double cw = sw / (double)n, sigma = sqw - cw * sq;
+      st->aux = cw;
+      st->pAp = sigma;
+      if (!(sigma > 0.0)) {
+        st->done = 1;
+        st->status = 5;  // SEM_ERR_BREAKDOWN
+      } else {
+        st->alpha = st->rho / sigma;
+      }
+      st->cnt[0] = 0;
+    }
+  }
+}
+
+// x += alpha q; r -= alpha (w - aux); JAC: z = dinv r with its sum, <r, z> and sum(r).
+// The last block forms rr, rho_new = <r, z - cz> (JAC) or rr, and applies the tests:
+// rr <= tol2 bb (MIXED: gamma2 tol2 bb) pauses for the true residual (ru = 1); MIXED
+// also pauses when rr <= delta2 rr_max at least `gap` iterations after the last
+// replacement; maxit ends the run; otherwise beta = rho_new / rho.
+template <bool JAC, bool MIXED>
+__global__ void k_pcg_pupd(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ q,
+                           const double* __restrict__ w, const double* __restrict__ dinv, double* __restrict__ z,
+                           int64_t n, PcgState* st, double* partial, double gamma2, int gap) {
+  __shared__ double s[kRedThreads];
+  __shared__ int sdone;
+  __shared__ double salpha, scw;
+  if (threadIdx.x == 0) {
+    sdone = st->done;
+    salpha = st->alpha;
+    scw = st->aux;
+  }
+  __syncthreads();
+  if (sdone) return;
+  const double alpha = salpha, cw = scw;
+  double arr = 0.0, az = 0.0, arz = 0.0, ar = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
+    x[i] += alpha * q[i];
+    const double v = r[i] - alpha * (w[i] - cw);
+    r[i] = v;
+    arr += v * v;
+    if (JAC) {
+      const double zv = dinv[i] * v;
+      z[i] = zv;
+      az += zv;
+      arz += v * zv;
+      ar += v;
+    }
+  }
+  const double t0 = block_sum(arr, s);
+  double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+  if (JAC) {
+    t1 = block_sum(az, s);
+    t2 = block_sum(arz, s);
+    t3 = block_sum(ar, s);
+  }
+  if (threadIdx.x == 0) {
+    partial[4 * blockIdx.x] = t0;
+    partial[4 * blockIdx.x + 1] = t1;
+    partial[4 * blockIdx.x + 2] = t2;
+    partial[4 * blockIdx.x + 3] = t3;
+  }
+  if (last_block(&st->cnt[1])) {
+    double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kRedThreads) {
+      b0 += __ldcg(partial + 4 * b);
+      b1 += __ldcg(partial + 4 * b + 1);
+      b2 += __ldcg(partial + 4 * b + 2);
+      b3 += __ldcg(partial + 4 * b + 3);
+    }
+    const double rr = block_sum(b0, s);
+    double sz = 0.0, srz = 0.0, sr = 0.0;
+    if (JAC) {
+      sz = block_sum(b1, s);
+      srz = block_sum(b2, s);
+      sr = block_sum(b3, s);
+    }
+    if (threadIdx.x == 0) {
+      const double cz = JAC ? sz / (double)n : 0.0;
+      const double rho_new = JAC ? srz - cz * sr : rr;
+      st->iter += 1;
+      st->rr = rr;
+      st->cz = cz;
+      if (rr != rr || rho_new != rho_new) {
+        st->done = 1;
+        st->status = 5;
+      } else if (rr <= (MIXED ? gamma2 : 1.0) * st->tol2 * st->bb) {
+        st->done = 1;
+        st->ru = 1;  // the host checks the true residual
+      } else if (MIXED && rr <= st->delta2 * st->rr_max && st->iter - st->last >= gap) {
+        st->done = 1;
+        st->ru = 1;  // reliable update
+      } else if (st->iter >= st->maxit) {
+        st->done = 1;
+        st->status = 4;  // SEM_ERR_NOT_CONVERGED
+      } else {
+        if (rr > st->rr_max) st->rr_max = rr;
+        st->beta = rho_new / st->rho;
+        st->rho = rho_new;
+      }
+      st->cnt[1] = 0;
+    }
+  }
+}
+
+// q = (zd - cz) + beta q (zd = z with Jacobi, r without, where cz = 0)
+__global__ void k_pcg_pdir(double* __restrict__ q, const double* __restrict__ zd, int64_t n,
+                           const PcgState* __restrict__ st) {
+  if (st->done) return;
+  const double beta = st->beta, cz = st->cz;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    q[i] = (zd[i] - cz) + beta * q[i];
+}
+
 // FP32 copies for the mixed-precision pressure solve
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -469,6 +618,34 @@ cudaError_t launch_presidual(const double* g, double cg, const double* w, double
   k_psum_finish<<<1, kRedThreads, 0, s>>>(partial, kPressureRedBlocks, out);
   return cudaGetLastError();
 }
+
+cudaError_t launch_pcg_psig(const double* q, const double* w, int64_t n, PcgState* st, double* partial,
+                            cudaStream_t s) {
+  k_pcg_psig<<<kPressureRedBlocks, kRedThreads, 0, s>>>(q, w, n, st, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_pupd(bool jac, bool mixed, double* x, double* r, const double* q, const double* w,
+                            const double* dinv, double* z, int64_t n, PcgState* st, double* partial, double gamma2,
+                            int gap, cudaStream_t s) {
+  if (jac && mixed)
+    k_pcg_pupd<true, true><<<kPressureRedBlocks, kRedThreads, 0, s>>>(x, r, q, w, dinv, z, n, st, partial, gamma2, gap);
+  else if (jac)
+    k_pcg_pupd<true, false><<<kPressureRedBlocks, kRedThreads, 0, s>>>(x, r, q, w, dinv, z, n, st, partial, gamma2, gap);
+  else if (mixed)
+    k_pcg_pupd<false, true><<<kPressureRedBlocks, kRedThreads, 0, s>>>(x, r, q, w, dinv, z, n, st, partial, gamma2, gap);
+  else
+    k_pcg_pupd<false, false><<<kPressureRedBlocks, kRedThreads, 0, s>>>(x, r, q, w, dinv, z, n, st, partial, gamma2,
+                                                                       gap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_pdir(double* q, const double* zd, int64_t n, const PcgState* st, cudaStream_t s) {
+  k_pcg_pdir<<<kPressureRedBlocks, kRedThreads, 0, s>>>(q, zd, n, st);
+  return cudaGetLastError();
+}
+
+int pressure_partials() { return 4 * kPressureRedBlocks; }
 
 cudaError_t launch_presidual_keep(const double* g, double cg, const double* w, double cw, double* r, int64_t n,
                                   double* partial, double* out, cudaStream_t s) {

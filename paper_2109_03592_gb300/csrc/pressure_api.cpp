@@ -9,6 +9,7 @@
 // synchronises.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -268,33 +269,70 @@ constexpr int kPressureRuGap = 8;  // iterations between residual replacements o
 namespace sem {
 namespace {
 
-// Mixed precision for Eq. 5: CG recurrences in FP64 on the pressure values
-// with the operator applied in FP32 (E p rounded to FP32 factors and fields,
-// the costly part: the FP64 operator runs on GB300's narrow FP64 pipe), and
-// reliable updates: when the recurrence residual has dropped by delta since the
-// last replacement (at least 8 iterations later), or below 0.2 tol, the true
-// residual Pm (g - E x) is formed with the FP64 operator and replaces it, and
-// CG continues with its direction.  The solve stops when the true residual
-// meets tol.
-sem_status pressure_solve_mixed(const sem_mesh* m, const double* g_dev, double* p_dev, double tol, int maxit,
-                                double delta, bool jac, sem_solve_result* result, cudaStream_t s) {
-  SEM_TRY_STATUS(ensure_pressure32(m, s));
-  if (jac) SEM_TRY_STATUS(ensure_pdiag(m, s));
+// CG for Eq. 5 on the mean-free pressure space, Pm E Pm p = Pm g with
+// Pm = I - 1 1^T / n_p, from p = 0, Jacobi preconditioned (z = Pm(r / diag E))
+// or plain.  The iteration runs on the device: its scalars live in a PcgState
+// and kChunk iterations are one CUDA graph (E, then k_pcg_psig, k_pcg_pupd and
+// k_pcg_pdir), so the host reads the state once per chunk instead of after
+// every reduction.  When the recurrence residual meets tol the run pauses and
+// the host forms the true residual Pm(g - E p) with the FP64 operator: done if
+// it meets tol too; otherwise the FP64 solve restarts from p (at most
+// kPressureMaxRestarts times).
+// mixed: E applied in FP32 (rounded factors and fields; the FP64 operator is
+// bound by GB300's narrow FP64 pipe), FP64 recurrences, and reliable updates:
+// the run also pauses when the recurrence residual has dropped by delta since
+// the last replacement (at least kPressureRuGap iterations later); the true
+// residual then replaces r and CG continues with its direction.  The solve
+// stops when the true residual meets tol (the recurrence test is 0.2 tol).
+sem_status pressure_cg(const sem_mesh* m, const double* g_dev, double* p_dev, double tol, int maxit, bool mixed,
+                       double delta, bool jac, sem_solve_result* result, cudaStream_t us) {
+  SEM_TRY_STATUS(ensure_pressure(m, us));
+  if (mixed) SEM_TRY_STATUS(ensure_pressure32(m, us));
+  if (jac) SEM_TRY_STATUS(ensure_pdiag(m, us));
+  // the solve runs on a stream of its own (graph capture needs a non-legacy
+  // stream), ordered after the caller's
+  cudaStream_t s = nullptr;
+  cudaEvent_t ein = nullptr;
+  SEM_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  struct Str {
+    cudaStream_t* s;
+    cudaEvent_t* e;
+    ~Str() {
+      if (*s) {
+        cudaStreamSynchronize(*s);
+        cudaStreamDestroy(*s);
+      }
+      if (*e) cudaEventDestroy(*e);
+    }
+  } sguard{&s, &ein};
+  SEM_CUDA(cudaEventCreateWithFlags(&ein, cudaEventDisableTiming));
+  SEM_CUDA(cudaEventRecord(ein, us));
+  SEM_CUDA(cudaStreamWaitEvent(s, ein, 0));
+  constexpr int kChunk = 8;
+  constexpr double kGamma = 0.2;
   const int64_t mm = m->N - 1, np = m->E * mm * mm * mm, nl = m->n_local;
-  const int nb = pressure_red_blocks();
+  const int nb = std::max(pressure_red_blocks() + 1, pressure_partials());
+  // scratch: r, q, w, z [np]; velocity work [3 n_local]; partials; one sum; the state
   double* buf = nullptr;
   float* buf32 = nullptr;
-  SEM_CUDA(cudaMalloc((void**)&buf, (4 * (size_t)np + 3 * (size_t)nl + nb + 1) * sizeof(double)));
-  cudaError_t e0 = cudaMalloc((void**)&buf32, (2 * (size_t)np + 3 * (size_t)nl) * sizeof(float));
+  PcgState* sth = nullptr;
+  const size_t count = 4 * (size_t)np + 3 * (size_t)nl + nb + 1 + (sizeof(PcgState) + 7) / 8;
+  SEM_CUDA(cudaMalloc((void**)&buf, count * sizeof(double)));
+  cudaGraphExec_t exec = nullptr;
   struct Free {
     double* b;
-    float* f;
+    float** f;
+    PcgState** h;
+    cudaGraphExec_t* x;
     ~Free() {
-      if (b) cudaFree(b);
-      if (f) cudaFree(f);
+      if (*x) cudaGraphExecDestroy(*x);
+      cudaFree(b);
+      if (*f) cudaFree(*f);
+      if (*h) cudaFreeHost(*h);
     }
-  } guard{buf, buf32};
-  if (e0 != cudaSuccess) return cuda_fail(e0, "cudaMalloc");
+  } guard{buf, &buf32, &sth, &exec};
+  if (mixed) SEM_CUDA(cudaMalloc((void**)&buf32, (2 * (size_t)np + 3 * (size_t)nl) * sizeof(float)));
+  SEM_CUDA(cudaMallocHost((void**)&sth, sizeof(PcgState)));
   double* r = buf;
   double* q = r + np;
   double* w = q + np;
@@ -302,36 +340,36 @@ sem_status pressure_solve_mixed(const sem_mesh* m, const double* g_dev, double* 
   double* work = z + np;
   double* partial = work + 3 * nl;
   double* sum_d = partial + nb;
+  PcgState* st = reinterpret_cast<PcgState*>(sum_d + 1);
   float* q32 = buf32;
-  float* w32 = q32 + np;
-  float* work32 = w32 + np;
+  float* w32 = mixed ? q32 + np : nullptr;
+  float* work32 = mixed ? w32 + np : nullptr;
   const GsDev g = gs_dev(m);
   auto read = [&](double& v) -> sem_status {
     SEM_CUDA(cudaMemcpyAsync(&v, sum_d, sizeof(double), cudaMemcpyDeviceToHost, s));
     SEM_CUDA(cudaStreamSynchronize(s));
     return SEM_OK;
   };
-  cudaEvent_t ev0, ev1;
-  SEM_CUDA(cudaEventCreate(&ev0));
-  SEM_CUDA(cudaEventCreate(&ev1));
-  struct Ev {
-    cudaEvent_t a, b;
-    ~Ev() {
-      cudaEventDestroy(a);
-      cudaEventDestroy(b);
-    }
-  } evguard{ev0, ev1};
-  SEM_CUDA(cudaEventRecord(ev0, s));
+  auto put = [&]() -> sem_status {
+    SEM_CUDA(cudaMemcpyAsync(st, sth, sizeof(PcgState), cudaMemcpyHostToDevice, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    return SEM_OK;
+  };
+  auto get = [&]() -> sem_status {
+    SEM_CUDA(cudaMemcpyAsync(sth, st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    return SEM_OK;
+  };
   uint64_t launches = 0;
-  double gsum = 0.0, rho = 0.0;
-  SEM_CUDA(launch_pdot(g_dev, nullptr, np, partial, sum_d, s));
-  launches += 2;
-  SEM_TRY_STATUS(read(gsum));
-  SEM_CUDA(launch_pstart(g_dev, gsum / (double)np, r, q, p_dev, np, partial, sum_d, s));
-  launches += 2;
-  SEM_TRY_STATUS(read(rho));
-  const double gnorm = std::sqrt(rho);
-  // z = Pm (dinv r) and rho = <r, z> (Jacobi); without it z is r itself
+  // out = E v in FP64: weak gradient, QQ^T with mask on each component, inverse mass, weak divergence
+  auto apply_E = [&](const double* v, double* out) -> sem_status {
+    SEM_CUDA(launch_pgrad<double>(v, m->Fgl, m->Igl, m->DIgl, m->n, (int)mm, m->E, work, nl, s));
+    for (int a = 0; a < 3; ++a) SEM_CUDA(launch_gs<double>(work + a * nl, g, 1, nullptr, s));
+    SEM_CUDA(launch_pdiv<double>(work, m->dB, nullptr, m->Fgl, m->Igl, m->DIgl, m->n, (int)mm, m->E, out, nl, s));
+    launches += 5;
+    return SEM_OK;
+  };
+  // z = Pm (dinv r) in place and <r, z>, host-synchronous (start and after replacements)
   auto precondition = [&](double& rz) -> sem_status {
     double zs = 0.0;
     SEM_CUDA(launch_pscale(r, m->pdinv, z, np, partial, sum_d, s));
@@ -342,83 +380,129 @@ sem_status pressure_solve_mixed(const sem_mesh* m, const double* g_dev, double* 
     return SEM_OK;
   };
   const double* zdir = jac ? z : r;
-  const double rr0 = rho;  // <r, r>; rho becomes <r, z>
-  if (jac && gnorm > 0.0) {
-    SEM_TRY_STATUS(precondition(rho));
-    SEM_CUDA(launch_pdir(q, z, 0.0, np, s));
-    launches += 1;
-  }
-  constexpr double kGamma = 0.2;
-  int it = 0, outer = 0, status = SEM_OK;
+
+  cudaEvent_t e0, e1;
+  SEM_CUDA(cudaEventCreate(&e0));
+  SEM_CUDA(cudaEventCreate(&e1));
+  struct Ev {
+    cudaEvent_t a, b;
+    ~Ev() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } evguard{e0, e1};
+  SEM_CUDA(cudaEventRecord(e0, s));
+  // mean of g, then r = q = g - mean, x = 0, <r, r>
+  double gsum = 0.0, rr0 = 0.0;
+  SEM_CUDA(launch_pdot(g_dev, nullptr, np, partial, sum_d, s));
+  SEM_TRY_STATUS(read(gsum));
+  SEM_CUDA(launch_pstart(g_dev, gsum / (double)np, r, q, p_dev, np, partial, sum_d, s));
+  SEM_TRY_STATUS(read(rr0));
+  launches += 4;
+  const double gnorm = std::sqrt(rr0);
+  int status = SEM_OK, outer = 0, restarts = 0, iters = 0;
   double rel = 0.0;
   if (gnorm > 0.0) {
+    double rho = rr0;
+    if (jac) {
+      SEM_TRY_STATUS(precondition(rho));
+      SEM_CUDA(launch_pdir(q, z, 0.0, np, s));
+      launches += 1;
+    }
+    std::memset(sth, 0, sizeof(PcgState));
+    sth->rho = rho;
+    sth->rr = rr0;
+    sth->rr_max = rr0;
+    sth->bb = rr0;
+    sth->tol2 = tol * tol;
+    sth->delta2 = mixed ? delta * delta : 0.0;
+    sth->maxit = maxit;
+    SEM_TRY_STATUS(put());
+    // one iteration, kChunk times in a graph
+    auto iteration = [&]() -> sem_status {
+      if (mixed) {
+        launch_to_f32(q, q32, np, s);
+        SEM_TRY_STATUS(apply_E32(m, q32, w32, work32, s));
+        launch_to_f64(w32, w, np, s);
+      } else {
+        SEM_TRY_STATUS(apply_E(q, w));
+      }
+      SEM_CUDA(launch_pcg_psig(q, w, np, st, partial, s));
+      SEM_CUDA(launch_pcg_pupd(jac, mixed, p_dev, r, q, w, m->pdinv, z, np, st, partial, kGamma * kGamma,
+                               kPressureRuGap, s));
+      SEM_CUDA(launch_pcg_pdir(q, zdir, np, st, s));
+      return SEM_OK;
+    };
+    const int per_iter = mixed ? 10 : 8;
+    {
+      cudaGraph_t graph = nullptr;
+      SEM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      sem_status cst = SEM_OK;
+      for (int k = 0; k < kChunk && cst == SEM_OK; ++k) cst = iteration();
+      cudaError_t ce = cudaStreamEndCapture(s, &graph);
+      if (cst != SEM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return cst;
+      }
+      SEM_CUDA(ce);
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      SEM_CUDA(ce);
+    }
     status = SEM_ERR_NOT_CONVERGED;
     rel = 1.0;
-    double rr_max = rr0;
-    int last = 0;
-    for (it = 1; it <= maxit; ++it) {
-      // w = E q with the FP32 operator, then w -= mean(w) and sigma = <q, w> in FP64
-      launch_to_f32(q, q32, np, s);
-      SEM_TRY_STATUS(apply_E32(m, q32, w32, work32, s));
-      launch_to_f64(w32, w, np, s);
-      double wsum = 0.0, sigma = 0.0, rho_new = 0.0;
-      SEM_CUDA(launch_pdot(w, nullptr, np, partial, sum_d, s));
-      SEM_TRY_STATUS(read(wsum));
-      SEM_CUDA(launch_pshift_dot(w, q, wsum / (double)np, np, partial, sum_d, s));
-      SEM_TRY_STATUS(read(sigma));
-      launches += 6;
-      if (!(sigma > 0.0)) {
-        status = SEM_ERR_BREAKDOWN;
+    for (;;) {
+      SEM_CUDA(cudaGraphLaunch(exec, s));
+      launches += (uint64_t)kChunk * per_iter;
+      SEM_TRY_STATUS(get());
+      if (!sth->done) continue;
+      iters = sth->iter;
+      rel = std::sqrt(sth->rr) / gnorm;
+      if (!sth->ru) {  // breakdown or the iteration cap
+        status = sth->status;
         break;
       }
-      const double alpha = rho / sigma;
-      double rr_new = 0.0;
-      SEM_CUDA(launch_pupdate(p_dev, r, q, w, alpha, np, partial, sum_d, s));
-      launches += 2;
-      SEM_TRY_STATUS(read(rr_new));
-      rel = std::sqrt(rr_new) / gnorm;
-      const bool converged = std::sqrt(rr_new) <= kGamma * tol * gnorm;
-      if (converged || (rr_new <= delta * delta * rr_max && it - last >= kPressureRuGap)) {
-        // replace r by the true residual Pm (g - E x) with the FP64 operator
-        SEM_CUDA(launch_pgrad<double>(p_dev, m->Fgl, m->Igl, m->DIgl, m->n, (int)mm, m->E, work, nl, s));
-        for (int a = 0; a < 3; ++a) SEM_CUDA(launch_gs<double>(work + a * nl, g, 1, nullptr, s));
-        SEM_CUDA(launch_pdiv<double>(work, m->dB, nullptr, m->Fgl, m->Igl, m->DIgl, m->n, (int)mm, m->E, w, nl, s));
-        double xs = 0.0, rho_t = 0.0;
-        SEM_CUDA(launch_pdot(w, nullptr, np, partial, sum_d, s));
-        SEM_TRY_STATUS(read(xs));
-        SEM_CUDA(launch_presidual_keep(g_dev, gsum / (double)np, w, xs / (double)np, r, np, partial, sum_d, s));
-        SEM_TRY_STATUS(read(rho_t));
-        launches += 9;
-        ++outer;
-        rel = std::sqrt(rho_t) / gnorm;
-        if (std::sqrt(rho_t) <= tol * gnorm) {
-          status = SEM_OK;
-          break;
-        }
-        rr_max = rho_t;
-        last = it;
-        if (jac) SEM_TRY_STATUS(precondition(rho_new));
-        else rho_new = rho_t;
-        SEM_CUDA(launch_pdir(q, zdir, rho_new / rho, np, s));
-        launches += 1;
-        rho = rho_new;
-        continue;
+      // the true residual Pm (g - E x) with the FP64 operator
+      double xs = 0.0, rr_t = 0.0;
+      SEM_TRY_STATUS(apply_E(p_dev, w));
+      SEM_CUDA(launch_pdot(w, nullptr, np, partial, sum_d, s));
+      SEM_TRY_STATUS(read(xs));
+      SEM_CUDA(launch_presidual_keep(g_dev, gsum / (double)np, w, xs / (double)np, r, np, partial, sum_d, s));
+      SEM_TRY_STATUS(read(rr_t));
+      launches += 4;
+      rel = std::sqrt(rr_t) / gnorm;
+      if (std::sqrt(rr_t) <= tol * gnorm) {
+        status = SEM_OK;
+        break;
       }
-      if (rr_new > rr_max) rr_max = rr_new;
+      if (sth->iter >= maxit) break;
+      double rho_new = rr_t;
       if (jac) SEM_TRY_STATUS(precondition(rho_new));
-      else rho_new = rr_new;
-      SEM_CUDA(launch_pdir(q, zdir, rho_new / rho, np, s));
+      if (mixed) {  // replacement: CG keeps its direction
+        ++outer;
+        SEM_CUDA(launch_pdir(q, zdir, rho_new / sth->rho, np, s));
+        sth->rr_max = rr_t;
+        sth->last = sth->iter;
+      } else {  // restart from x with the true residual
+        if (restarts == kPressureMaxRestarts) break;
+        ++restarts;
+        SEM_CUDA(launch_pdir(q, zdir, 0.0, np, s));
+      }
       launches += 1;
-      rho = rho_new;
+      sth->rho = rho_new;
+      sth->rr = rr_t;
+      sth->done = 0;
+      sth->ru = 0;
+      sth->status = 0;
+      SEM_TRY_STATUS(put());
     }
-    if (it > maxit) it = maxit;
   }
-  SEM_CUDA(cudaEventRecord(ev1, s));
-  SEM_CUDA(cudaEventSynchronize(ev1));
+  SEM_CUDA(cudaEventRecord(e1, s));
+  SEM_CUDA(cudaEventSynchronize(e1));
   float ms = 0.f;
-  SEM_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+  SEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
   count_launches(launches);
-  result->iters = it;
+  result->iters = iters;
   result->outer_iters = outer;
   result->rel_res = rel;
   result->ms = ms;
@@ -542,13 +626,6 @@ sem_status sem_pressure_apply_f32(const sem_mesh* m, const float* p_dev, float* 
   return apply_E32(m, p_dev, q_dev, work_dev, s);
 }
 
-// CG on the mean-free pressure space: Pm E Pm p = Pm g, Pm = I - 1 1^T / n_p.
-// When the recurrence residual meets the tolerance, the true residual
-// Pm (g - E p) is formed; CG restarts from p with it (at most
-// kPressureMaxRestarts times) unless it meets the tolerance as well.
-// Host-driven: each iteration applies E (five launches), then three
-// deterministic reductions whose sums the host reads back to form the mean of
-// E p, alpha and beta.
 sem_status sem_pressure_diag(const sem_mesh* m, double* d_dev, void* stream) {
   sem_status st = check_mesh(m, "sem_pressure_diag");
   if (st != SEM_OK) return st;
@@ -582,155 +659,13 @@ sem_status sem_pressure_solve(const sem_mesh* m, const double* g_dev, double* p_
     return SEM_ERR_INVALID;
   }
   const bool jac = opts->precond != SEM_PRECOND_NONE;
-  if (opts->prec == SEM_MIXED)
-    return pressure_solve_mixed(m, g_dev, p_dev, tol, maxit, opts->delta > 0.0 ? opts->delta : 0.1, jac, result, s);
-  if (opts->prec != SEM_FP64) {
+  if (opts->prec != SEM_FP64 && opts->prec != SEM_MIXED) {
     set_error("sem_pressure_solve: prec must be SEM_FP64 or SEM_MIXED");
     return SEM_ERR_INVALID;
   }
-  st = ensure_pressure(m, s);
-  if (st != SEM_OK) return st;
-  if (jac) {
-    st = ensure_pdiag(m, s);
-    if (st != SEM_OK) return st;
-  }
-  const int64_t mm = m->N - 1, np = m->E * mm * mm * mm;
-  const int nb = pressure_red_blocks();
-  // scratch: r, q (direction), w, z [np]; velocity work [3 n_local]; partials; one sum
-  double* buf = nullptr;
-  const size_t count = 4 * (size_t)np + 3 * (size_t)m->n_local + nb + 1;
-  SEM_CUDA(cudaMalloc((void**)&buf, count * sizeof(double)));
-  struct Free {
-    double* b;
-    ~Free() { cudaFree(b); }
-  } guard{buf};
-  double* r = buf;
-  double* q = r + np;
-  double* w = q + np;
-  double* z = w + np;
-  double* work = z + np;
-  double* partial = work + 3 * m->n_local;
-  double* sum_d = partial + nb;
-  const GsDev g = gs_dev(m);
-  auto read = [&](double& v) -> sem_status {
-    SEM_CUDA(cudaMemcpyAsync(&v, sum_d, sizeof(double), cudaMemcpyDeviceToHost, s));
-    SEM_CUDA(cudaStreamSynchronize(s));
-    return SEM_OK;
-  };
-  cudaEvent_t e0, e1;
-  SEM_CUDA(cudaEventCreate(&e0));
-  SEM_CUDA(cudaEventCreate(&e1));
-  struct Ev {
-    cudaEvent_t a, b;
-    ~Ev() {
-      cudaEventDestroy(a);
-      cudaEventDestroy(b);
-    }
-  } evguard{e0, e1};
-  SEM_CUDA(cudaEventRecord(e0, s));
-  uint64_t launches = 0;
-  // mean of g, then r = q = g - mean, x = 0, rho = <r, r>
-  double gsum = 0.0, rho = 0.0;
-  SEM_CUDA(launch_pdot(g_dev, nullptr, np, partial, sum_d, s));
-  launches += 2;
-  SEM_TRY_STATUS(read(gsum));
-  SEM_CUDA(launch_pstart(g_dev, gsum / (double)np, r, q, p_dev, np, partial, sum_d, s));
-  launches += 2;
-  SEM_TRY_STATUS(read(rho));
-  const double gnorm = std::sqrt(rho);
-  // z = Pm (dinv r) and rho = <r, z> (Jacobi); without it z is r itself
-  auto precondition = [&](double& rz) -> sem_status {
-    double zs = 0.0;
-    SEM_CUDA(launch_pscale(r, m->pdinv, z, np, partial, sum_d, s));
-    SEM_TRY_STATUS(read(zs));
-    SEM_CUDA(launch_pshift_dot(z, r, zs / (double)np, np, partial, sum_d, s));
-    SEM_TRY_STATUS(read(rz));
-    launches += 4;
-    return SEM_OK;
-  };
-  const double* zdir = jac ? z : r;
-  if (jac && gnorm > 0.0) {
-    SEM_TRY_STATUS(precondition(rho));
-    SEM_CUDA(launch_pdir(q, z, 0.0, np, s));
-    launches += 1;
-  }
-  // out = E v (weak gradient, QQ^T with mask on each component, inverse mass, weak divergence)
-  auto apply_E = [&](const double* v, double* out) -> sem_status {
-    SEM_CUDA(launch_pgrad<double>(v, m->Fgl, m->Igl, m->DIgl, m->n, (int)mm, m->E, work, m->n_local, s));
-    for (int a = 0; a < 3; ++a) SEM_CUDA(launch_gs<double>(work + a * m->n_local, g, 1, nullptr, s));
-    SEM_CUDA(launch_pdiv<double>(work, m->dB, nullptr, m->Fgl, m->Igl, m->DIgl, m->n, (int)mm, m->E, out, m->n_local, s));
-    launches += 5;
-    return SEM_OK;
-  };
-  int it = 0, restarts = 0;
-  int status = SEM_OK;
-  double rel = 0.0;
-  if (gnorm > 0.0) {
-    status = SEM_ERR_NOT_CONVERGED;
-    rel = 1.0;
-    for (it = 1; it <= maxit; ++it) {
-      // w = E q, then w -= mean(w) and sigma = <q, w>
-      SEM_TRY_STATUS(apply_E(q, w));
-      double wsum = 0.0, sigma = 0.0, rho_new = 0.0;
-      SEM_CUDA(launch_pdot(w, nullptr, np, partial, sum_d, s));
-      SEM_TRY_STATUS(read(wsum));
-      SEM_CUDA(launch_pshift_dot(w, q, wsum / (double)np, np, partial, sum_d, s));
-      SEM_TRY_STATUS(read(sigma));
-      launches += 4;
-      if (!(sigma > 0.0)) {
-        status = SEM_ERR_BREAKDOWN;
-        break;
-      }
-      const double alpha = rho / sigma;
-      double rr_new = 0.0;
-      SEM_CUDA(launch_pupdate(p_dev, r, q, w, alpha, np, partial, sum_d, s));
-      launches += 2;
-      SEM_TRY_STATUS(read(rr_new));
-      rel = std::sqrt(rr_new) / gnorm;
-      if (std::sqrt(rr_new) <= tol * gnorm) {
-        // the true residual Pm (g - E x); restart from x if the recurrence drifted
-        SEM_TRY_STATUS(apply_E(p_dev, w));
-        double xs = 0.0, rr_t = 0.0;
-        SEM_CUDA(launch_pdot(w, nullptr, np, partial, sum_d, s));
-        SEM_TRY_STATUS(read(xs));
-        SEM_CUDA(launch_presidual(g_dev, gsum / (double)np, w, xs / (double)np, r, q, np, partial, sum_d, s));
-        launches += 4;
-        SEM_TRY_STATUS(read(rr_t));
-        rel = std::sqrt(rr_t) / gnorm;
-        if (std::sqrt(rr_t) <= tol * gnorm) {
-          status = SEM_OK;
-          break;
-        }
-        if (restarts == kPressureMaxRestarts) break;
-        ++restarts;
-        // a steepest-descent restart: q = z
-        if (jac) {
-          SEM_TRY_STATUS(precondition(rho));
-          SEM_CUDA(launch_pdir(q, z, 0.0, np, s));
-          launches += 1;
-        } else {
-          rho = rr_t;  // q = r already
-        }
-        continue;
-      }
-      if (jac) SEM_TRY_STATUS(precondition(rho_new));
-      else rho_new = rr_new;
-      SEM_CUDA(launch_pdir(q, zdir, rho_new / rho, np, s));
-      launches += 1;
-      rho = rho_new;
-    }
-    if (it > maxit) it = maxit;
-  }
-  SEM_CUDA(cudaEventRecord(e1, s));
-  SEM_CUDA(cudaEventSynchronize(e1));
-  float ms = 0.f;
-  SEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-  count_launches(launches);
-  result->iters = it;
-  result->rel_res = rel;
-  result->ms = ms;
-  result->status = status;
-  return (sem_status)status;
+  SEM_CUDA(cudaSetDevice(m->device));
+  return pressure_cg(m, g_dev, p_dev, tol, maxit, opts->prec == SEM_MIXED, opts->delta > 0.0 ? opts->delta : 0.1, jac,
+                     result, s);
 }
 
 }  // extern "C"
