@@ -147,6 +147,16 @@ __global__ void __launch_bounds__(EPB* eo_threads_per_element<N>(), eo_min_block
     __syncthreads();
     if (sdone) return;
   }
+  // The CTA's G (hi and lo) into L2 while the forward contractions run: one
+  // bulk prefetch per array (a hint, nothing waits on it), so the G loads of
+  // the pointwise step hit L2 instead of waiting on DRAM.
+  if (tid == 0) {
+    const int64_t e0 = (int64_t)blockIdx.x * EPB;
+    const int64_t ne = min((int64_t)EPB, P.E - e0);
+    const uint32_t bytes = (uint32_t)(ne * 6 * n3 * sizeof(float));
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(P.Ghi + e0 * 6 * n3), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(P.Glo + e0 * 6 * n3), "r"(bytes) : "memory");
+  }
   // coefficient tables; h1 scales the forward ones
   if (P.h1 == 1.0) {
     for (int q = tid; q < 2 * h * h; q += blockDim.x) sC[q] = reinterpret_cast<const float4*>(P.eodf)[q];

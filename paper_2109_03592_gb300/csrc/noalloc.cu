@@ -104,7 +104,7 @@ extern "C" sem_status sem_pcg_solve_noalloc(const sem_mesh* m, const double* b_d
   {
     std::lock_guard<std::mutex> lk(mm->ws_mutex);
     var_native = m->ax_var[0];
-    var_df = m->ax_var[2];
+    var_df = m->ax_var_dff;  // the fused form runs here
     use_df = m->fp64_df;
   }
 

@@ -141,6 +141,7 @@ struct sem_mesh {
   // variant index per precision (0 FP64 native, 1 FP32, 2 FP64 double-float)
   // and whether FP64 requests run the double-float kernel.
   int ax_var[3] = {0, 0, 0};
+  int ax_var_dff = 0;           // double-float variant of the fused form (the FP64 CG's operator)
   int fp64_df = 0;
   float ax_ms[3][4] = {{0}};
 
