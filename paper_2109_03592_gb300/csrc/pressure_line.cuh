@@ -54,6 +54,13 @@ __device__ __forceinline__ void row_load(const double* p, double (&row)[L]) {
     asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(row[c]), "=d"(row[c + 1]) : "r"(a + 8u * c));
 }
 
+// A hint to bring [p, p + bytes) into L2 (one bulk prefetch; nothing waits
+// on it).  Skipped unless the range is 16-byte aligned at both ends.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  if (((uintptr_t)p & 15u) || (bytes & 15u) || bytes == 0 || bytes >= (1ull << 31)) return;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"((uint32_t)bytes) : "memory");
+}
+
 template <typename T, int N>
 struct Shape {
   static constexpr int n = N + 1, m = N - 1, n2 = n * n, n3 = n2 * n, m2 = m * m, m3 = m2 * m;
@@ -111,6 +118,13 @@ __global__ void __launch_bounds__(kThreads) k_pdiv_line(const T* __restrict__ u,
   T* el = sm + S::mats;
   const int64_t e0 = (int64_t)blockIdx.x * EPB;
   const int ne = (int)min((int64_t)EPB, E - e0);
+  // every F block and the later directions' velocity blocks are read only
+  // after contractions: into L2 now
+  if (threadIdx.x == 0) {
+    prefetch_l2(F + e0 * 9 * m3, sizeof(T) * (size_t)ne * 9 * m3);
+    prefetch_l2(u + n_local + e0 * n3, sizeof(T) * (size_t)ne * n3);
+    prefetch_l2(u + 2 * n_local + e0 * n3, sizeof(T) * (size_t)ne * n3);
+  }
   constexpr int np1 = S::np1, mp1 = S::mp1;
   auto V = [&](int le) { return el + le * S::elem; };
   auto XD = [&](int le) { return V(le) + n2 * np1; };
@@ -234,6 +248,7 @@ __global__ void __launch_bounds__(kThreads) k_pgrad_line(const T* __restrict__ p
   T* el = sm + S::mats;
   const int64_t e0 = (int64_t)blockIdx.x * EPB;
   const int ne = (int)min((int64_t)EPB, E - e0);
+  if (threadIdx.x == 0) prefetch_l2(F + e0 * 9 * m3, sizeof(T) * (size_t)ne * 9 * m3);
   // per element: U [n^2][n + 1], A0, A1 [n^2][m + 1], S0, S1, S2 [n m^2], P [m^3]
   constexpr int np1 = S::np1, mp1 = S::mp1;
   auto U = [&](int le) { return el + le * S::elem; };
