@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_ax(const AxParams<T> 
 #pragma unroll
       for (int k = 0; k < n; ++k) {
         const T v = P.z[base + k * n2] + beta * P.p[base + k * n2];
-        P.p[base + k * n2] = v;
+        (P.pout ? P.pout : P.p)[base + k * n2] = v;
         ru[k] = v;
       }
     } else {

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_ax_tma(const AxParams
         if (FUSED) {
           v += beta * st[EPB * n3 + le * n3 + k * n2 + ij];
           su[k * n2 + ij] = v;
-          P.p[base + k * n2] = v;
+          (P.pout ? P.pout : P.p)[base + k * n2] = v;
         }
         ru[k] = v;
       }

@@ -43,6 +43,7 @@ struct AxParams {
   PcgState* st;
   double* partial;   // [gridDim.x]
   int* err;          // device error word (bounded-wait timeouts of the bulk-copy kernels)
+  T* pout;           // fused: the new direction goes here (nullptr: over p)
 };
 
 // Double-float (FP32 pair) FP64-accurate variant: G = Ghi + Glo, D = Dhi + Dlo,
@@ -107,12 +108,18 @@ struct VecParams {
   int64_t n;
   PcgState* st;
   double* partial;  // [3 * grid]
+  const T* p2;      // the previous direction (x updated with two directions, see k_pcg_update)
 };
 int vec_grid();
 // ext = true: an external preconditioner (its kernels write z = M^{-1} r
 // between k_pcg_update and launch_pcg_rho; init and restart read that z).
+// xmode (FP32 CG, no external preconditioner): 0 x += alpha p; 1 x not
+// updated (alpha kept as alpha_prev, xpend set); 2 x += alpha_prev p2 + alpha p.
 template <typename T>
-cudaError_t launch_pcg_update(const VecParams<T>& p, cudaStream_t s, bool ext = false);
+cudaError_t launch_pcg_update(const VecParams<T>& p, cudaStream_t s, bool ext = false, int xmode = 0);
+// Completes a pair of x updates after a pause (k_pcg_update xmode 1 was the
+// last): x += alpha_prev p2, p = p2; clears xpend.
+cudaError_t launch_pcg_xflush(float* x, float* p, const float* p2, PcgState* st, int64_t n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pcg_init(const VecParams<T>& p, cudaStream_t s, bool ext = false);
 template <typename T>

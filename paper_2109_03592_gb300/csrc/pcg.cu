@@ -85,7 +85,12 @@ struct Vec16<double> {
 // EXT (a preconditioner applied by other kernels, e.g. overlapping Schwarz):
 // only x, r and <r, r> with the stop tests here; z = M^{-1} r and beta come
 // from the preconditioner's kernels and k_pcg_rho afterwards.
-template <typename T, bool EXT>
+// XM: how x is advanced.  0: x += alpha p.  1: not at all (the first of a
+// pair of iterations: alpha is kept in the state as alpha_prev and xpend
+// set).  2: x += alpha_prev p2 + alpha p (the second of the pair, p2 the
+// first's direction).  Pairing the x updates saves one read and one write of
+// x per two iterations; k_pcg_xflush completes a pair cut short by a pause.
+template <typename T, bool EXT, int XM>
 __global__ void __launch_bounds__(kVecThreads) k_pcg_update(const VecParams<T> P) {
   using Acc = typename AccOf<T>::type;
   using VT = Vec16<T>;
@@ -100,15 +105,28 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(const VecParams<T> P
   __syncthreads();
   if (sdone) return;
   const T alpha = (T)P.st->alpha;
+  const T alpha_prev = XM == 2 ? (T)P.st->alpha_prev : T(0);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // read by the next update, after this kernel
+    if (XM == 1) {
+      P.st->alpha_prev = P.st->alpha;
+      P.st->xpend = 1;
+    } else if (XM == 2) {
+      P.st->xpend = 0;
+    }
+  }
   Acc rz, rr;
   const int64_t nv = P.n / W;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   for (int64_t q = t0; q < nv; q += stride) {
-    const V pv = reinterpret_cast<const V*>(P.p)[q];
+    V pv, p2v, xv;
+    if (XM != 1) {
+      pv = reinterpret_cast<const V*>(P.p)[q];
+      xv = reinterpret_cast<const V*>(P.x)[q];
+    }
+    if (XM == 2) p2v = reinterpret_cast<const V*>(P.p2)[q];
     const V wv = reinterpret_cast<const V*>(P.w)[q];
     V rv = reinterpret_cast<const V*>(P.r)[q];
-    V xv = reinterpret_cast<const V*>(P.x)[q];
     V mv;
     if (!EXT) mv = reinterpret_cast<const V*>(P.minv)[q];
     const M wm = reinterpret_cast<const M*>(P.wm)[q];
@@ -116,7 +134,8 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(const VecParams<T> P
 #pragma unroll
     for (int k = 0; k < W; ++k) {
       const T rq = VT::get(rv, k) - alpha * VT::get(wv, k);
-      VT::set(xv, k, VT::get(xv, k) + alpha * VT::get(pv, k));
+      if (XM == 0) VT::set(xv, k, VT::get(xv, k) + alpha * VT::get(pv, k));
+      if (XM == 2) VT::set(xv, k, (VT::get(xv, k) + alpha_prev * VT::get(p2v, k)) + alpha * VT::get(pv, k));
       VT::set(rv, k, rq);
       const T im = sinv[VT::getm(wm, k) & 0x7f];
       if (!EXT) {
@@ -126,13 +145,14 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(const VecParams<T> P
       }
       rr.add(rq * rq * im);
     }
-    reinterpret_cast<V*>(P.x)[q] = xv;
+    if (XM != 1) reinterpret_cast<V*>(P.x)[q] = xv;
     reinterpret_cast<V*>(P.r)[q] = rv;
     if (!EXT) reinterpret_cast<V*>(P.z)[q] = zv;
   }
   for (int64_t q = nv * W + t0; q < P.n; q += stride) {  // tail (n not a multiple of W)
     const T rq = P.r[q] - alpha * P.w[q];
-    P.x[q] = P.x[q] + alpha * P.p[q];
+    if (XM == 0) P.x[q] = P.x[q] + alpha * P.p[q];
+    if (XM == 2) P.x[q] = (P.x[q] + alpha_prev * P.p2[q]) + alpha * P.p[q];
     P.r[q] = rq;
     const T im = sinv[P.wm[q] & 0x7f];
     if (!EXT) {
@@ -335,12 +355,38 @@ template cudaError_t launch_pcg_restart<float>(const VecParams<float>&, cudaStre
 template cudaError_t launch_pcg_restart<double>(const VecParams<double>&, cudaStream_t, bool);
 
 template <typename T>
-cudaError_t launch_pcg_update(const VecParams<T>& p, cudaStream_t s, bool ext) {
+cudaError_t launch_pcg_update(const VecParams<T>& p, cudaStream_t s, bool ext, int xmode) {
   if (ext)
-    k_pcg_update<T, true><<<kVecBlocks, kVecThreads, 0, s>>>(p);
+    k_pcg_update<T, true, 0><<<kVecBlocks, kVecThreads, 0, s>>>(p);
+  else if (xmode == 1)
+    k_pcg_update<T, false, 1><<<kVecBlocks, kVecThreads, 0, s>>>(p);
+  else if (xmode == 2)
+    k_pcg_update<T, false, 2><<<kVecBlocks, kVecThreads, 0, s>>>(p);
   else
-    k_pcg_update<T, false><<<kVecBlocks, kVecThreads, 0, s>>>(p);
+    k_pcg_update<T, false, 0><<<kVecBlocks, kVecThreads, 0, s>>>(p);
   return cudaGetLastError();
+}
+
+// A pair of x updates cut short by a pause (the first of the pair ran): x +=
+// alpha_prev p2 and p = p2, so that x is current and the direction is back in
+// p; nothing otherwise.  The caller clears xpend afterwards.
+__global__ void __launch_bounds__(kVecThreads) k_pcg_xflush(float* __restrict__ x, float* __restrict__ p,
+                                                           const float* __restrict__ p2, const PcgState* st,
+                                                           int64_t n) {
+  if (!st->xpend) return;
+  const float a = (float)st->alpha_prev;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const float v = p2[q];
+    x[q] = x[q] + a * v;
+    p[q] = v;
+  }
+}
+
+cudaError_t launch_pcg_xflush(float* x, float* p, const float* p2, PcgState* st, int64_t n, cudaStream_t s) {
+  k_pcg_xflush<<<kVecBlocks, kVecThreads, 0, s>>>(x, p, p2, st, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(&st->xpend, 0, sizeof(int), s);
 }
 template <typename T>
 cudaError_t launch_pcg_init(const VecParams<T>& p, cudaStream_t s, bool ext) {
@@ -350,8 +396,8 @@ cudaError_t launch_pcg_init(const VecParams<T>& p, cudaStream_t s, bool ext) {
     k_pcg_init<T, false><<<kVecBlocks, kVecThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
-template cudaError_t launch_pcg_update<double>(const VecParams<double>&, cudaStream_t, bool);
-template cudaError_t launch_pcg_update<float>(const VecParams<float>&, cudaStream_t, bool);
+template cudaError_t launch_pcg_update<double>(const VecParams<double>&, cudaStream_t, bool, int);
+template cudaError_t launch_pcg_update<float>(const VecParams<float>&, cudaStream_t, bool, int);
 template cudaError_t launch_pcg_init<double>(const VecParams<double>&, cudaStream_t, bool);
 template cudaError_t launch_pcg_init<float>(const VecParams<float>&, cudaStream_t, bool);
 

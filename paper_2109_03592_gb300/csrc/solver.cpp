@@ -38,7 +38,7 @@ static void destroy_ws(Workspace* ws) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
   for (void* p : {(void*)ws->x, (void*)ws->r, (void*)ws->z, (void*)ws->p, (void*)ws->w, (void*)ws->minv,
                   (void*)ws->b, (void*)ws->x32, (void*)ws->r32, (void*)ws->z32, (void*)ws->p32, (void*)ws->w32,
-                  (void*)ws->minv32, (void*)ws->st, (void*)ws->part_ax, (void*)ws->part_vec})
+                  (void*)ws->minv32, (void*)ws->p32b, (void*)ws->st, (void*)ws->part_ax, (void*)ws->part_vec})
     if (p) cudaFree(p);
   if (ws->sth) cudaFreeHost(ws->sth);
   for (cudaEvent_t e : {ws->e0, ws->e1, ws->eu, ws->ev[0], ws->ev[1]})
@@ -75,7 +75,7 @@ sem_status alloc_ws(sem_mesh* m, Workspace** out) {
   cudaError_t e = cudaSuccess;
   for (double** p : {&ws->x, &ws->r, &ws->z, &ws->p, &ws->w, &ws->minv, &ws->b})
     if ((e = cudaMalloc((void**)p, n * sizeof(double))) != cudaSuccess) return fail(e, "cudaMalloc workspace");
-  for (float** p : {&ws->x32, &ws->r32, &ws->z32, &ws->p32, &ws->w32, &ws->minv32})
+  for (float** p : {&ws->x32, &ws->r32, &ws->z32, &ws->p32, &ws->w32, &ws->minv32, &ws->p32b})
     if ((e = cudaMalloc((void**)p, n * sizeof(float))) != cudaSuccess) return fail(e, "cudaMalloc workspace");
   if ((e = cudaMalloc((void**)&ws->st, sizeof(PcgState))) != cudaSuccess) return fail(e, "cudaMalloc state");
   if ((e = cudaMalloc((void**)&ws->part_ax, (size_t)max_ax_grid(m) * sizeof(double))) != cudaSuccess)
@@ -118,9 +118,9 @@ cudaError_t ax64_exact(const sem_mesh* m, const double* u, double* w, double h1,
 }
 
 cudaError_t ax32(const sem_mesh* m, const float* u, float* w, double h1, double h2, bool fused, const float* z,
-                 float* p, PcgState* st, double* part, cudaStream_t s) {
+                 float* p, PcgState* st, double* part, cudaStream_t s, float* pout) {
   AxParams<float> a{u, w, m->opG32(), m->opB32(), m->D32, (float)h1, (float)h2, h2 != 0.0, m->E, z, p, st, part,
-                    m->dev_err};
+                    m->dev_err, pout};
   int var = m->ax_var[1];
   // the bulk-copy kernels read u with 16-byte aligned copies: a caller's
   // unaligned u takes the faster of the register kernels instead
@@ -333,12 +333,28 @@ static sem_status iter64(sem_mesh* m, Workspace* ws, double h1, double h2) {
   return SEM_OK;
 }
 
-static sem_status iter32(sem_mesh* m, Workspace* ws, double h1, double h2) {
-  SEM_CUDA(ax32(m, nullptr, ws->w32, h1, h2, true, ws->z32, ws->p32, ws->st, ws->part_ax, ws->s));
+// Iteration j of a chunk (kChunk is even).  The directions alternate between
+// p32 and p32b: iteration j reads p from one and writes z + beta p to the
+// other, so the direction of an even j survives the odd j after it, whose
+// update then advances x by both (x += alpha_j p_j + alpha_{j+1} p_{j+1}):
+// x is read and written once per two iterations instead of every iteration.
+// A chunk starts and ends with the direction in p32 and x current; a pause
+// after an even j leaves a pair open, which flush_x32 completes.
+static sem_status iter32(sem_mesh* m, Workspace* ws, double h1, double h2, int j) {
+  float* src = (j & 1) ? ws->p32b : ws->p32;
+  float* dst = (j & 1) ? ws->p32 : ws->p32b;
+  SEM_CUDA(ax32(m, nullptr, ws->w32, h1, h2, true, ws->z32, src, ws->st, ws->part_ax, ws->s, dst));
   SEM_CUDA(launch_gs<float>(ws->w32, gs_dev(m), 1, ws->st, ws->s));
-  VecParams<float> v{ws->x32, ws->r32, ws->z32, ws->p32, ws->w32, ws->minv32, ws->r32, m->wm, ws->n, ws->st,
-                     ws->part_vec};
-  SEM_CUDA(launch_pcg_update<float>(v, ws->s));
+  VecParams<float> v{ws->x32, ws->r32, ws->z32, dst,   ws->w32, ws->minv32, ws->r32, m->wm,
+                     ws->n,   ws->st,  ws->part_vec, src};
+  SEM_CUDA(launch_pcg_update<float>(v, ws->s, false, (j & 1) ? 2 : 1));
+  return SEM_OK;
+}
+
+// After a run of chunks: complete an open pair of x updates (see iter32).
+static sem_status flush_x32(Workspace* ws) {
+  SEM_CUDA(launch_pcg_xflush(ws->x32, ws->p32, ws->p32b, ws->st, ws->n, ws->s));
+  count_launches(1);
   return SEM_OK;
 }
 
@@ -375,13 +391,14 @@ static sem_status get_graph(sem_mesh* m, Workspace* ws, bool fp32, double h1, do
   // per-kernel attributes are set outside the capture.
   sem_status st = put_state(ws, 0.0, 0, 1);
   if (st != SEM_OK) return st;
-  st = fp32 ? iter32(m, ws, h1, h2) : iter64(m, ws, h1, h2);
+  for (int j = 0; j < (fp32 ? 2 : 1) && st == SEM_OK; ++j) st = fp32 ? iter32(m, ws, h1, h2, j) : iter64(m, ws, h1, h2);
   if (st != SEM_OK) return st;
   count_launches(3);
   SEM_CUDA(cudaStreamSynchronize(ws->s));
   cudaGraph_t graph = nullptr;
   SEM_CUDA(cudaStreamBeginCapture(ws->s, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < kChunk && st == SEM_OK; ++k) st = fp32 ? iter32(m, ws, h1, h2) : iter64(m, ws, h1, h2);
+  static_assert(kChunk % 2 == 0, "the FP32 iterations pair their x updates within a chunk");
+  for (int k = 0; k < kChunk && st == SEM_OK; ++k) st = fp32 ? iter32(m, ws, h1, h2, k) : iter64(m, ws, h1, h2);
   cudaError_t e = cudaStreamEndCapture(ws->s, &graph);
   if (st != SEM_OK) {
     if (graph) cudaGraphDestroy(graph);
@@ -530,6 +547,8 @@ static sem_status pcg_mixed(sem_mesh* m, Workspace* ws, const sem_solve_opts& o,
     PcgState fin;
     st = run_chunks(ws, ws->g32, maxit, fin);
     if (st != SEM_OK) return st;
+    st = flush_x32(ws);
+    if (st != SEM_OK) return st;
     res.iters += fin.iter;
     if (fin.status == SEM_ERR_BREAKDOWN) {
       res.status = SEM_ERR_BREAKDOWN;
@@ -585,6 +604,8 @@ static sem_status pcg_mixed_reliable(sem_mesh* m, Workspace* ws, const sem_solve
   for (;;) {
     PcgState fin;
     st = run_chunks(ws, ws->g32, maxit, fin);
+    if (st != SEM_OK) return st;
+    st = flush_x32(ws);
     if (st != SEM_OK) return st;
     res.iters = fin.iter;
     launch_accumulate(ws->x, ws->x32, bnorm, ws->n, ws->s);

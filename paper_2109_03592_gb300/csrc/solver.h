@@ -17,6 +17,7 @@ struct Workspace {
   int64_t n = 0;
   double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr, *minv = nullptr, *b = nullptr;
   float *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *w32 = nullptr, *minv32 = nullptr;
+  float* p32b = nullptr;  // the FP32 CG's second direction buffer (directions alternate between p32 and p32b)
   PcgState* st = nullptr;
   PcgState* sth = nullptr;  // pinned host [2]
   double* part_ax = nullptr;
@@ -32,9 +33,10 @@ void free_ws(Workspace* ws);  // a workspace from alloc_ws that is not a mesh's
 // FP64 local operator with the mesh's tuned kernel (native or double-float).
 // w = A_L u with the native FP64 kernel (exact FP64 arithmetic)
 cudaError_t ax64_exact(const sem_mesh* m, const double* u, double* w, double h1, double h2, cudaStream_t s);
-// FP32 local operator with the mesh's tuned kernel (fused: the CG prologue and <p, A_L p>).
+// FP32 local operator with the mesh's tuned kernel (fused: the CG prologue and <p, A_L p>;
+// pout, when given, receives the new direction z + beta p instead of p).
 cudaError_t ax32(const sem_mesh* m, const float* u, float* w, double h1, double h2, bool fused, const float* z,
-                 float* p, PcgState* st, double* part, cudaStream_t s);
+                 float* p, PcgState* st, double* part, cudaStream_t s, float* pout = nullptr);
 cudaError_t ax64(const sem_mesh* m, const double* u, double* w, double h1, double h2, bool fused, const double* z,
                  double* p, PcgState* st, double* part, cudaStream_t s);
 // Write a fresh PcgState (tol, maxit, done) to ws->st / read it back (both synchronise ws->s).
