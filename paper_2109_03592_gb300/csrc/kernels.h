@@ -189,12 +189,7 @@ cudaError_t launch_pscale(const double* r, const double* dinv, double* z, int64_
                           cudaStream_t s);
 cudaError_t launch_pshift_dot(double* w, const double* p, double c, int64_t n, double* partial, double* out,
                               cudaStream_t s);
-cudaError_t launch_pupdate(double* x, double* r, const double* p, const double* w, double alpha, int64_t n,
-                           double* partial, double* out, cudaStream_t s);
 cudaError_t launch_pdir(double* y, const double* a, double beta, int64_t n, cudaStream_t s);
 cudaError_t launch_pstart(const double* g, double c, double* r, double* p, double* x, int64_t n, double* partial,
                           double* out, cudaStream_t s);
-cudaError_t launch_presidual(const double* g, double cg, const double* w, double cw, double* r, double* q, int64_t n,
-                             double* partial, double* out, cudaStream_t s);
-
 }  // namespace sem

@@ -136,21 +136,6 @@ __global__ void k_pshift_dot(double* __restrict__ w, const double* __restrict__ 
   if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
-// x += alpha p; r -= alpha w; partial sums of r_i r_i
-__global__ void k_pupdate(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                          const double* __restrict__ w, double alpha, int64_t n, double* partial) {
-  __shared__ double s[kRedThreads];
-  double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
-    x[i] += alpha * p[i];
-    const double v = r[i] - alpha * w[i];
-    r[i] = v;
-    acc += v * v;
-  }
-  const double t = block_sum(acc, s);
-  if (threadIdx.x == 0) partial[blockIdx.x] = t;
-}
-
 // y = a + beta y (the CG direction p = r + beta p)
 __global__ void k_pdir(double* __restrict__ y, const double* __restrict__ a, double beta, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -167,22 +152,6 @@ __global__ void k_pstart(const double* __restrict__ g, double c, double* __restr
     r[i] = v;
     p[i] = v;
     x[i] = 0.0;
-    acc += v * v;
-  }
-  const double t = block_sum(acc, s);
-  if (threadIdx.x == 0) partial[blockIdx.x] = t;
-}
-
-// r = (g - cg) - (w - cw), q = r; partial sums of r_i r_i (the true residual
-// Pm (g - E x) when w = E x and cg, cw are the means of g and w)
-__global__ void k_presidual(const double* __restrict__ g, double cg, const double* __restrict__ w, double cw,
-                            double* __restrict__ r, double* __restrict__ q, int64_t n, double* partial) {
-  __shared__ double s[kRedThreads];
-  double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
-    const double v = (g[i] - cg) - (w[i] - cw);
-    r[i] = v;
-    q[i] = v;
     acc += v * v;
   }
   const double t = block_sum(acc, s);
@@ -593,12 +562,6 @@ cudaError_t launch_pshift_dot(double* w, const double* p, double c, int64_t n, d
   return cudaGetLastError();
 }
 
-cudaError_t launch_pupdate(double* x, double* r, const double* p, const double* w, double alpha, int64_t n,
-                           double* partial, double* out, cudaStream_t s) {
-  k_pupdate<<<kPressureRedBlocks, kRedThreads, 0, s>>>(x, r, p, w, alpha, n, partial);
-  k_psum_finish<<<1, kRedThreads, 0, s>>>(partial, kPressureRedBlocks, out);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_pdir(double* y, const double* a, double beta, int64_t n, cudaStream_t s) {
   k_pdir<<<kPressureRedBlocks, kRedThreads, 0, s>>>(y, a, beta, n);
@@ -612,12 +575,6 @@ cudaError_t launch_pstart(const double* g, double c, double* r, double* p, doubl
   return cudaGetLastError();
 }
 
-cudaError_t launch_presidual(const double* g, double cg, const double* w, double cw, double* r, double* q, int64_t n,
-                             double* partial, double* out, cudaStream_t s) {
-  k_presidual<<<kPressureRedBlocks, kRedThreads, 0, s>>>(g, cg, w, cw, r, q, n, partial);
-  k_psum_finish<<<1, kRedThreads, 0, s>>>(partial, kPressureRedBlocks, out);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_pcg_psig(const double* q, const double* w, int64_t n, PcgState* st, double* partial,
                             cudaStream_t s) {
