@@ -113,8 +113,8 @@ struct VecParams {
 int vec_grid();
 // ext = true: an external preconditioner (its kernels write z = M^{-1} r
 // between k_pcg_update and launch_pcg_rho; init and restart read that z).
-// xmode (FP32 CG, no external preconditioner): 0 x += alpha p; 1 x not
-// updated (alpha kept as alpha_prev, xpend set); 2 x += alpha_prev p2 + alpha p.
+// xmode: 0 x += alpha p; 1 x not updated (alpha kept as alpha_prev, xpend
+// set); 2 x += alpha_prev p2 + alpha p.
 template <typename T>
 cudaError_t launch_pcg_update(const VecParams<T>& p, cudaStream_t s, bool ext = false, int xmode = 0);
 // Completes a pair of x updates after a pause (k_pcg_update xmode 1 was the

@@ -356,7 +356,11 @@ template cudaError_t launch_pcg_restart<double>(const VecParams<double>&, cudaSt
 
 template <typename T>
 cudaError_t launch_pcg_update(const VecParams<T>& p, cudaStream_t s, bool ext, int xmode) {
-  if (ext)
+  if (ext && xmode == 1)
+    k_pcg_update<T, true, 1><<<kVecBlocks, kVecThreads, 0, s>>>(p);
+  else if (ext && xmode == 2)
+    k_pcg_update<T, true, 2><<<kVecBlocks, kVecThreads, 0, s>>>(p);
+  else if (ext)
     k_pcg_update<T, true, 0><<<kVecBlocks, kVecThreads, 0, s>>>(p);
   else if (xmode == 1)
     k_pcg_update<T, false, 1><<<kVecBlocks, kVecThreads, 0, s>>>(p);

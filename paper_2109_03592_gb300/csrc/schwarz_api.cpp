@@ -467,16 +467,20 @@ sem_status apply_t(const sem_schwarz* sw, const T* r, T* z, PcgState* st, double
 }
 
 // One CG iteration with the preconditioner (FP64 or FP32 fields).
-sem_status iter_t(sem_schwarz* sw, bool f32) {
+// FP32: iteration j of a chunk, the directions alternating between p32 and
+// p32b and x advanced once per two iterations, as in the Jacobi solver.
+sem_status iter_t(sem_schwarz* sw, bool f32, int j) {
   sem_mesh* m = sw->m;
   Workspace* ws = sw->ws;
   const bool fused_rho = sw->coarse != 0;
   if (f32) {
-    SEM_CUDA(ax32(m, nullptr, ws->w32, sw->h1, sw->h2, true, ws->z32, ws->p32, ws->st, ws->part_ax, ws->s));
+    float* src = (j & 1) ? ws->p32b : ws->p32;
+    float* dst = (j & 1) ? ws->p32 : ws->p32b;
+    SEM_CUDA(ax32(m, nullptr, ws->w32, sw->h1, sw->h2, true, ws->z32, src, ws->st, ws->part_ax, ws->s, dst));
     SEM_CUDA(launch_gs<float>(ws->w32, gs_dev(m), 1, ws->st, ws->s));
-    VecParams<float> v{ws->x32, ws->r32, ws->z32, ws->p32, ws->w32, nullptr, ws->r32, m->wm, ws->n, ws->st,
-                       ws->part_vec};
-    SEM_CUDA(launch_pcg_update<float>(v, ws->s, true));
+    VecParams<float> v{ws->x32, ws->r32, ws->z32, dst,          ws->w32, nullptr, ws->r32,
+                       m->wm,   ws->n,   ws->st,  ws->part_vec, src};
+    SEM_CUDA(launch_pcg_update<float>(v, ws->s, true, (j & 1) ? 2 : 1));
     count_launches(3);
     SW_TRY(apply_t<float>(sw, ws->r32, ws->z32, ws->st, ws->part_vec, fused_rho, ws->s));
     if (!fused_rho) {
@@ -531,12 +535,14 @@ sem_status get_graph(sem_schwarz* sw, bool f32) {
   // one eager pass with done = 1 (every kernel returns at once): per-kernel
   // attributes are set outside the capture
   SW_TRY(put_state(ws, 0.0, 0, 1));
-  SW_TRY(iter_t(sw, f32));
+  SW_TRY(iter_t(sw, f32, 0));
+  if (f32) SW_TRY(iter_t(sw, f32, 1));
   SEM_CUDA(cudaStreamSynchronize(ws->s));
   cudaGraph_t graph = nullptr;
   SEM_CUDA(cudaStreamBeginCapture(ws->s, cudaStreamCaptureModeThreadLocal));
   sem_status st = SEM_OK;
-  for (int k = 0; k < kSolveChunk && st == SEM_OK; ++k) st = iter_t(sw, f32);
+  static_assert(kSolveChunk % 2 == 0, "the FP32 iterations pair their x updates within a chunk");
+  for (int k = 0; k < kSolveChunk && st == SEM_OK; ++k) st = iter_t(sw, f32, k);
   cudaError_t e = cudaStreamEndCapture(ws->s, &graph);
   if (st != SEM_OK) {
     if (graph) cudaGraphDestroy(graph);
@@ -646,6 +652,8 @@ sem_status pcg_mixed(sem_schwarz* sw, double tol, int maxit, double delta, Out& 
   for (;;) {
     PcgState fin;
     SW_TRY(run_chunks(ws, sw->g32, maxit, fin));
+    SEM_CUDA(launch_pcg_xflush(ws->x32, ws->p32, ws->p32b, ws->st, ws->n, ws->s));  // an open pair of x updates
+    count_launches(1);
     res.iters = fin.iter;
     launch_accumulate(ws->x, ws->x32, bnorm, ws->n, ws->s);
     launch_zero_f32(ws->x32, ws->n, ws->s);
