@@ -642,7 +642,8 @@ def desc_elements(d):
 # tma::k_ax_tma<7, 2, 3, false>, from ncu on the E = 32,768 pipe (N = 7):
 # 469,796,096 + 55,301,888 bytes.  The kernel streams its elements once
 # (no reuse across elements), so a launch over E elements moves E / 32,768
-# times that; profiles/k_ax_tma_fp32_pipe32768_n7.md has the command.
+# times that (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on one
+# launch of this script with --workload pipe32768_n7).
 TRAFFIC_E32768_N7 = 469_796_096 + 55_301_888
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of tma::k_ax_tma<7, 2, 3, false> on the "
                   "E = 32,768 pipe, scaled by the element count")
