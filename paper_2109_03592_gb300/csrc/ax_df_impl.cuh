@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_ax_df(const AxDFParam
 #pragma unroll
       for (int k = 0; k < n; ++k) {
         const double v = P.z[base + k * n2] + beta * P.p[base + k * n2];
-        P.p[base + k * n2] = v;
+        (P.pout ? P.pout : P.p)[base + k * n2] = v;
         ud[k] = v;
       }
     } else {
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(EPB*(N + 1) * (N + 1)) k_ax_df(const AxDFParam
   if (act) {
     const DF h1 = split64(P.h1);
     const DF h2 = split64(P.h2);
-    const DF c0 = split64(FUSED ? P.p[e * n3] : P.u[e * n3]);  // u0 again (not kept live in registers)
+    const DF c0 = split64(FUSED ? (P.pout ? P.pout : P.p)[e * n3] : P.u[e * n3]);  // u0 again (not kept live in registers)
 #pragma unroll
     for (int k = 0; k < n; ++k) {
       Acc acc = rw[k];

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(EPB* eo_threads_per_element<N>(), eo_min_block
       double v;
       if (FUSED) {
         v = P.z[g] + beta * P.p[g];
-        P.p[g] = v;
+        (P.pout ? P.pout : P.p)[g] = v;
       } else {
         v = P.u[g];
       }
@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(EPB* eo_threads_per_element<N>(), eo_min_block
   Pair sw{0.f, 0.f};
   if (act) {
     const DF h2 = split64(P.h2);
-    const Pair c0 = split_bits(FUSED ? P.p[base] : P.u[base]);  // u0 again (not kept live in registers)
+    const Pair c0 = split_bits(FUSED ? (P.pout ? P.pout : P.p)[base] : P.u[base]);  // u0 again (not kept live in registers)
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int64_t gi = base + I[q & 1] + n * J[(q >> 1) & 1] + n2 * K[q >> 2];

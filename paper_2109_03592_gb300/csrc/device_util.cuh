@@ -23,9 +23,9 @@ struct PcgState {
   double rr_max; // largest <r, r> since the last reliable update
   double delta2; // reliable-update trigger: pause when <r,r> <= delta2 * rr_max (0 = never)
   double cz;     // pressure CG: mean of D^-1 r (aux holds the mean of E q)
-  double alpha_prev;  // FP32 CG, x updated every second iteration: alpha of the pending direction
+  double alpha_prev;  // CG with x updated every second iteration: alpha of the pending direction
   int last;      // pressure CG: iteration of the last residual replacement
-  int xpend;     // FP32 CG: 1 while x lacks alpha_prev times the last direction
+  int xpend;     // 1 while x lacks alpha_prev times the last direction
   int iter;
   int maxit;
   int done;      // 1 once converged / failed / paused: later kernels of the chunk return at once

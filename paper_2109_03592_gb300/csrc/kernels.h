@@ -66,6 +66,7 @@ struct AxDFParams {
   double* partial;
   const double* eo64;  // even-odd coefficient tables (even n; see sem_mesh::eo64)
   const float* eodf;
+  double* pout;        // fused: the new direction goes here (nullptr: over p)
 };
 
 // Kernel variants of the local operator for one (N, precision): 0 and 1 are
@@ -119,7 +120,8 @@ template <typename T>
 cudaError_t launch_pcg_update(const VecParams<T>& p, cudaStream_t s, bool ext = false, int xmode = 0);
 // Completes a pair of x updates after a pause (k_pcg_update xmode 1 was the
 // last): x += alpha_prev p2, p = p2; clears xpend.
-cudaError_t launch_pcg_xflush(float* x, float* p, const float* p2, PcgState* st, int64_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pcg_xflush(T* x, T* p, const T* p2, PcgState* st, int64_t n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pcg_init(const VecParams<T>& p, cudaStream_t s, bool ext = false);
 template <typename T>

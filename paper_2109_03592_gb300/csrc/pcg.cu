@@ -374,24 +374,27 @@ cudaError_t launch_pcg_update(const VecParams<T>& p, cudaStream_t s, bool ext, i
 // A pair of x updates cut short by a pause (the first of the pair ran): x +=
 // alpha_prev p2 and p = p2, so that x is current and the direction is back in
 // p; nothing otherwise.  The caller clears xpend afterwards.
-__global__ void __launch_bounds__(kVecThreads) k_pcg_xflush(float* __restrict__ x, float* __restrict__ p,
-                                                           const float* __restrict__ p2, const PcgState* st,
-                                                           int64_t n) {
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_pcg_xflush(T* __restrict__ x, T* __restrict__ p,
+                                                           const T* __restrict__ p2, const PcgState* st, int64_t n) {
   if (!st->xpend) return;
-  const float a = (float)st->alpha_prev;
+  const T a = (T)st->alpha_prev;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-    const float v = p2[q];
+    const T v = p2[q];
     x[q] = x[q] + a * v;
     p[q] = v;
   }
 }
 
-cudaError_t launch_pcg_xflush(float* x, float* p, const float* p2, PcgState* st, int64_t n, cudaStream_t s) {
-  k_pcg_xflush<<<kVecBlocks, kVecThreads, 0, s>>>(x, p, p2, st, n);
+template <typename T>
+cudaError_t launch_pcg_xflush(T* x, T* p, const T* p2, PcgState* st, int64_t n, cudaStream_t s) {
+  k_pcg_xflush<T><<<kVecBlocks, kVecThreads, 0, s>>>(x, p, p2, st, n);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return cudaMemsetAsync(&st->xpend, 0, sizeof(int), s);
 }
+template cudaError_t launch_pcg_xflush<float>(float*, float*, const float*, PcgState*, int64_t, cudaStream_t);
+template cudaError_t launch_pcg_xflush<double>(double*, double*, const double*, PcgState*, int64_t, cudaStream_t);
 template <typename T>
 cudaError_t launch_pcg_init(const VecParams<T>& p, cudaStream_t s, bool ext) {
   if (ext)

@@ -652,7 +652,7 @@ sem_status pcg_mixed(sem_schwarz* sw, double tol, int maxit, double delta, Out& 
   for (;;) {
     PcgState fin;
     SW_TRY(run_chunks(ws, sw->g32, maxit, fin));
-    SEM_CUDA(launch_pcg_xflush(ws->x32, ws->p32, ws->p32b, ws->st, ws->n, ws->s));  // an open pair of x updates
+    SEM_CUDA(launch_pcg_xflush<float>(ws->x32, ws->p32, ws->p32b, ws->st, ws->n, ws->s));  // an open pair of x updates
     count_launches(1);
     res.iters = fin.iter;
     launch_accumulate(ws->x, ws->x32, bnorm, ws->n, ws->s);

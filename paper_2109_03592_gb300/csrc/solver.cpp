@@ -38,7 +38,7 @@ static void destroy_ws(Workspace* ws) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
   for (void* p : {(void*)ws->x, (void*)ws->r, (void*)ws->z, (void*)ws->p, (void*)ws->w, (void*)ws->minv,
                   (void*)ws->b, (void*)ws->x32, (void*)ws->r32, (void*)ws->z32, (void*)ws->p32, (void*)ws->w32,
-                  (void*)ws->minv32, (void*)ws->p32b, (void*)ws->st, (void*)ws->part_ax, (void*)ws->part_vec})
+                  (void*)ws->minv32, (void*)ws->p32b, (void*)ws->pb, (void*)ws->st, (void*)ws->part_ax, (void*)ws->part_vec})
     if (p) cudaFree(p);
   if (ws->sth) cudaFreeHost(ws->sth);
   for (cudaEvent_t e : {ws->e0, ws->e1, ws->eu, ws->ev[0], ws->ev[1]})
@@ -73,7 +73,7 @@ sem_status alloc_ws(sem_mesh* m, Workspace** out) {
     return st;
   };
   cudaError_t e = cudaSuccess;
-  for (double** p : {&ws->x, &ws->r, &ws->z, &ws->p, &ws->w, &ws->minv, &ws->b})
+  for (double** p : {&ws->x, &ws->r, &ws->z, &ws->p, &ws->w, &ws->minv, &ws->b, &ws->pb})
     if ((e = cudaMalloc((void**)p, n * sizeof(double))) != cudaSuccess) return fail(e, "cudaMalloc workspace");
   for (float** p : {&ws->x32, &ws->r32, &ws->z32, &ws->p32, &ws->w32, &ws->minv32, &ws->p32b})
     if ((e = cudaMalloc((void**)p, n * sizeof(float))) != cudaSuccess) return fail(e, "cudaMalloc workspace");
@@ -95,13 +95,14 @@ sem_status alloc_ws(sem_mesh* m, Workspace** out) {
 // ---- local operator dispatch ---------------------------------------------------
 
 cudaError_t ax64(const sem_mesh* m, const double* u, double* w, double h1, double h2, bool fused,
-                        const double* z, double* p, PcgState* st, double* part, cudaStream_t s) {
+                        const double* z, double* p, PcgState* st, double* part, cudaStream_t s, double* pout) {
   if (m->fp64_df) {
     AxDFParams a{u,      w, m->opG32(), m->opG32lo(), m->opB32(), m->opB32lo(), m->D32, m->D32lo, h1, h2,
-                 h2 != 0.0, m->E, z, p, st, part, m->eo64, m->eodf};
+                 h2 != 0.0, m->E, z, p, st, part, m->eo64, m->eodf, pout};
     return launch_ax_df(m->N, fused ? m->ax_var_dff : m->ax_var[2], fused, a, s, nullptr);
   }
-  AxParams<double> a{u, w, m->opG64(), m->opB64(), m->D64, h1, h2, h2 != 0.0, m->E, z, p, st, part, m->dev_err};
+  AxParams<double> a{u, w, m->opG64(), m->opB64(), m->D64, h1, h2, h2 != 0.0, m->E, z, p, st, part, m->dev_err,
+                     pout};
   return launch_ax_f64(m->N, m->ax_var[0], fused, a, s, nullptr);
 }
 
@@ -325,11 +326,15 @@ forced:
 
 // ---- CG chunks ---------------------------------------------------------------------
 
-static sem_status iter64(sem_mesh* m, Workspace* ws, double h1, double h2) {
-  SEM_CUDA(ax64(m, nullptr, ws->w, h1, h2, true, ws->z, ws->p, ws->st, ws->part_ax, ws->s));
+// Iteration j of a chunk, the directions alternating between p and pb and x
+// advanced once per two iterations, as in iter32 below.
+static sem_status iter64(sem_mesh* m, Workspace* ws, double h1, double h2, int j) {
+  double* src = (j & 1) ? ws->pb : ws->p;
+  double* dst = (j & 1) ? ws->p : ws->pb;
+  SEM_CUDA(ax64(m, nullptr, ws->w, h1, h2, true, ws->z, src, ws->st, ws->part_ax, ws->s, dst));
   SEM_CUDA(launch_gs<double>(ws->w, gs_dev(m), 1, ws->st, ws->s));
-  VecParams<double> v{ws->x, ws->r, ws->z, ws->p, ws->w, ws->minv, ws->b, m->wm, ws->n, ws->st, ws->part_vec};
-  SEM_CUDA(launch_pcg_update<double>(v, ws->s));
+  VecParams<double> v{ws->x, ws->r, ws->z, dst, ws->w, ws->minv, ws->b, m->wm, ws->n, ws->st, ws->part_vec, src};
+  SEM_CUDA(launch_pcg_update<double>(v, ws->s, false, (j & 1) ? 2 : 1));
   return SEM_OK;
 }
 
@@ -351,9 +356,14 @@ static sem_status iter32(sem_mesh* m, Workspace* ws, double h1, double h2, int j
   return SEM_OK;
 }
 
-// After a run of chunks: complete an open pair of x updates (see iter32).
+// After a run of chunks: complete an open pair of x updates (see iter32 and iter64).
 static sem_status flush_x32(Workspace* ws) {
-  SEM_CUDA(launch_pcg_xflush(ws->x32, ws->p32, ws->p32b, ws->st, ws->n, ws->s));
+  SEM_CUDA(launch_pcg_xflush<float>(ws->x32, ws->p32, ws->p32b, ws->st, ws->n, ws->s));
+  count_launches(1);
+  return SEM_OK;
+}
+static sem_status flush_x64(Workspace* ws) {
+  SEM_CUDA(launch_pcg_xflush<double>(ws->x, ws->p, ws->pb, ws->st, ws->n, ws->s));
   count_launches(1);
   return SEM_OK;
 }
@@ -391,14 +401,14 @@ static sem_status get_graph(sem_mesh* m, Workspace* ws, bool fp32, double h1, do
   // per-kernel attributes are set outside the capture.
   sem_status st = put_state(ws, 0.0, 0, 1);
   if (st != SEM_OK) return st;
-  for (int j = 0; j < (fp32 ? 2 : 1) && st == SEM_OK; ++j) st = fp32 ? iter32(m, ws, h1, h2, j) : iter64(m, ws, h1, h2);
+  for (int j = 0; j < 2 && st == SEM_OK; ++j) st = fp32 ? iter32(m, ws, h1, h2, j) : iter64(m, ws, h1, h2, j);
   if (st != SEM_OK) return st;
-  count_launches(3);
+  count_launches(6);
   SEM_CUDA(cudaStreamSynchronize(ws->s));
   cudaGraph_t graph = nullptr;
   SEM_CUDA(cudaStreamBeginCapture(ws->s, cudaStreamCaptureModeThreadLocal));
-  static_assert(kChunk % 2 == 0, "the FP32 iterations pair their x updates within a chunk");
-  for (int k = 0; k < kChunk && st == SEM_OK; ++k) st = fp32 ? iter32(m, ws, h1, h2, k) : iter64(m, ws, h1, h2);
+  static_assert(kChunk % 2 == 0, "the iterations pair their x updates within a chunk");
+  for (int k = 0; k < kChunk && st == SEM_OK; ++k) st = fp32 ? iter32(m, ws, h1, h2, k) : iter64(m, ws, h1, h2, k);
   cudaError_t e = cudaStreamEndCapture(ws->s, &graph);
   if (st != SEM_OK) {
     if (graph) cudaGraphDestroy(graph);
@@ -492,6 +502,8 @@ static sem_status pcg64(sem_mesh* m, Workspace* ws, const sem_solve_opts& o, int
     }
     PcgState fin = s0;
     st = run_chunks(ws, ws->g64, maxit - res.iters, fin);
+    if (st != SEM_OK) return st;
+    st = flush_x64(ws);
     if (st != SEM_OK) return st;
     res.iters += fin.iter;
     if (fin.status != SEM_OK) {  // breakdown, or maxit without meeting the tolerance

@@ -18,6 +18,7 @@ struct Workspace {
   double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr, *minv = nullptr, *b = nullptr;
   float *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *w32 = nullptr, *minv32 = nullptr;
   float* p32b = nullptr;  // the FP32 CG's second direction buffer (directions alternate between p32 and p32b)
+  double* pb = nullptr;   // the FP64 CG's second direction buffer (with p)
   PcgState* st = nullptr;
   PcgState* sth = nullptr;  // pinned host [2]
   double* part_ax = nullptr;
@@ -38,7 +39,7 @@ cudaError_t ax64_exact(const sem_mesh* m, const double* u, double* w, double h1,
 cudaError_t ax32(const sem_mesh* m, const float* u, float* w, double h1, double h2, bool fused, const float* z,
                  float* p, PcgState* st, double* part, cudaStream_t s, float* pout = nullptr);
 cudaError_t ax64(const sem_mesh* m, const double* u, double* w, double h1, double h2, bool fused, const double* z,
-                 double* p, PcgState* st, double* part, cudaStream_t s);
+                 double* p, PcgState* st, double* part, cudaStream_t s, double* pout = nullptr);
 // Write a fresh PcgState (tol, maxit, done) to ws->st / read it back (both synchronise ws->s).
 sem_status put_state(Workspace* ws, double tol, int maxit, int done);
 sem_status read_state(Workspace* ws, PcgState& out);
