@@ -34,6 +34,26 @@ METRIC = "FP64 Ax GDOF/s & %HBM roofline; mixed-prec PCG solves/s, p50/p99 at 1e
 WORKLOAD = "pipe262144_n7"
 # algorithmic bytes per local point (one read of u, G (6 factors), one write of w)
 AX_BYTES = {"fp64": 64, "fp32": 32}
+# Nominal dense FP64 rate of one GB300 on its CUDA cores, TFLOP/s.
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def ax_fp64_roofs(N, n_local, ms, hbm_gbs):
+    """Both roofs of the FP64 Poisson operator of Alg. 1 and which one binds a
+    kernel that evaluates it on the FP64 pipe: HBM at 64 B a local point, and
+    FP64 arithmetic at 12 n + 18 flops a point (n = N + 1: three forward and
+    three transposed derivative contractions of about 2 n flops each, the
+    symmetric G applied to the gradient, 15, and the accumulation of the three
+    transposed terms, 3).  `vs_binding_roof` is the binding roof's time over
+    the measured time: above 1, the kernel beats what a native FP64 kernel
+    could reach."""
+    n = N + 1
+    flops = 12 * n + 18
+    hbm_ms = AX_BYTES["fp64"] * n_local / (hbm_gbs * 1e6)
+    fp64_ms = flops * n_local / (FP64_NOMINAL_TFLOPS * 1e9)
+    return {"flops_per_point": flops, "hbm_roof_ms": hbm_ms, "fp64_roof_ms": fp64_ms,
+            "fp64_tflops_nominal": FP64_NOMINAL_TFLOPS, "binds": "fp64" if fp64_ms > hbm_ms else "hbm",
+            "vs_binding_roof": max(hbm_ms, fp64_ms) / ms}
 
 
 def peaks():
@@ -861,6 +881,7 @@ def run_gpu(args):
             "gs": {"fp64_ms": gs64_ms, "fp32_ms": gs32_ms},
             "ax": {"fp64_ms": ax64_ms, "fp64_gdofs": dof / (ax64_ms * 1e6), "fp64_gbs": ax64_gbs,
                    "fp64_hbm_frac": ax64_gbs / hbm, "fp64_kernel": "double-float" if fp64_df else "native",
+                   "fp64_roofs": ax_fp64_roofs(mesh_N, P, ax64_ms, hbm),
                    "fp32_ms": ax32_ms, "fp32_gdofs": dof / (ax32_ms * 1e6), "fp32_gbs": ax32_gbs,
                    "fp32_hbm_frac": ax32_gbs / hbm},
         }

@@ -44,3 +44,17 @@ def test_single_rank_aggregate():
     import bench
     value, t = bench.aggregate(4.0, steps=2, world=1)
     assert t == 4.0 and value == 0.5
+
+
+def test_fp64_operator_roofs():
+    """E = 262,144, N = 7: 64 B and 114 flops a point; the FP64 pipe binds."""
+    sys.path.insert(0, ROOT)
+    import bench
+    P = 262144 * 512
+    r = bench.ax_fp64_roofs(7, P, 3.16, 6786.6)
+    assert r["flops_per_point"] == 114
+    assert r["binds"] == "fp64"
+    assert r["hbm_roof_ms"] == pytest.approx(64 * P / 6786.6e6)
+    assert r["fp64_roof_ms"] == pytest.approx(114 * P / 1.25e9)
+    assert r["vs_binding_roof"] == pytest.approx(r["fp64_roof_ms"] / 3.16)
+    assert bench.ax_fp64_roofs(1, 8, 1.0, 1e-9)["binds"] == "hbm"  # a slow memory
