@@ -212,7 +212,9 @@ typedef struct {
 typedef struct {
   int iters;       /* CG iterations (summed over inner solves for SEM_MIXED) */
   int outer_iters; /* refinement steps (SEM_MIXED), else 0 */
-  double rel_res;  /* final ||r|| / ||b|| (FP64 true residual for SEM_MIXED; the CG recurrence residual for SEM_FP64) */
+  double rel_res;  /* final ||r|| / ||b||: the true residual b - A x with the FP64 operator, except
+                      when a SEM_FP64 solve stops on breakdown or maxit (then its CG recurrence
+                      residual); SEM_MIXED always reports its last true residual */
   double ms;       /* device time of the solve (CUDA events on the internal stream) */
   int status;      /* sem_status of the solve */
 } sem_solve_result;
