@@ -16,7 +16,17 @@
  *   - Jacobi-preconditioned conjugate gradients (Sec. 2: "iterative solvers
  *     with proper preconditioners"), in FP64 and as FP32-inner / FP64-outer
  *     iterative refinement;
- *   - a request server that solves many such problems concurrently.
+ *   - a request server that solves many such problems concurrently;
+ *
+ * and, around that path:
+ *
+ *   - per-point coefficients h1(x), h2(x) for the velocity Helmholtz solves
+ *     of Sec. 2, Eq. 4 (sem_mesh_set_coefficients);
+ *   - projection of the initial guess onto previous solutions (sem_proj_*);
+ *   - the P_N - P_{N-2} pressure operator E = D B^-1 D^T of Sec. 2, Eq. 5,
+ *     and its CG (sem_pressure_*);
+ *   - the overlapping Schwarz preconditioner of Sec. 2, Eq. 6, with a coarse
+ *     grid solve (sem_schwarz_*).
  *
  * Conventions shared by every entry point:
  *
