@@ -32,6 +32,39 @@ def test_dense_spd_pcg_matches_cholesky(maker, h2):
     assert np.linalg.norm(xg - xd) <= 1e-9 * np.linalg.norm(xd)
 
 
+@pytest.mark.parametrize("maker,h2", [
+    (lambda: mesh.pipe(2, 1, 2, 3, L=2.0), 0.0),
+    (lambda: mesh.box(2, 2, 2, 3), 1.5),
+])
+def test_pcg_iterates_minimise_the_energy_error_over_the_krylov_space(maker, h2):
+    """k steps of Jacobi-PCG from x0 = 0 give the element of the Krylov space
+    K_k(M^-1 A, M^-1 b) closest to the solution in the A-norm (Hestenes and
+    Stiefel 1952): x_k = V (V^T A V)^-1 V^T b for any basis V of that space.
+    V is built here by Arnoldi on the dense matrix, independently of the
+    oracle's recurrences, so a wrong step length, direction update, inner
+    product or preconditioner application fails at some k."""
+    m = maker()
+    P = solver.Problem(m, 1.0, h2)
+    A, free, rep = P.dense()
+    minv = P.jacobi_inverse().reshape(-1)[rep[free]]
+    b = P.rhs(forcing.evaluate(m.xyz, forcing.random_modes(11, L=2.0)))
+    bg = b.reshape(-1)[rep[free]]
+    Q = []
+    v = minv * bg
+    for k in range(1, 8):
+        for q in Q:  # modified Gram-Schmidt, twice
+            v = v - (q @ v) * q
+        for q in Q:
+            v = v - (q @ v) * q
+        Q.append(v / np.linalg.norm(v))
+        V = np.stack(Q, axis=1)
+        ref = V @ np.linalg.solve(V.T @ A @ V, V.T @ bg)
+        res = solver.pcg(P, b, tol=1e-30, maxit=k)
+        got = res.x.reshape(-1)[rep[free]]
+        assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref), k
+        v = minv * (A @ Q[-1])
+
+
 def test_manufactured_solution_spectral_convergence_box():
     errs = []
     for N in (2, 4, 6, 8):
