@@ -166,6 +166,25 @@ CASES += [
      "B[end, end] += (ln / 2.0) * w[N]", "B[end, end] += 0.0 * w[N]", [],
      "test_oracle_schwarz",
      lambda t: t.test_fdm_local_solve_is_the_exact_overlapping_subdomain_inverse_on_a_tensor_box(2.5)),
+    ("pressure_cg_operator_not_projected", pressure, "cg",
+     "w = P.E(p)\n        w = w - w.mean()\n", "w = P.E(p)\n", [],
+     "test_oracle_pressure",
+     lambda t: t.test_pressure_cg_matches_dense_solve_on_the_mean_free_space(lambda: mesh.pipe(2, 1, 3, 3, L=1.5))),
+    ("pressure_jacobi_not_projected", pressure, "cg",
+     "return z - z.mean()", "return z", [],
+     "test_oracle_pressure", lambda t: t.test_jacobi_cg_reaches_the_plain_solution_in_fewer_iterations()),
+    ("schwarz_weight_on_one_side", schwarz.Schwarz, "apply",
+     "self.prob.gs(W * self.local_solve(W * r))", "self.prob.gs(self.local_solve(W * r))", [],
+     "test_oracle_schwarz",
+     lambda t: t.test_preconditioner_is_symmetric_positive_definite(lambda: mesh.box(2, 2, 2, 3), False)),
+    ("coarse_restriction_counts_copies", schwarz.Schwarz, "restrict",
+     "r / self.prob.mult", "r", [],
+     "test_oracle_schwarz",
+     lambda t: t.test_preconditioner_is_symmetric_positive_definite(lambda: mesh.pipe(2, 1, 3, 3, L=1.5), True)),
+    ("coarse_functions_i_and_k_swapped", schwarz.Schwarz, "_coarse_space",
+     "fk[:, None, None] * fj[None, :, None] * fi[None, None, :]",
+     "fi[:, None, None] * fj[None, :, None] * fk[None, None, :]", [],
+     "test_oracle_schwarz", lambda t: t.test_coarse_functions_reproduce_trilinear_fields()),
     ("fdm_local_solve_without_h2", schwarz.Schwarz, "local_solve",
      "+ lt[:, :, None, None]) + h2", "+ lt[:, :, None, None])", [],
      "test_oracle_schwarz",
