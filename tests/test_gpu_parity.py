@@ -196,6 +196,40 @@ def test_zero_rhs_and_initial_guess():
     assert res["iters"] == 0
 
 
+@pytest.mark.parametrize("N", [1, 2, 7])
+def test_single_element_degenerate_systems(N):
+    """One element with Dirichlet faces all round: at N = 1 every node lies on
+    the boundary (no unknowns: b = 0 and both solves return x = 0 at once);
+    at N = 2 one free node (Jacobi-PCG is exact in one step); at N = 7 a 6^3
+    interior, on one ragged tile of the element-blocked kernels.  Ax, QQ^T
+    and the FP64 and mixed solves against the oracle."""
+    import torch
+    import paper_2109_03592_gb300 as sem
+    desc = dict(kind="box", nx=1, ny=1, nz=1, N=N, lx=0.7, ly=1.0, lz=1.3)
+    m = sem.Mesh(desc)
+    P = solver.Problem(_oracle_mesh(desc))
+    assert m.E == 1 and m.n_global == P.Pg
+    u = vectors.local_field(5, 1, N + 1)
+    w = torch.empty(m.shape, dtype=torch.float64, device="cuda")
+    m.ax(to_gpu(u), w, 1.0, 0.0)
+    assert relerr(w.cpu().numpy(), operator.ax_local(u, P.G, P.B, P.D)) < AX_TOL
+    m.gs(w, apply_mask=True)
+    ref = P.mask * P.gs(operator.ax_local(u, P.G, P.B, P.D))
+    np.testing.assert_allclose(w.cpu().numpy(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    b = P.rhs(forcing.evaluate(P.mesh.xyz, forcing.random_modes(3, L=1.3)))
+    for prec in (sem.FP64, sem.MIXED):
+        x = torch.zeros(m.shape, dtype=torch.float64, device="cuda")
+        res = m.solve(to_gpu(b), x, tol=1e-10, prec=prec)
+        assert res["status"] == 0, res
+        xs = x.cpu().numpy()
+        if N == 1:
+            assert not b.any() and res["iters"] == 0 and not xs.any()
+            continue
+        assert _residual(P, b, xs) <= 1.1e-10
+        if N == 2 and prec == sem.FP64:  # the mixed solve adds FP64 residual replacements
+            assert res["iters"] == 1
+
+
 def test_determinism():
     import torch
     m, P = setup("pipe_n5")
