@@ -154,12 +154,13 @@ def aggregate(local_seconds, steps, world, dist=None):
 
 # ---------------------------------------------------------------- oracle arm
 
-def _oracle_slab_worker(budget_s):
+def _oracle_slab_worker(budget_s, warmup=0, steps=1):
     """One host core: the oracle's FP64 Jacobi-PCG iteration (A = mask QQ^T
     A_L, Jacobi, weighted dots; oracle/solver.py restated as a loop) on a
-    3-layer slab of the bench pipe (nc = 16, nr = 4, N = 7, E = 1536) for
-    budget_s seconds.  Returns (local points x iterations per second,
-    iterations, seconds)."""
+    3-layer slab of the bench pipe (nc = 16, nr = 4, N = 7, E = 1536):
+    `warmup` untimed steps, then `steps` timed ones, each iterating for
+    budget_s / steps seconds.  Returns (local points x iterations per second
+    of each timed step, iterations, seconds)."""
     os.environ["OMP_NUM_THREADS"] = "1"
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
     import numpy as np
@@ -174,23 +175,36 @@ def _oracle_slab_worker(budget_s):
     z = Minv * r
     p = z.copy()
     rho = P.dot(r, z)
-    t0 = time.perf_counter()
-    k = 0
-    while True:
-        w = P.A(p)
-        alpha = rho / P.dot(p, w)
-        x += alpha * p
-        r -= alpha * w
-        P.dot(r, r)
-        z = Minv * r
-        rho_new = P.dot(r, z)
-        p = z + (rho_new / rho) * p
-        rho = rho_new
-        k += 1
-        el = time.perf_counter() - t0
-        if el >= budget_s:
-            break
-    return k * m.E * 512 / el, k, el
+
+    def run(seconds):
+        nonlocal x, r, z, p, rho
+        t0 = time.perf_counter()
+        k = 0
+        while True:
+            w = P.A(p)
+            alpha = rho / P.dot(p, w)
+            x += alpha * p
+            r -= alpha * w
+            P.dot(r, r)
+            z = Minv * r
+            rho_new = P.dot(r, z)
+            p = z + (rho_new / rho) * p
+            rho = rho_new
+            k += 1
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                return k, el
+
+    per_step = budget_s / max(1, steps)
+    for _ in range(warmup):
+        run(per_step)
+    rates, its, secs = [], 0, 0.0
+    for _ in range(max(1, steps)):
+        k, el = run(per_step)
+        rates.append(k * m.E * 512 / el)
+        its += k
+        secs += el
+    return rates, its, secs
 
 
 def _oracle_full_solve(workload):
@@ -255,23 +269,28 @@ def host_cpu():
     return os.cpu_count() or 1, model
 
 
-def oracle_sample(budget_s=20.0, cores=None):
+def oracle_sample(budget_s=20.0, cores=None, warmup=0, steps=1):
     """The oracle's FP64 PCG iteration timed on every host core at once: one
     spawned process per core, each iterating on its own copy of the 3-layer
-    slab (independent problems, as the GPU replicas).  Returns (seconds per
-    local point per iteration for the whole host, cores, description)."""
+    slab (independent problems, as the GPU replicas), `warmup` untimed and
+    `steps` timed steps of budget_s / steps seconds each.  Returns (seconds
+    per local point per iteration for the whole host, averaged over the timed
+    steps, cores, CPU model, description, the same per timed step)."""
     import multiprocessing as mp
     ncores, model = host_cpu()
     cores = cores or ncores
     ctx = mp.get_context("spawn")  # no fork after CUDA initialisation
     with ctx.Pool(cores) as pool:
-        res = pool.map(_oracle_slab_worker, [budget_s] * cores)
-    rate = sum(r[0] for r in res)
+        res = pool.starmap(_oracle_slab_worker, [(budget_s, warmup, steps)] * cores)
+    nsteps = len(res[0][0])
+    step_rates = [sum(r[0][j] for r in res) for j in range(nsteps)]  # the host's rate in each step
+    rate = sum(step_rates) / nsteps
     its = sum(r[1] for r in res)
     desc = (f"oracle FP64 Jacobi-PCG iterations on a 3-layer slab of the pipe (nc=16, nr=4, N=7, E=1536), one "
-            f"process per core on {cores} cores ({model}), {budget_s:.0f} s each, {its} iterations in total; the "
-            f"host's points x iterations per second scaled to the solve")
-    return 1.0 / rate, cores, model, desc
+            f"process per core on {cores} cores ({model}), {budget_s:.0f} s each"
+            + (f" in {nsteps} timed steps after {warmup} untimed" if nsteps > 1 or warmup else "")
+            + f", {its} iterations in total; the host's points x iterations per second scaled to the solve")
+    return 1.0 / rate, cores, model, desc, [1.0 / q for q in step_rates]
 
 
 # FP64 Jacobi-PCG iterations of the bench system (E = 262,144 pipe, seed-2
@@ -289,7 +308,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     E, n3 = 262144, 512
-    sec_pt, cores, model, desc = oracle_sample(budget_s=max(10.0, 20.0 / max(1, args.steps)))
+    # W untimed and K timed steps, each a bounded sample of the workload
+    # (about 20 s of timed work in all, at least 2 s a step)
+    budget = max(20.0, 2.0 * max(1, args.steps))
+    sec_pt, cores, model, desc, step_sec_pt = oracle_sample(budget_s=budget, warmup=args.warmup, steps=args.steps)
     sec_per_solve = sec_pt * E * n3 * FP64_ITERS_BENCH
     value = 1.0 / sec_per_solve
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
@@ -298,7 +320,8 @@ def run_reference(args):
             "data": "synthetic", "config": {"workload": f"{WORKLOAD}: O-grid pipe E=262144 N=7, FP64 Jacobi-PCG to 1e-10"},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "cpu": model, "kind": "oracle",
                              "sample": desc + f" and {FP64_ITERS_BENCH} iterations (the system's FP64 PCG count)"},
-            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "step_values": [1.0 / (q * E * n3 * FP64_ITERS_BENCH) for q in step_sec_pt]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -838,7 +861,7 @@ def run_gpu(args):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu:
-            sec_pt, cores, model, desc_s = oracle_sample(budget_s=20.0)
+            sec_pt, cores, model, desc_s, _ = oracle_sample(budget_s=20.0)
             iters_cpu = fp64["iters"] if fp64 else FP64_ITERS_BENCH
             sec = sec_pt * P * iters_cpu
             cpu = {"value": 1.0 / sec, "unit": "solves/s", "cores": cores, "cpu": model, "kind": "oracle",
