@@ -58,3 +58,15 @@ def test_fp64_operator_roofs():
     assert r["fp64_roof_ms"] == pytest.approx(114 * P / 1.25e9)
     assert r["vs_binding_roof"] == pytest.approx(r["fp64_roof_ms"] / 3.16)
     assert bench.ax_fp64_roofs(1, 8, 1.0, 1e-9)["binds"] == "hbm"  # a slow memory
+
+
+def test_oracle_sample_reports_each_timed_step():
+    """The CPU oracle arm's sampler: two spawned processes, one untimed and
+    two timed steps; the mean of the per-step values is the reported one."""
+    sys.path.insert(0, ROOT)
+    import bench
+    sec_pt, cores, model, desc, steps = bench.oracle_sample(budget_s=1.0, cores=2, warmup=1, steps=2)
+    assert cores == 2 and len(steps) == 2 and all(s > 0 for s in steps)
+    rate = sum(1.0 / s for s in steps) / 2
+    assert sec_pt == pytest.approx(1.0 / rate)
+    assert "2 timed steps after 1 untimed" in desc
