@@ -615,6 +615,26 @@ class EngineImpl {
     return SEM_OK;
   }
 
+  void abandon() {
+    if (s_) cudaStreamSynchronize(s_);
+    auto drop = [](Req* q) {
+      if (q->ws) {
+        cudaStreamSynchronize(q->ws->s);
+        if (q->own_ws) q->m->spare_ws.push_back(q->ws);
+      }
+      q->ws = nullptr;
+      q->own_ws = false;
+      q->slot = -1;
+    };
+    for (Req*& q : slots_) {
+      if (q) drop(q);
+      q = nullptr;
+    }
+    for (Req* q : pending_) drop(q);
+    pending_.clear();
+    dirty_ = true;
+  }
+
   sem_status add(Req* q) {
     int taken = 0;
     sem_status st = add_many(&q, 1, &taken);
@@ -1008,6 +1028,7 @@ sem_status Engine::add(Req* q) { return impl_->add(q); }
 sem_status Engine::add_many(Req* const* qs, int count, int* taken) { return impl_->add_many(qs, count, taken); }
 sem_status Engine::step() { return impl_->step(); }
 bool Engine::idle() const { return impl_->idle(); }
+void Engine::abandon() { impl_->abandon(); }
 int Engine::order() const { return impl_->order(); }
 
 }  // namespace batch
@@ -1098,6 +1119,12 @@ extern "C" sem_status sem_pcg_solve_batch(const sem_mesh* const* meshes, const d
   }
   if (st != SEM_OK) return st;
   batch::Engine& eng = *held;
+  // a failure leaves the requests unfinished: the engine lets go of them (and
+  // of the meshes) before it is destroyed
+  auto fail = [&](sem_status s) {
+    eng.abandon();
+    return s;
+  };
   size_t next = 0;
   const int max_steps = 1 << 20;
   for (int step = 0; step < max_steps; ++step) {
@@ -1107,14 +1134,18 @@ extern "C" sem_status sem_pcg_solve_batch(const sem_mesh* const* meshes, const d
       for (size_t k = next; k < reqs.size(); ++k) qs.push_back(&reqs[k]);
       int taken = 0;
       st = eng.add_many(qs.data(), (int)qs.size(), &taken);
-      if (st != SEM_OK) return st;
+      if (st != SEM_OK) return fail(st);
       next += taken;
     }
     if (eng.idle() && next == reqs.size()) break;
     st = eng.step();
-    if (st != SEM_OK) return st;
+    if (st != SEM_OK) return fail(st);
   }
-  if (eng.idle()) put_idle_engine(dev, N, held.release());  // kept with its captured graph
+  if (!eng.idle() || next < reqs.size()) {
+    set_error("sem_pcg_solve_batch: the batch did not finish within its step limit");
+    return fail(SEM_ERR_DEVICE_TIMEOUT);
+  }
+  put_idle_engine(dev, N, held.release());  // kept with its captured graph
   sem_status first_bad = SEM_OK;
   for (auto& q : reqs)
     if (q.status != SEM_OK && first_bad == SEM_OK) first_bad = q.status;

@@ -45,6 +45,11 @@ class Engine {
   sem_status step();
   bool idle() const;
   int order() const;
+  // After a failure: drop every request the engine holds (each request's own
+  // workspace goes back to its mesh, to be freed with it) once their streams
+  // are idle, so that the engine keeps no pointer to a request or mesh the
+  // caller releases next.  The requests are left unfinished.
+  void abandon();
 
  private:
   EngineImpl* impl_;

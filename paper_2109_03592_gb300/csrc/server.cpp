@@ -153,20 +153,36 @@ void engine_main(sem_server* srv, EngineThread* et) {
       int taken = 0;
       sem_status st = init_st;
       if (st == SEM_OK) st = eng.add_many(qs.data(), (int)qs.size(), &taken);
-      for (size_t k = 0; k < incoming.size(); ++k) {
-        auto& q = incoming[k];
-        if (st != SEM_OK || (int)k >= taken) {
+      if (st != SEM_OK) {  // the engine is not used again: fail the new requests and those it holds
+        eng.abandon();
+        for (auto& q : incoming) {
           q->x.clear();
           free_request_device(*q);
-          complete(srv, q, st != SEM_OK ? st : SEM_ERR_BUSY);
+          complete(srv, q, st);
+        }
+        for (auto& q : et->active) {
+          free_request_device(*q);
+          complete(srv, q, st);
+        }
+        et->active.clear();
+        init_st = st;
+        continue;
+      }
+      for (size_t k = 0; k < incoming.size(); ++k) {
+        auto& q = incoming[k];
+        if ((int)k >= taken) {
+          q->x.clear();
+          free_request_device(*q);
+          complete(srv, q, SEM_ERR_BUSY);
           continue;
         }
         et->active.push_back(q);
       }
     }
-    if (!eng.idle()) {
+    if (init_st == SEM_OK && !eng.idle()) {
       sem_status st = eng.step();
       if (st != SEM_OK) {  // a CUDA failure: fail every request of this engine
+        eng.abandon();
         for (auto& q : et->active) {
           free_request_device(*q);
           complete(srv, q, st);
