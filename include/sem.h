@@ -519,7 +519,12 @@ sem_status sem_schwarz_info(const sem_schwarz* sw, sem_schwarz_info_t* info);
 
 /* z = M^{-1} r for a continuous, masked local vector r (as the CG residual):
  * r_dev, z_dev [E][n^3] device arrays of doubles (SEM_FP64) or floats
- * (SEM_FP32, the FP32 tables and fields), distinct; asynchronous on stream. */
+ * (SEM_FP32, the FP32 tables and fields), distinct; asynchronous on stream.
+ * The coarse term works in scratch arrays of the preconditioner, so the
+ * applies of one preconditioner must not overlap on the device: issue them
+ * on one stream (or order their streams), and not while a sem_schwarz_solve
+ * with it runs.  Errors: SEM_ERR_INVALID (null or equal arrays, another
+ * prec, coefficients changed since create), SEM_ERR_CUDA. */
 sem_status sem_schwarz_apply(const sem_schwarz* sw, const void* r_dev, void* z_dev, sem_prec prec, void* stream);
 
 /* PCG for A x = b with z = M^{-1} r in place of Jacobi; b_dev, x_dev, opts and
