@@ -383,6 +383,9 @@ sem_status sem_pressure_div(const sem_mesh* mesh, const double* u_dev, double* q
 /* q = E p (Sec. 2, Eq. 5).  work_dev: caller-owned scratch of 3 n_local
  * doubles (the three velocity components), overwritten; it must not overlap
  * p or q.  q may equal p (p is read in full before q is written). */
+sem_status sem_pressure_apply(const sem_mesh* mesh, const double* p_dev, double* q_dev, double* work_dev,
+                              void* stream);
+
 /* q = E p in FP32 (the factors, basis matrices and fields rounded from FP64,
  * the inverse assembled mass applied as its FP32 reciprocal): p, q [E][m^3]
  * floats, work_dev 3 n_local floats of caller-owned scratch; p, q, work
@@ -390,9 +393,6 @@ sem_status sem_pressure_div(const sem_mesh* mesh, const double* u_dev, double* q
  * the stream). */
 sem_status sem_pressure_apply_f32(const sem_mesh* mesh, const float* p_dev, float* q_dev, float* work_dev,
                                   void* stream);
-
-sem_status sem_pressure_apply(const sem_mesh* mesh, const double* p_dev, double* q_dev, double* work_dev,
-                              void* stream);
 
 /* Pressure solve for Sec. 2, Eq. 5: E p = g on the mean-free pressure space.
  * The constants are E's null space when the velocity is Dirichlet on the
