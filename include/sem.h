@@ -257,7 +257,9 @@ sem_status sem_pcg_solve_host(const sem_mesh* mesh, const double* b_host, double
  * batches and frees with sem_mesh_destroy.  The engine of an order (its
  * buffers and captured graph) is kept for later calls of the same order.
  * Returns SEM_OK, or the first request's failing status (results[k].status
- * has each). */
+ * has each).  A failure of the batch itself (SEM_ERR_CUDA, SEM_ERR_OOM, or
+ * SEM_ERR_DEVICE_TIMEOUT when it does not finish within 2^20 steps) is
+ * returned at once, and the requests it had not finished get no result. */
 sem_status sem_pcg_solve_batch(const sem_mesh* const* meshes, const double* const* b_dev, double* const* x_dev,
                                const sem_solve_opts* opts, sem_solve_result* results, int count, void* stream);
 
