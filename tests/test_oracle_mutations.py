@@ -157,7 +157,25 @@ CASES += [
     ("pressure_diagonal_rows_not_squared", pressure.Pressure, "diagonal",
      "row * row", "row", [],
      "test_oracle_pressure", lambda t: t.test_diagonal_is_the_dense_diagonal("box", 3)),
+    ("lagrange_derivative_sign", pressure, "lagrange_derivative",
+     "1.0 / (x_nodes[l] - xq)", "1.0 / (xq - x_nodes[l])", [],
+     "test_oracle_pressure", lambda t: t.test_interpolation_and_derivative_at_gl_points(6)),
+    ("lagrange_basis_denominator_sign", gll, "lagrange_eval",
+     "(t - xm) / (x_nodes[j] - xm)", "(t - xm) / (xm - x_nodes[j])", [],
+     # N sign flips: the same polynomial at even N, so the pin runs at odd N
+     "test_oracle_pressure", lambda t: t.test_interpolation_and_derivative_at_gl_points(3)),
+    ("pressure_space_with_n_gl_points", pressure, "interpolation_matrices",
+     "gl_nodes_weights(N - 1)", "gl_nodes_weights(N)", [],
+     "test_oracle_pressure", lambda t: t.test_interpolation_and_derivative_at_gl_points(6)),
     # -- overlapping Schwarz local solves (Sec. 2, Eq. 6)
+    ("element_lengths_r_and_s_swapped", schwarz, "element_lengths",
+     "np.stack([lr, ls, lt], axis=1)", "np.stack([ls, lr, lt], axis=1)", [],
+     "test_oracle_schwarz",
+     lambda t: t.test_fdm_local_solve_is_the_exact_overlapping_subdomain_inverse_on_a_tensor_box(0.0)),
+    ("face_neighbour_recorded_on_one_side", schwarz, "face_neighbours",
+     "nb[e2, f2] = (e1, f1)", "nb[e2, f2] = (-1, -1)", [],
+     "test_oracle_schwarz",
+     lambda t: t.test_fdm_local_solve_is_the_exact_overlapping_subdomain_inverse_on_a_tensor_box(0.0)),
     ("fdm_extension_with_own_length", schwarz, "fdm_1d",
      "K[end, end] += (2.0 / ln) * Kref[N, N]", "K[end, end] += (2.0 / l) * Kref[N, N]", [],
      "test_oracle_schwarz",
