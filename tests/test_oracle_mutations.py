@@ -127,7 +127,16 @@ CASES += [
      "x = x + x32.astype(np.float64) / s\n            x32[:] = 0.0",
      "x = x + x32.astype(np.float64)\n            x32[:] = 0.0", [],
      "test_oracle_solver", lambda t: t.test_mixed_reliable_updates()),
+    ("fp32_operator_unmasked", solver.Problem32, "A",
+     "return self.mask * self.prob.gs(w)", "return self.prob.gs(w)", [],
+     "test_oracle_solver", lambda t: t.test_mixed_precision_refinement(1e-5)),
+    ("fp32_cg_beta_inverted", solver, "pcg32",
+     "beta = np.float32(rho_new / rho)", "beta = np.float32(rho / rho_new)", [],
+     "test_oracle_solver", lambda t: t.test_fp32_inner_pcg_iterates_follow_the_krylov_optimum()),
     # -- projection onto previous solutions
+    ("projection_never_restarts", projection.Projection, "solve",
+     "if len(self.X) >= self.max_vectors:", "if False:", [],
+     "test_oracle_projection", lambda t: t.test_full_basis_restarts_from_the_newest_solution()),
     ("projection_basis_euclidean_orthogonal", projection.Projection, "_append",
      "beta = [P.dot(ax, v) for ax in self.AX]", "beta = [P.dot(x, v) for x in self.X]", [],
      "test_oracle_projection", lambda t: t.test_basis_is_a_orthonormal()),
@@ -203,6 +212,9 @@ CASES += [
      "fk[:, None, None] * fj[None, :, None] * fi[None, None, :]",
      "fi[:, None, None] * fj[None, :, None] * fk[None, None, :]", [],
      "test_oracle_schwarz", lambda t: t.test_coarse_functions_reproduce_trilinear_fields()),
+    ("schwarz_cg_beta_inverted", schwarz, "pcg",
+     "p = z + (rho_new / rho) * p", "p = z + (rho / rho_new) * p", [],
+     "test_oracle_schwarz", lambda t: t.test_schwarz_pcg_iterates_minimise_the_energy_error_over_the_krylov_space()),
     ("fdm_local_solve_without_h2", schwarz.Schwarz, "local_solve",
      "+ lt[:, :, None, None]) + h2", "+ lt[:, :, None, None])", [],
      "test_oracle_schwarz",

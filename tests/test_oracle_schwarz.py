@@ -80,9 +80,42 @@ def test_preconditioner_is_symmetric_positive_definite(maker, coarse):
     M = np.zeros_like(A)
     for c, g in enumerate(free):
         r = (glo == g).astype(np.float64)
-        M[:, c] = sw.apply(r).reshape(-1)[rep[free]]
+        z = sw.apply(r)
+        # z is a continuous field (equal on every copy of a node) and zero on
+        # the Dirichlet nodes, like the CG vectors it feeds
+        assert np.abs(z[prob.mask == 0]).max(initial=0.0) == 0.0
+        np.testing.assert_allclose(prob.gs(z / prob.mult), z, rtol=0, atol=1e-13 * np.abs(z).max())
+        M[:, c] = z.reshape(-1)[rep[free]]
     assert np.abs(M - M.T).max() <= 1e-12 * np.abs(M).max()
     assert np.linalg.eigvalsh(0.5 * (M + M.T))[0] > 0
+
+
+def test_schwarz_pcg_iterates_minimise_the_energy_error_over_the_krylov_space():
+    """Schwarz-PCG is CG with z = M r: its k-th iterate is the A-norm-closest
+    element of K_k(M A, M b), computed densely (M assembled column by column
+    from the preconditioner, the space by Arnoldi)."""
+    prob = solver.Problem(mesh.pipe(2, 1, 3, 3, L=1.5))
+    sw = schwarz.Schwarz(prob, coarse=True)
+    A, free, rep = prob.dense()
+    glo = prob.glo.reshape(prob.shape)
+    M = np.zeros_like(A)
+    for c, g in enumerate(free):
+        M[:, c] = sw.apply((glo == g).astype(np.float64)).reshape(-1)[rep[free]]
+    b = prob.rhs(np.random.default_rng(1).standard_normal(prob.shape))
+    bg = b.reshape(-1)[rep[free]]
+    Q = []
+    v = M @ bg
+    for k in range(1, 7):
+        for _ in range(2):
+            for q in Q:
+                v = v - (q @ v) * q
+        Q.append(v / np.linalg.norm(v))
+        V = np.stack(Q, axis=1)
+        ref = V @ np.linalg.solve(V.T @ A @ V, V.T @ bg)
+        res = schwarz.pcg(prob, b, sw.apply, tol=1e-30, maxit=k)
+        got = res.x.reshape(-1)[rep[free]]
+        assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref), k
+        v = M @ (A @ Q[-1])
 
 
 def test_schwarz_pcg_solves_the_system_and_the_coarse_grid_bounds_iterations():

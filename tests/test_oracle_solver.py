@@ -32,6 +32,23 @@ def test_dense_spd_pcg_matches_cholesky(maker, h2):
     assert np.linalg.norm(xg - xd) <= 1e-9 * np.linalg.norm(xd)
 
 
+def krylov_optima(A, prec, bg, kmax):
+    """(k, x_k) for k = 1..kmax: the A-norm-closest element to A^-1 bg of the
+    preconditioned Krylov space K_k(M A, M bg), x_k = V (V^T A V)^-1 V^T bg,
+    with V built by Arnoldi (modified Gram-Schmidt, twice) on the dense
+    matrix; prec(v) applies M."""
+    Q = []
+    v = prec(bg)
+    for k in range(1, kmax + 1):
+        for _ in range(2):
+            for q in Q:
+                v = v - (q @ v) * q
+        Q.append(v / np.linalg.norm(v))
+        V = np.stack(Q, axis=1)
+        yield k, V @ np.linalg.solve(V.T @ A @ V, V.T @ bg)
+        v = prec(A @ Q[-1])
+
+
 @pytest.mark.parametrize("maker,h2", [
     (lambda: mesh.pipe(2, 1, 2, 3, L=2.0), 0.0),
     (lambda: mesh.box(2, 2, 2, 3), 1.5),
@@ -40,29 +57,37 @@ def test_pcg_iterates_minimise_the_energy_error_over_the_krylov_space(maker, h2)
     """k steps of Jacobi-PCG from x0 = 0 give the element of the Krylov space
     K_k(M^-1 A, M^-1 b) closest to the solution in the A-norm (Hestenes and
     Stiefel 1952): x_k = V (V^T A V)^-1 V^T b for any basis V of that space.
-    V is built here by Arnoldi on the dense matrix, independently of the
-    oracle's recurrences, so a wrong step length, direction update, inner
-    product or preconditioner application fails at some k."""
+    V is built by Arnoldi on the dense matrix, independently of the oracle's
+    recurrences, so a wrong step length, direction update, inner product or
+    preconditioner application fails at some k."""
     m = maker()
     P = solver.Problem(m, 1.0, h2)
     A, free, rep = P.dense()
     minv = P.jacobi_inverse().reshape(-1)[rep[free]]
     b = P.rhs(forcing.evaluate(m.xyz, forcing.random_modes(11, L=2.0)))
     bg = b.reshape(-1)[rep[free]]
-    Q = []
-    v = minv * bg
-    for k in range(1, 8):
-        for q in Q:  # modified Gram-Schmidt, twice
-            v = v - (q @ v) * q
-        for q in Q:
-            v = v - (q @ v) * q
-        Q.append(v / np.linalg.norm(v))
-        V = np.stack(Q, axis=1)
-        ref = V @ np.linalg.solve(V.T @ A @ V, V.T @ bg)
+    for k, ref in krylov_optima(A, lambda v: minv * v, bg, 7):
         res = solver.pcg(P, b, tol=1e-30, maxit=k)
         got = res.x.reshape(-1)[rep[free]]
         assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref), k
-        v = minv * (A @ Q[-1])
+
+
+def test_fp32_inner_pcg_iterates_follow_the_krylov_optimum():
+    """The FP32 inner PCG of the mixed solvers is the same CG in single
+    precision: its k-th iterate matches the FP64 Krylov optimum to FP32
+    accuracy."""
+    m = mesh.pipe(2, 1, 2, 3, L=2.0)
+    P = solver.Problem(m)
+    A, free, rep = P.dense()
+    minv = P.jacobi_inverse().reshape(-1)[rep[free]]
+    b = P.rhs(forcing.evaluate(m.xyz, forcing.random_modes(11, L=2.0)))
+    bg = b.reshape(-1)[rep[free]]
+    p32 = solver.Problem32(P)
+    for k, ref in krylov_optima(A, lambda v: minv * v, bg, 6):
+        x32, it, st = solver.pcg32(p32, b.astype(np.float32), 1e-30, k)
+        assert it == k
+        got = x32.astype(np.float64).reshape(-1)[rep[free]]
+        assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref), k
 
 
 def test_manufactured_solution_spectral_convergence_box():
