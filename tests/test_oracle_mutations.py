@@ -197,6 +197,12 @@ CASES += [
      "w = P.E(p)\n        w = w - w.mean()\n", "w = P.E(p)\n", [],
      "test_oracle_pressure",
      lambda t: t.test_pressure_cg_matches_dense_solve_on_the_mean_free_space(lambda: mesh.pipe(2, 1, 3, 3, L=1.5))),
+    ("pressure_cg_beta_inverted", pressure, "cg",
+     "p = z + (rho_new / rho) * p", "p = z + (rho / rho_new) * p", [],
+     "test_oracle_pressure", lambda t: t.test_pressure_cg_iterates_minimise_the_energy_error_over_the_krylov_space(False)),
+    ("pressure_cg_step_with_r_dot_r", pressure, "cg",
+     "alpha = rho / sigma", "alpha = np.sum(r * r) / sigma", [],
+     "test_oracle_pressure", lambda t: t.test_pressure_cg_iterates_minimise_the_energy_error_over_the_krylov_space(True)),
     ("pressure_jacobi_not_projected", pressure, "cg",
      "return z - z.mean()", "return z", [],
      "test_oracle_pressure", lambda t: t.test_jacobi_cg_reaches_the_plain_solution_in_fewer_iterations()),

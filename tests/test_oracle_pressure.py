@@ -218,3 +218,33 @@ def test_jacobi_cg_reaches_the_plain_solution_in_fewer_iterations():
     assert r1 <= 1e-10 and it1 < it0
     assert abs(x1.mean()) <= 1e-12 * np.abs(x1).max()
     np.testing.assert_allclose(x1, x0, rtol=0, atol=1e-7 * np.abs(x0).max())
+
+
+@pytest.mark.parametrize("jacobi", [False, True])
+def test_pressure_cg_iterates_minimise_the_energy_error_over_the_krylov_space(jacobi):
+    """On the mean-free space the pressure CG is CG for S = Pm E Pm with the
+    preconditioner Pm D^-1 Pm (Jacobi) or Pm: its k-th iterate is the
+    S-norm-closest element of K_k(M S, M Pm g), computed densely (Arnoldi on
+    the dense E), so a wrong projection, step or direction update fails."""
+    P = pressure.Pressure(solver.Problem(mesh.pipe(2, 1, 3, 3, L=1.5)))
+    A = P.dense()
+    n = A.shape[0]
+    Pm = np.eye(n) - np.ones((n, n)) / n
+    S = Pm @ A @ Pm
+    dinv = 1.0 / P.diagonal()
+    M = Pm @ np.diag(dinv.reshape(-1)) @ Pm if jacobi else Pm
+    g = vectors.local_field(31, P.shape[0], P.shape[1])
+    gv = Pm @ g.reshape(-1)
+    Q = []
+    v = M @ gv
+    for k in range(1, 7):
+        for _ in range(2):
+            for q in Q:
+                v = v - (q @ v) * q
+        Q.append(v / np.linalg.norm(v))
+        V = np.stack(Q, axis=1)
+        ref = V @ np.linalg.solve(V.T @ S @ V, V.T @ gv)
+        x, it, rel, st = pressure.cg(P, g, tol=1e-30, maxit=k, dinv=dinv if jacobi else None)
+        assert it == k
+        assert np.linalg.norm(x.reshape(-1) - ref) <= 1e-9 * np.linalg.norm(ref), k
+        v = M @ (S @ Q[-1])
