@@ -123,6 +123,9 @@ CASES += [
     ("refinement_correction_not_rescaled", solver, "pcg_mixed",
      "x = x + rnorm * d.astype(np.float64)", "x = x + d.astype(np.float64)", [],
      "test_oracle_solver", lambda t: t.test_mixed_precision_refinement(1e-5)),
+    ("reliable_update_restarts_cg", solver, "pcg_mixed_reliable",
+     "            rr_max = p32.dot(r, r)\n", "            rr_max = p32.dot(r, r)\n            p = 0 * p\n", [],
+     "test_oracle_solver", lambda t: t.test_reliable_updates_keep_the_krylov_iterates(0.9)),
     ("reliable_update_increment_not_rescaled", solver, "pcg_mixed_reliable",
      "x = x + x32.astype(np.float64) / s\n            x32[:] = 0.0",
      "x = x + x32.astype(np.float64)\n            x32[:] = 0.0", [],

@@ -90,6 +90,27 @@ def test_fp32_inner_pcg_iterates_follow_the_krylov_optimum():
         assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref), k
 
 
+@pytest.mark.parametrize("delta", [0.0, 0.9])
+def test_reliable_updates_keep_the_krylov_iterates(delta):
+    """The reliable-update solver replaces the FP32 recurrence residual by the
+    FP64 true one and keeps CG's direction (Sleijpen and van der Vorst 1996),
+    so its iterates stay the Krylov optimum of the FP64 problem, to FP32
+    accuracy, whether it never replaces (delta = 0) or replaces after every
+    iteration (delta = 0.9).  A solver that restarted CG at a replacement, or
+    mixed up the scaling of its increment, leaves that optimum."""
+    m = mesh.pipe(2, 1, 2, 3, L=2.0)
+    P = solver.Problem(m)
+    A, free, rep = P.dense()
+    minv = P.jacobi_inverse().reshape(-1)[rep[free]]
+    b = P.rhs(forcing.evaluate(m.xyz, forcing.random_modes(11, L=2.0)))
+    bg = b.reshape(-1)[rep[free]]
+    for k, ref in krylov_optima(A, lambda v: minv * v, bg, 8):
+        res = solver.pcg_mixed_reliable(P, b, tol=1e-30, delta=delta, maxit=k)
+        assert res.outer_iters == (k if delta > 0 else 0)
+        got = res.x.reshape(-1)[rep[free]]
+        assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref), k
+
+
 def test_manufactured_solution_spectral_convergence_box():
     errs = []
     for N in (2, 4, 6, 8):
