@@ -43,7 +43,7 @@ struct AxParams {
   PcgState* st;
   double* partial;   // [gridDim.x]
   int* err;          // device error word (bounded-wait timeouts of the bulk-copy kernels)
-  T* pout;           // fused: the new direction goes here (nullptr: over p)
+  T* pout = nullptr;  // fused: the new direction goes here (nullptr: over p)
 };
 
 // Double-float (FP32 pair) FP64-accurate variant: G = Ghi + Glo, D = Dhi + Dlo,
@@ -66,7 +66,7 @@ struct AxDFParams {
   double* partial;
   const double* eo64;  // even-odd coefficient tables (even n; see sem_mesh::eo64)
   const float* eodf;
-  double* pout;        // fused: the new direction goes here (nullptr: over p)
+  double* pout = nullptr;  // fused: the new direction goes here (nullptr: over p)
 };
 
 // Kernel variants of the local operator for one (N, precision): 0 and 1 are
@@ -109,7 +109,7 @@ struct VecParams {
   int64_t n;
   PcgState* st;
   double* partial;  // [3 * grid]
-  const T* p2;      // the previous direction (x updated with two directions, see k_pcg_update)
+  const T* p2 = nullptr;  // the previous direction (x updated with two directions, see k_pcg_update)
 };
 int vec_grid();
 // ext = true: an external preconditioner (its kernels write z = M^{-1} r
