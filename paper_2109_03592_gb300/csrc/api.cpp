@@ -374,6 +374,7 @@ const char* sem_status_str(sem_status s) {
 }
 
 sem_status sem_mesh_create(const sem_mesh_desc* desc, void* stream, sem_mesh** out) {
+  SEM_TRACE("sem_mesh_create");
   if (!desc || !out) {
     set_error("sem_mesh_create: null argument");
     return SEM_ERR_INVALID;
@@ -413,6 +414,7 @@ sem_status sem_mesh_destroy(sem_mesh* m) {
 }
 
 sem_status sem_mesh_set_coefficients(sem_mesh* m, const double* h1_dev, const double* h2_dev, void* stream) {
+  SEM_TRACE("sem_mesh_set_coefficients");
   if (!m) {
     set_error("sem_mesh_set_coefficients: null mesh");
     return SEM_ERR_INVALID;
@@ -514,6 +516,7 @@ sem_status sem_mesh_weights(const sem_mesh* m, double* mult_dev, double* mask_de
 
 sem_status sem_ax(const sem_mesh* m, const void* u_dev, void* w_dev, double h1, double h2, sem_prec prec,
                   void* stream) {
+  SEM_TRACE("sem_ax");
   if (!m || !u_dev || !w_dev) {
     set_error("sem_ax: null argument");
     return SEM_ERR_INVALID;
@@ -526,6 +529,7 @@ sem_status sem_ax(const sem_mesh* m, const void* u_dev, void* w_dev, double h1, 
 }
 
 sem_status sem_gs(const sem_mesh* m, void* v_dev, sem_prec prec, int apply_mask, void* stream) {
+  SEM_TRACE("sem_gs");
   if (!m || !v_dev) {
     set_error("sem_gs: null argument");
     return SEM_ERR_INVALID;
@@ -544,6 +548,7 @@ sem_status sem_gs(const sem_mesh* m, void* v_dev, sem_prec prec, int apply_mask,
 }
 
 sem_status sem_rhs(const sem_mesh* m, const double* f_dev, double* b_dev, void* stream) {
+  SEM_TRACE("sem_rhs");
   if (!m || !f_dev || !b_dev) {
     set_error("sem_rhs: null argument");
     return SEM_ERR_INVALID;
@@ -557,6 +562,7 @@ sem_status sem_rhs(const sem_mesh* m, const double* f_dev, double* b_dev, void* 
 }
 
 sem_status sem_apply(const sem_mesh* m, const double* x_dev, double* y_dev, double h1, double h2, void* stream) {
+  SEM_TRACE("sem_apply");
   if (!m || !x_dev || !y_dev || x_dev == y_dev) {
     set_error("sem_apply: null or overlapping argument");
     return SEM_ERR_INVALID;
@@ -570,6 +576,7 @@ sem_status sem_apply(const sem_mesh* m, const double* x_dev, double* y_dev, doub
 }
 
 sem_status sem_jacobi(const sem_mesh* m, double h1, double h2, double* minv_dev, void* stream) {
+  SEM_TRACE("sem_jacobi");
   if (!m || !minv_dev) {
     set_error("sem_jacobi: null argument");
     return SEM_ERR_INVALID;
@@ -581,6 +588,7 @@ sem_status sem_jacobi(const sem_mesh* m, double h1, double h2, double* minv_dev,
 }
 
 sem_status sem_topology_numbering(int64_t E, int N, const int64_t* vert, int64_t* glo_host, int64_t* n_global) {
+  SEM_TRACE("sem_topology_numbering");
   if (!vert || !glo_host) {
     set_error("sem_topology_numbering: null argument");
     return SEM_ERR_INVALID;

@@ -1064,6 +1064,7 @@ void put_idle_engine(int dev, int N, batch::Engine* e) {
 extern "C" sem_status sem_pcg_solve_batch(const sem_mesh* const* meshes, const double* const* b_dev,
                                           double* const* x_dev, const sem_solve_opts* opts,
                                           sem_solve_result* results, int count, void* stream) {
+  SEM_TRACE("sem_pcg_solve_batch");
   if (count < 0 || (count > 0 && (!meshes || !b_dev || !x_dev || !opts))) {
     set_error("sem_pcg_solve_batch: null argument");
     return SEM_ERR_INVALID;

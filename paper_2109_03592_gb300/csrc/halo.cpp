@@ -19,6 +19,7 @@ using namespace sem;
 extern "C" sem_status sem_gs_halo(int64_t E, int N, const int64_t* vert, const int32_t* elem_rank, int rank,
                                   int64_t* n_nodes, int64_t* n_copies, int64_t* node_gid, int64_t* node_ptr,
                                   int32_t* copy_rank, int64_t* copy_local) {
+  SEM_TRACE("sem_gs_halo");
   if (!vert || !elem_rank || !n_nodes || !n_copies || E < 1) {
     set_error("sem_gs_halo: null argument or no elements");
     return SEM_ERR_INVALID;

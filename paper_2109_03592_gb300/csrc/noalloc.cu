@@ -70,6 +70,7 @@ using namespace sem;
 
 extern "C" sem_status sem_pcg_solve_noalloc(const sem_mesh* m, const double* b_dev, double* x_dev,
                                             const sem_solve_opts* opts, sem_solve_result* result, void* stream) {
+  SEM_TRACE("sem_pcg_solve_noalloc");
   if (!m || !b_dev || !x_dev || !opts) {
     set_error("sem_pcg_solve_noalloc: null argument");
     return SEM_ERR_INVALID;

@@ -588,6 +588,7 @@ sem_status sem_pressure_div(const sem_mesh* m, const double* u_dev, double* q_de
 }
 
 sem_status sem_pressure_apply(const sem_mesh* m, const double* p_dev, double* q_dev, double* work_dev, void* stream) {
+  SEM_TRACE("sem_pressure_apply");
   sem_status st = check_mesh(m, "sem_pressure_apply");
   if (st != SEM_OK) return st;
   if (!p_dev || !q_dev || !work_dev) {
@@ -614,6 +615,7 @@ sem_status sem_pressure_apply(const sem_mesh* m, const double* p_dev, double* q_
 }
 
 sem_status sem_pressure_apply_f32(const sem_mesh* m, const float* p_dev, float* q_dev, float* work_dev, void* stream) {
+  SEM_TRACE("sem_pressure_apply_f32");
   sem_status st = check_mesh(m, "sem_pressure_apply_f32");
   if (st != SEM_OK) return st;
   if (!p_dev || !q_dev || !work_dev || p_dev == q_dev) {
@@ -627,6 +629,7 @@ sem_status sem_pressure_apply_f32(const sem_mesh* m, const float* p_dev, float* 
 }
 
 sem_status sem_pressure_diag(const sem_mesh* m, double* d_dev, void* stream) {
+  SEM_TRACE("sem_pressure_diag");
   sem_status st = check_mesh(m, "sem_pressure_diag");
   if (st != SEM_OK) return st;
   if (!d_dev) {
@@ -643,6 +646,7 @@ sem_status sem_pressure_diag(const sem_mesh* m, double* d_dev, void* stream) {
 
 sem_status sem_pressure_solve(const sem_mesh* m, const double* g_dev, double* p_dev, const sem_solve_opts* opts,
                               sem_solve_result* result, void* stream) {
+  SEM_TRACE("sem_pressure_solve");
   sem_status st = check_mesh(m, "sem_pressure_solve");
   if (st != SEM_OK) return st;
   if (!g_dev || !p_dev || !opts || !result || g_dev == p_dev) {

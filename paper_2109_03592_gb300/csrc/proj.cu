@@ -201,6 +201,7 @@ sem_status sem_proj_reset(sem_proj* p) {
 
 sem_status sem_proj_solve(sem_proj* p, const double* b_dev, double* x_dev, const sem_solve_opts* opts,
                           sem_solve_result* result, void* stream) {
+  SEM_TRACE("sem_proj_solve");
   if (!p || !b_dev || !x_dev || !opts) {
     set_error("sem_proj_solve: null argument");
     return SEM_ERR_INVALID;

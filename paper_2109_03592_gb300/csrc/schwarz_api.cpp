@@ -687,6 +687,7 @@ using namespace sem;
 extern "C" {
 
 sem_status sem_schwarz_create(const sem_mesh* mesh, double h1, double h2, int flags, sem_schwarz** out) {
+  SEM_TRACE("sem_schwarz_create");
   if (!mesh || !out) {
     set_error("sem_schwarz_create: null argument");
     return SEM_ERR_INVALID;
@@ -793,6 +794,7 @@ sem_status sem_schwarz_info(const sem_schwarz* sw, sem_schwarz_info_t* info) {
 }
 
 sem_status sem_schwarz_apply(const sem_schwarz* sw, const void* r_dev, void* z_dev, sem_prec prec, void* stream) {
+  SEM_TRACE("sem_schwarz_apply");
   if (!sw || !r_dev || !z_dev || r_dev == z_dev) {
     set_error("sem_schwarz_apply: null argument, or r and z the same array");
     return SEM_ERR_INVALID;
@@ -811,6 +813,7 @@ sem_status sem_schwarz_apply(const sem_schwarz* sw, const void* r_dev, void* z_d
 
 sem_status sem_schwarz_solve(sem_schwarz* sw, const double* b_dev, double* x_dev, const sem_solve_opts* opts,
                              sem_solve_result* result, void* stream) {
+  SEM_TRACE("sem_schwarz_solve");
   if (!sw || !b_dev || !x_dev || !opts) {
     set_error("sem_schwarz_solve: null argument");
     return SEM_ERR_INVALID;

@@ -227,6 +227,7 @@ sem_status sem_schwarz_fdm_1d(int N, double l, double l_lo, double l_hi, int dir
 sem_status sem_schwarz_setup_host(int64_t E, int N, const int64_t* glo, const double* xyz,
                                   const uint8_t* dirichlet_face, double* S_host, double* lam_host,
                                   int64_t* n_distinct) {
+  SEM_TRACE("sem_schwarz_setup_host");
   if (E < 1 || N < 1 || N > kMaxN || !glo || !xyz || !dirichlet_face || !S_host || !lam_host) {
     set_error("sem_schwarz_setup_host: need E >= 1, N in [1, 11] and non-null arrays");
     return SEM_ERR_INVALID;

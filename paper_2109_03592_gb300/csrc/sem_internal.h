@@ -8,10 +8,23 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/sem.h"
 #include "kernels.h"
 
 namespace sem {
+
+// A named range on the NVTX timeline of the Nsight tools for the lifetime of
+// the object (each C-ABI call opens one); without a tool attached the calls
+// return at once.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+#define SEM_TRACE(name) ::sem::TraceRange sem_trace_range_(name)
 
 constexpr int kMaxN = 11;  // highest polynomial order compiled
 

@@ -180,7 +180,11 @@ void engine_main(sem_server* srv, EngineThread* et) {
       }
     }
     if (init_st == SEM_OK && !eng.idle()) {
-      sem_status st = eng.step();
+      sem_status st = SEM_OK;
+      {
+        sem::TraceRange trace("sem_server: batch step");
+        st = eng.step();
+      }
       if (st != SEM_OK) {  // a CUDA failure: fail every request of this engine
         eng.abandon();
         for (auto& q : et->active) {
@@ -325,6 +329,8 @@ void worker_main(sem_server* srv) {
       }
       if (!q) break;
     }
+    sem::TraceRange trace(srv->batch && batchable(*q) ? "sem_server: stage a request for its batch"
+                                                      : "sem_server: solve a request");
     if (srv->batch && batchable(*q)) {
       sem_status st = stage_for_batch(srv, q, s);
       if (st != SEM_OK) {

@@ -741,11 +741,13 @@ extern "C" {
 
 sem_status sem_pcg_solve(const sem_mesh* m, const double* b_dev, double* x_dev, const sem_solve_opts* opts,
                          sem_solve_result* result, void* stream) {
+  SEM_TRACE("sem_pcg_solve");
   return solve_common(m, b_dev, x_dev, false, opts, result, (cudaStream_t)stream);
 }
 
 sem_status sem_pcg_solve_host(const sem_mesh* m, const double* b_host, double* x_host, const sem_solve_opts* opts,
                               sem_solve_result* result, void* stream) {
+  SEM_TRACE("sem_pcg_solve_host");
   return solve_common(m, b_host, x_host, true, opts, result, (cudaStream_t)stream);
 }
 
