@@ -133,7 +133,10 @@ typedef struct {
  * g1..g6 and B (FP64, plus FP32 copies), the first-touch global numbering,
  * the gather-scatter plan, multiplicities, the Dirichlet mask and the
  * assembled diagonals used by the Jacobi preconditioner.  Synchronous.
- * SEM_ERR_BAD_MESH if some det J <= 0 or the topology is inconsistent. */
+ * SEM_ERR_BAD_MESH if some det J <= 0 or the topology is inconsistent;
+ * SEM_ERR_INVALID for a bad descriptor (N outside 1..11, empty or
+ * inconsistent sizes) or a mesh of 2^31 or more local points (the
+ * gather-scatter plan holds 32-bit local indices); SEM_ERR_OOM. */
 sem_status sem_mesh_create(const sem_mesh_desc* desc, void* stream, sem_mesh** out);
 sem_status sem_mesh_destroy(sem_mesh* mesh);
 sem_status sem_mesh_info(const sem_mesh* mesh, sem_mesh_info_t* info);
