@@ -101,3 +101,39 @@ def test_inconsistent_topology_rejected(sem):
     with pytest.raises(sem.SemError) as ei:
         sem.topology_numbering(2, 2, vert)
     assert ei.value.status == sem.SEM_ERR_BAD_MESH
+
+
+# entry points whose first argument is a handle (mesh, space, preconditioner,
+# server) or a descriptor; host-only helpers with sizes first are checked
+# elsewhere
+_HANDLE_CALLS = ("sem_mesh_", "sem_ax", "sem_gs", "sem_rhs", "sem_apply", "sem_jacobi", "sem_pcg_", "sem_proj_",
+                 "sem_pressure_", "sem_schwarz_", "sem_server_")
+_HOST_ONLY = {"sem_mesh_vertices", "sem_pressure_basis", "sem_schwarz_fdm_1d", "sem_schwarz_setup_host",
+              "sem_gs_halo", "sem_topology_numbering"}
+
+
+def test_every_entry_point_rejects_null_handles_without_a_gpu(sem):
+    """Every status-returning call given null handles and buffers returns a
+    status and never aborts: SEM_OK for the destroy calls (a null handle is
+    nothing to free), SEM_ERR_INVALID otherwise.  No call reaches the GPU."""
+    import ctypes as C
+    lib = sem.lib()
+    checked = 0
+    for name, (res, args) in sem.SIGNATURES.items():
+        if res is not C.c_int or name in _HOST_ONLY or not name.startswith(_HANDLE_CALLS):
+            continue
+        if name in ("sem_mesh_fp64_kernel", "sem_mesh_ax_variant"):
+            continue  # not a status: -1 or a variant number
+        vals = []
+        for a in args:
+            if a in (C.c_double, C.c_float):
+                vals.append(1.0)
+            elif a in (C.c_int, C.c_int64, C.c_uint64, C.c_size_t, C.c_uint32, C.c_int32):
+                vals.append(1)
+            else:
+                vals.append(None)
+        st = getattr(lib, name)(*vals)
+        want = sem.SEM_OK if name.endswith("_destroy") else sem.SEM_ERR_INVALID
+        assert st == want, (name, st)
+        checked += 1
+    assert checked >= 35
